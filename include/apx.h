@@ -1,0 +1,151 @@
+/*
+ * apx.h -- C ABI of libapx.so: GB300 (sm_103a) approximate overlap-save
+ * convolution and cross-correlation with per-block companding and tight
+ * packing, after Anam & Andreopoulos, "Throughput Scaling Of Convolution For
+ * Error-Tolerant Multimedia Applications" (arXiv 1201.3018).
+ *
+ * The problem (Section II, Eq. 1): r_out[m] = sum_{n<N} s_in[m-n] k[n] for
+ * m in [0, L+N-1).  Overlap-save splits s_in into P blocks of W_block samples
+ * (Section III).  Per block the middle layer companded the block (Eq. 2),
+ * packs pairs or triples of small integers into one FP64 word (symmetric
+ * packing, Eqs. 4-5; asymmetric packing, Eq. 7), convolves the packed words
+ * with a direct or FFT core (Eqs. 8-9), unpacks (Eqs. 11-15), inverse-companded
+ * (Eq. 16) and places the block's W outputs (Eq. 17).  Under an SNR target the
+ * packing and companding range are chosen per block from the block's marginal
+ * statistics (Table 1 model, Section IV.D); when no packing meets the target
+ * the block runs in full precision (FP32).
+ *
+ * Conventions for every call below:
+ *  - Pointers named s_in, k, r_out, rq_out and stats are DEVICE pointers on the
+ *    context's device unless a call says "host".  The caller owns them.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *    = legacy default stream).  Argument errors are returned immediately;
+ *    data-dependent errors (non-finite input) are recorded in the context and
+ *    returned by apx_sync().
+ *  - Layouts: all arrays are dense, contiguous, element 0 first.
+ *  - Return value: APX_OK (0) or a negative APX_ERR_* code; apx_strerror()
+ *    names it.  No call aborts the process.
+ *  - A context is not thread-safe: one host thread issues its calls.
+ */
+#ifndef APX_H
+#define APX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define APX_OK              0
+#define APX_ERR_ARG        (-1)  /* null pointer, bad length, bad mode bits   */
+#define APX_ERR_WBLOCK     (-2)  /* W_block odd, < N'+3, too large, or not a power of two (FFT core) */
+#define APX_ERR_RANGE      (-3)  /* fixed S_q/K_q beyond the packing's exactness bound */
+#define APX_ERR_NONFINITE  (-4)  /* NaN/Inf in the input or kernel (outputs of the affected blocks are NaN) */
+#define APX_ERR_OOM        (-5)  /* device allocation failed                   */
+#define APX_ERR_BUDGET     (-6)  /* request needs more workspace than the context's budget */
+#define APX_ERR_CUDA       (-7)  /* a CUDA runtime call failed                  */
+#define APX_ERR_TIMEOUT    (-8)  /* a bounded device wait gave up               */
+
+/* ---- mode word: op | core | pack ------------------------------------- */
+#define APX_OP_CONV      0x000u  /* Eq. (1)                                   */
+#define APX_OP_XCORR     0x001u  /* x[l+N-1] = sum_n s[n+l] t[n], l in [-(N-1), L-1] */
+#define APX_CORE_DIRECT  0x000u  /* time-domain block convolution             */
+#define APX_CORE_FFT     0x010u  /* frequency-domain block convolution (W_block a power of two) */
+#define APX_PACK_AUTO    0x000u  /* per-block choice under snr_target_db (Section IV.D) */
+#define APX_PACK_NONE    0x100u  /* full precision, FP32                        */
+#define APX_PACK_SYM     0x200u  /* symmetric packing, Eqs. (4)-(5)            */
+#define APX_PACK_ASYM2   0x300u  /* asymmetric packing, M = 2, Eq. (7)         */
+#define APX_PACK_ASYM3   0x400u  /* asymmetric packing, M = 3, Eq. (7)         */
+
+/* ---- per-block modes reported in apx_block_stats.mode ----------------- */
+#define APX_BLK_FULL      0
+#define APX_BLK_SYM       1
+#define APX_BLK_ASYM2     2
+#define APX_BLK_ASYM3     3
+#define APX_BLK_ZERO      4      /* ||s||_inf = 0 or ||k||_inf = 0: exact zeros   */
+#define APX_BLK_NONFINITE 5
+
+/* What one block did.  48 bytes, naturally aligned. */
+typedef struct {
+    int32_t mode;         /* APX_BLK_*                                         */
+    int32_t Sq, Kq;       /* companding ranges of Eq. (2) (0 for full)          */
+    int32_t b;            /* packing coefficient eps = 2^-b (Eq. 6, power of two) */
+    float   cs;           /* c_s = S_q / ||s||_inf of the block                 */
+    float   maxabs;       /* ||s||_inf over the block's W_block window          */
+    double  sigma2;       /* second moment of the window (24-bit fixed point)   */
+    double  snr_pred_db;  /* Table 1 model SNR of the chosen packing (inf: full) */
+    double  fft_err;      /* FFT core: error bound in units of the finest digit */
+} apx_block_stats;
+
+typedef struct apx_ctx apx_ctx;
+
+/* Create a context on CUDA device `device`.  It owns a device workspace for
+ * prepared kernels (companded/packed taps, kernel spectra, twiddles), grown on
+ * demand up to mem_budget_bytes (0 = 4 GiB).  *out receives the handle.
+ * Errors: APX_ERR_ARG (out NULL, bad device), APX_ERR_CUDA. */
+int apx_create(apx_ctx** out, int device, size_t mem_budget_bytes);
+
+/* Free the context and its workspace (synchronises its device).  NULL is a no-op. */
+void apx_destroy(apx_ctx* ctx);
+
+/* Host-only block plan (Section III, Eq. 17).  For length-L input, length-N
+ * kernel and W_block samples per block: *W = W_block - N' - 1 outputs per
+ * block (N' = N rounded up to odd) and *P blocks.  The FFT core adds
+ * ceil((N'-1)/W) head blocks in front (a circular block convolution cannot
+ * produce the first block's leading outputs).  Either out pointer may be NULL.
+ * Errors: APX_ERR_ARG, APX_ERR_WBLOCK. */
+int apx_plan_blocks(int64_t L, int32_t N, int32_t W_block, uint32_t mode, int64_t* P, int32_t* W);
+
+/* Approximate convolution / cross-correlation under a per-block SNR target
+ * (pack bits APX_PACK_AUTO; Section IV.D), or with a forced packing whose
+ * S_q = K_q is the largest the packing's exactness bound admits.
+ *   s_in   : device, L FP32 samples
+ *   k      : device, N FP32 taps (the template t for APX_OP_XCORR)
+ *   r_out  : device, L+N-1 FP32 outputs
+ *   rq_out : device or NULL, L+N-1 int32: the exact integer-domain result
+ *            r~ = s~ * k~ of Eqs. (11)-(15) for outputs of packed blocks, 0 elsewhere
+ *   stats  : device or NULL, P entries (apx_plan_blocks with the same mode)
+ * Errors: APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_BUDGET, APX_ERR_OOM, APX_ERR_CUDA. */
+int apx_conv(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
+             uint32_t mode, double snr_target_db, float* r_out, int32_t* rq_out,
+             apx_block_stats* stats, void* stream);
+
+/* As apx_conv with a fixed companding range (S_q, K_q in [1, 2^20]) for every
+ * block and the packing given by the pack bits (SYM, ASYM2 or ASYM3).  Errors
+ * as apx_conv, plus APX_ERR_RANGE when N' S_q K_q exceeds the packing's
+ * exactness bound.  With the FFT core a block whose error bound exceeds 1/4
+ * digit runs in full precision instead (its stats say so). */
+int apx_conv_fixed(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N,
+                   int32_t W_block, uint32_t mode, int32_t S_q, int32_t K_q, float* r_out,
+                   int32_t* rq_out, apx_block_stats* stats, void* stream);
+
+/* Full-precision twin (no companding, no packing): FP32 overlap-save with the
+ * same block geometry and core.  Pack bits are ignored. */
+int apx_conv_full(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N,
+                  int32_t W_block, uint32_t mode, float* r_out, void* stream);
+
+/* End-to-end variant for callers holding HOST data: copies s_in (host, L) and
+ * k (host, N) to the device, runs apx_conv (S_q = K_q = 0) or apx_conv_fixed,
+ * and copies r_out (host, L+N-1) back, all on `stream`, then synchronises it.
+ * Host buffers should be pinned for full copy speed.  Device staging buffers
+ * come from the context workspace.  Returns the apx_sync() status. */
+int apx_conv_host(apx_ctx* ctx, const float* s_in_host, int64_t L, const float* k_host, int32_t N,
+                  int32_t W_block, uint32_t mode, double snr_target_db, int32_t S_q, int32_t K_q,
+                  float* r_out_host, void* stream);
+
+/* Wait for `stream` and return the data-dependent status of the calls issued
+ * since the previous apx_sync (APX_OK or APX_ERR_NONFINITE), then clear it. */
+int apx_sync(apx_ctx* ctx, void* stream);
+
+/* Number of CUDA kernel launches this context has issued since creation. */
+int64_t apx_launch_count(const apx_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* apx_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -74,6 +74,7 @@ def _declare(L):
         "or_conv_ref": (None, [vp, i64, vp, i32, vp]),
         "or_xcorr_ref": (None, [vp, i64, vp, i32, vp]),
         "or_conv_int": (None, [vp, i64, vp, i32, vp]),
+        "or_conv_ref_at": (None, [vp, i64, vp, i32, vp, i64, vp]),
         "or_plan": (C.c_int, [i64, i32, i32, C.c_int, C.POINTER(Plan)]),
         "or_block_start": (i64, [C.POINTER(Plan), i64]),
         "or_block_out_range": (None, [C.POINTER(Plan), i64, C.POINTER(i32), C.POINTER(i32)]),
@@ -99,7 +100,7 @@ def _declare(L):
         "or_unpack_sym_digits": (C.c_int, [vp, i32, i32, i32, vp]),
         "or_unpack_sym_fp64": (None, [vp, i32, i32, d, d, d, vp]),
         "or_unpack_asym": (C.c_int, [vp, i32, i32, i32, i64, i32, i32, vp]),
-        "or_apx_conv": (C.c_int, [vp, i64, vp, i32, i32, u32, d, i32, i32, vp, vp, vp, C.c_int]),
+        "or_apx_conv": (C.c_int, [vp, i64, vp, i32, i32, u32, d, i32, i32, vp, vp, vp, C.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -142,6 +143,14 @@ def xcorr_ref(s, t):
     s, t = _f64(s), _f64(t)
     r = np.empty(len(s) + len(t) - 1, np.float64)
     lib().or_xcorr_ref(_p(s), len(s), _p(t), len(t), _p(r))
+    return r
+
+
+def conv_ref_at(s, k, idx):
+    """Eq. (1) at the given output indices."""
+    s, k, idx = _f64(s), _f64(k), _i64(idx)
+    r = np.empty(len(idx), np.float64)
+    lib().or_conv_ref_at(_p(s), len(s), _p(k), len(k), _p(idx), len(idx), _p(r))
     return r
 
 
@@ -302,9 +311,11 @@ def unpack_asym(rbar, Ls, M, rmax, b, nout):
 
 
 # ---------------------------------------------------------------- pipeline
-def apx_conv(s, k, Wblock, mode, snr_db=0.0, Sq=0, Kq=0, nthreads=1, want_int=True):
+def apx_conv(s, k, Wblock, mode, snr_db=0.0, Sq=0, Kq=0, nthreads=1, want_int=True, want=None):
     """The whole method (a1..a9).  Returns (r_out float32, rq int64 or None,
-    stats list of BlockStats, rc)."""
+    stats list of BlockStats, rc).  `want` (bool mask over the L+N-1 outputs)
+    limits the full-precision outputs computed; packed blocks and statistics
+    are always computed in full."""
     s, k = _f32(s), _f32(k)
     L, N = len(s), len(k)
     fft = (mode & 0xF0) == CORE_FFT
@@ -316,8 +327,9 @@ def apx_conv(s, k, Wblock, mode, snr_db=0.0, Sq=0, Kq=0, nthreads=1, want_int=Tr
     r = np.zeros(L + N - 1, np.float32)
     rq = np.zeros(L + N - 1, np.int64) if want_int else None
     st = (BlockStats * max(P, 1))()
+    wm = None if want is None else np.ascontiguousarray(want, dtype=np.uint8)
     rc = lib().or_apx_conv(_p(s), L, _p(k), N, Wblock, mode, float(snr_db), Sq, Kq, _p(r),
-                           _p(rq) if want_int else None, st, nthreads)
+                           _p(rq) if want_int else None, st, nthreads, None if wm is None else _p(wm))
     return r, rq, list(st), rc
 
 

@@ -55,6 +55,20 @@ void or_xcorr_ref(const double* s, int64_t L, const double* t, int32_t N, double
     }
 }
 
+/* Eq. (1) at chosen output indices only (for spot checks of long signals). */
+void or_conv_ref_at(const double* s, int64_t L, const double* k, int32_t N, const int64_t* idx, int64_t n,
+                    double* r) {
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t m = idx[j];
+        double acc = 0.0;
+        for (int32_t q = 0; q < N; ++q) {
+            int64_t i = m - q;
+            if (i >= 0 && i < L) acc += s[i] * k[q];
+        }
+        r[j] = acc;
+    }
+}
+
 /* Eq. (1) over integers: the exact target r~ = s~ * k~ of the packed path. */
 void or_conv_int(const int64_t* s, int64_t L, const int64_t* k, int32_t N, int64_t* r) {
     for (int64_t m = 0; m < L + N - 1; ++m) {
@@ -617,7 +631,8 @@ static int run_packed_block(const mode_t_* md, const or_plan_t* p, int64_t i, co
 
 int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wblock, uint32_t mode,
                 double snr_db, int32_t Sq_fixed, int32_t Kq_fixed,
-                float* r_out, int64_t* rq_out, or_block_stats_t* stats, int nthreads) {
+                float* r_out, int64_t* rq_out, or_block_stats_t* stats, int nthreads,
+                const uint8_t* want) {
     if (!s || !k || !r_out) return OR_ERR_ARG;
     uint32_t op = mode & OR_OP_MASK, core = mode & OR_CORE_MASK, pack = mode & OR_PACK_MASK;
     if (op > OR_OP_XCORR || (core != OR_CORE_DIRECT && core != OR_CORE_FFT) || pack > OR_PACK_ASYM3)
@@ -725,7 +740,9 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
                     r_out[g] = (float)((double)rqb[j] / sc);
                     if (rq_out) rq_out[g] = rqb[j];
                 } else if (kind == 0) {
-                    /* no admissible packing: full precision, Eq. (1) over the window */
+                    /* no admissible packing: full precision, Eq. (1) over the window
+                     * (only where the caller asked for it: want[g] != 0 or want NULL) */
+                    if (want && !want[g]) continue;
                     double acc = 0.0;
                     for (int32_t n = 0; n < N; ++n) {
                         int32_t t = j - n;

@@ -78,6 +78,8 @@ typedef struct {
 void or_conv_ref(const double* s, int64_t L, const double* k, int32_t N, double* r);
 void or_xcorr_ref(const double* s, int64_t L, const double* t, int32_t N, double* r);
 void or_conv_int(const int64_t* s, int64_t L, const int64_t* k, int32_t N, int64_t* r);
+void or_conv_ref_at(const double* s, int64_t L, const double* k, int32_t N, const int64_t* idx, int64_t n,
+                    double* r);
 
 /* ---- a1: block plan ------------------------------------------------------ */
 int     or_plan(int64_t L, int32_t N, int32_t Wblock, int fft, or_plan_t* p);
@@ -121,7 +123,8 @@ int  or_unpack_asym(const double* rbar, int32_t nr, int32_t Ls, int32_t M, int64
 /* ---- a1..a9: whole pipeline ---------------------------------------------- */
 int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wblock, uint32_t mode,
                 double snr_db, int32_t Sq_fixed, int32_t Kq_fixed,
-                float* r_out, int64_t* rq_out, or_block_stats_t* stats, int nthreads);
+                float* r_out, int64_t* rq_out, or_block_stats_t* stats, int nthreads,
+                const uint8_t* want);
 
 #ifdef __cplusplus
 }

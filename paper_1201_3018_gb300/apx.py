@@ -1,0 +1,182 @@
+"""Python binding of libapx.so (argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module turns
+torch tensors into device pointers and sizes, calls the C ABI declared in
+``include/apx.h`` and raises on a non-zero status.  PyTorch supplies device
+memory and streams.  There is no fallback: if the library is missing or no GPU
+is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapx.so")
+_lock = threading.Lock()
+_lib = None
+
+APX_OK, APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE, APX_ERR_NONFINITE = 0, -1, -2, -3, -4
+APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA, APX_ERR_TIMEOUT = -5, -6, -7, -8
+OP_CONV, OP_XCORR = 0x000, 0x001
+CORE_DIRECT, CORE_FFT = 0x000, 0x010
+PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
+BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
+
+STATS_DTYPE = np.dtype([("mode", "<i4"), ("Sq", "<i4"), ("Kq", "<i4"), ("b", "<i4"), ("cs", "<f4"),
+                        ("maxabs", "<f4"), ("sigma2", "<f8"), ("snr_pred_db", "<f8"), ("fft_err", "<f8")])
+assert STATS_DTYPE.itemsize == 48
+
+# (restype, argtypes) of every entry point in include/apx.h
+_vp, _i32, _i64, _u32, _d, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double, C.c_size_t
+SIGNATURES = {
+    "apx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _sz]),
+    "apx_destroy": (None, [_vp]),
+    "apx_plan_blocks": (C.c_int, [_i64, _i32, _i32, _u32, C.POINTER(_i64), C.POINTER(_i32)]),
+    "apx_conv": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _d, _vp, _vp, _vp, _vp]),
+    "apx_conv_fixed": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "apx_conv_full": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _vp, _vp]),
+    "apx_conv_host": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _d, _i32, _i32, _vp, _vp]),
+    "apx_sync": (C.c_int, [_vp, _vp]),
+    "apx_launch_count": (_i64, [_vp]),
+    "apx_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+class ApxError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (fn, strerror(status), status))
+
+
+def lib():
+    """Load libapx.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libapx.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().apx_strerror(int(status)).decode()
+
+
+def _check(fn, rc):
+    if rc != APX_OK:
+        raise ApxError(fn, rc)
+    return rc
+
+
+def plan_blocks(L: int, N: int, W_block: int, mode: int = 0):
+    P, W = _i64(), _i32()
+    _check("apx_plan_blocks", lib().apx_plan_blocks(L, N, W_block, mode, C.byref(P), C.byref(W)))
+    return P.value, W.value
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_f32(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+    return t
+
+
+class Context:
+    """An apx_ctx on one device: owns the prepared-kernel workspace."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self.device = device
+        h = C.c_void_p()
+        _check("apx_create", lib().apx_create(C.byref(h), device, budget_bytes))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def launch_count(self) -> int:
+        return lib().apx_launch_count(self._h)
+
+    # ---------------------------------------------------------------- raw entry points
+    def apx_conv(self, s, k, W_block, mode, snr_db, r, rq=None, stats=None, stream=None):
+        _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        return _check("apx_conv", lib().apx_conv(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(), W_block, mode,
+                                                 float(snr_db), _ptr(r), _ptr(rq), _ptr(stats), _stream(stream)))
+
+    def apx_conv_fixed(self, s, k, W_block, mode, Sq, Kq, r, rq=None, stats=None, stream=None):
+        _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        return _check("apx_conv_fixed", lib().apx_conv_fixed(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(),
+                                                             W_block, mode, Sq, Kq, _ptr(r), _ptr(rq),
+                                                             _ptr(stats), _stream(stream)))
+
+    def apx_conv_full(self, s, k, W_block, mode, r, stream=None):
+        _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        return _check("apx_conv_full", lib().apx_conv_full(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(),
+                                                           W_block, mode, _ptr(r), _stream(stream)))
+
+    def apx_conv_host(self, s_host, k_host, W_block, mode, snr_db=0.0, Sq=0, Kq=0, r_host=None, stream=None):
+        """s_host, k_host, r_host: contiguous float32 CPU tensors (pinned for speed)."""
+        L, N = s_host.numel(), k_host.numel()
+        return _check("apx_conv_host", lib().apx_conv_host(self._h, _ptr(s_host), L, _ptr(k_host), N, W_block,
+                                                           mode, float(snr_db), Sq, Kq, _ptr(r_host),
+                                                           _stream(stream)))
+
+    def apx_sync(self, stream=None):
+        return _check("apx_sync", lib().apx_sync(self._h, _stream(stream)))
+
+    # ---------------------------------------------------------------- convenience
+    def conv(self, s, k, W_block, mode=0, snr_db=None, Sq=None, Kq=None, want_int=False, want_stats=False,
+             stream=None):
+        """Allocate outputs and run apx_conv / apx_conv_fixed / apx_conv_full.
+        Returns (r, rq or None, stats ndarray or None)."""
+        import torch
+        L, N = s.numel(), k.numel()
+        r = torch.empty(L + N - 1, dtype=torch.float32, device=s.device)
+        rq = torch.empty(L + N - 1, dtype=torch.int32, device=s.device) if want_int else None
+        st = None
+        if want_stats:
+            P, _ = plan_blocks(L, N, W_block, mode)
+            st = torch.empty(P * STATS_DTYPE.itemsize, dtype=torch.uint8, device=s.device)
+        pack = mode & 0xF00
+        if pack == PACK_NONE and rq is None and st is None:
+            self.apx_conv_full(s, k, W_block, mode, r, stream=stream)
+        elif Sq is not None and pack != PACK_NONE:
+            self.apx_conv_fixed(s, k, W_block, mode, Sq, Kq, r, rq, st, stream=stream)
+        else:
+            self.apx_conv(s, k, W_block, mode, 0.0 if snr_db is None else snr_db, r, rq, st, stream=stream)
+        stats = None
+        if st is not None:
+            stats = np.frombuffer(st.cpu().numpy().tobytes(), dtype=STATS_DTYPE)
+        return r, rq, stats

@@ -1,0 +1,486 @@
+// apx_api.cu -- host side of libapx: the C ABI declared in include/apx.h.
+//
+// Per call: validate, plan the blocks (Section III, Eq. 17), choose the packing
+// candidates (largest S_q = K_q within each packing's exactness bound, reading
+// c5; Section IV.D), then enqueue the kernel preparation and the block kernels
+// on the caller's stream.  Nothing here touches sample data on the host.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "apx_launch.h"
+
+using namespace apx;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct apx_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int64_t launches = 0;
+    DevBuf ki, kfull, kbar[kMaxCand], flags, sel, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    int tw_wb = 0;  // W_block the twiddle tables were built for
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return APX_OK;
+    return e == cudaErrorMemoryAllocation ? APX_ERR_OOM : APX_ERR_CUDA;
+}
+
+// Grow a workspace buffer to at least `bytes` (256-byte aligned by cudaMalloc).
+int ensure(apx_ctx* c, DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes) return APX_OK;
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (c->in_use - b.bytes + want > c->budget) return APX_ERR_BUDGET;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) return cuda_status(e);
+        c->in_use -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) { b.p = nullptr; return cuda_status(e); }
+    b.bytes = want;
+    c->in_use += want;
+    return APX_OK;
+}
+
+void release(apx_ctx* c, DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    c->in_use -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ------------------------------------------------------------------ host arithmetic of the selector
+// eps = 2^-b, smallest b with 2^b >= 2 R_max + 1 (reading c3).
+int bits_for(long long Rmax) {
+    int b = 0;
+    while (b < 62 && (1ll << b) < 2 * Rmax + 1) ++b;
+    return b;
+}
+
+typedef unsigned __int128 u128;
+
+// Reading c5: exactness of the FP64 packed convolution (scaled magnitude <= 2^53).
+bool exact_ok(int blk, int Nodd, int S, int K) {
+    if (Nodd < 1 || S < 1 || K < 1) return false;
+    u128 SK = (u128)(unsigned)S * (unsigned)K;
+    u128 R = SK * (unsigned)Nodd;
+    const u128 lim = (u128)1 << 53;
+    if (R >= lim) return false;
+    int b = bits_for((long long)R);
+    if (blk == APX_BLK_SYM) {
+        if (2 * b > 100) return false;
+        u128 A = (u128)((Nodd + 1) / 2) * SK, C = (u128)((Nodd - 1) / 2) * SK;
+        return (A << (2 * b)) + (R << b) + C <= lim;
+    }
+    int M = blk == APX_BLK_ASYM2 ? 2 : 3;
+    if (b * (M - 1) > 100) return false;
+    u128 gsum = 0;
+    for (int q = 0; q < M; ++q) gsum += (u128)1 << (b * q);
+    return R * gsum <= lim;
+}
+
+// Largest Q = S_q = K_q in [1, 2^20] within the exactness bound, 0 if none.
+int qmax_direct(int blk, int Nodd) {
+    if (!exact_ok(blk, Nodd, 1, 1)) return 0;
+    int lo = 1, hi = 1 << 20;
+    if (exact_ok(blk, Nodd, hi, hi)) return hi;
+    while (hi - lo > 1) {
+        int mid = lo + (hi - lo) / 2;
+        if (exact_ok(blk, Nodd, mid, mid)) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Reading c7: (3 phi + 16 u) with phi = Lg eta / (1 - Lg eta), eta = mu + gamma_4 (sqrt 2 + mu),
+// mu = 4u, Lg = log2(n) + 2 (Higham, Thm 24.2, for radix-2 structured FFTs).
+double fft_const(int log2n) {
+    const double u = ldexp(1.0, -53);
+    double mu = 4.0 * u;
+    double g4 = (4.0 * u) / (1.0 - 4.0 * u);
+    double eta = mu + g4 * (sqrt(2.0) + mu);
+    double Lg = (double)(log2n + 2);
+    double phi = (Lg * eta) / (1.0 - Lg * eta);
+    return 3.0 * phi + 16.0 * u;
+}
+
+int digit_shift(int blk, int b) { return blk == APX_BLK_ASYM3 ? 2 * b : b; }
+
+int ilog2i(long long n) { int l = 0; while ((1ll << l) < n) ++l; return l; }
+
+int fft_log2n(int blk, int Wb) { return blk == APX_BLK_SYM ? ilog2i(Wb / 2) : ilog2i(Wb); }
+
+// FFT core guide: largest Q <= qmax_direct whose a-priori bound (crest factor 3
+// for block and kernel) stays below 1/4 digit.  Every block is checked again
+// with its exact norm on the device.
+int qmax_fft(int blk, int Nodd, int Wb) {
+    int qd = qmax_direct(blk, Nodd);
+    int lg = fft_log2n(blk, Wb);
+    double C = fft_const(lg);
+    for (int Q = qd; Q >= 1; --Q) {
+        long long Rmax = (long long)Nodd * Q * Q;
+        int b = bits_for(Rmax);
+        double taps = blk == APX_BLK_SYM ? (double)((Nodd + 1) / 2) : (double)Nodd;
+        double kscale = blk == APX_BLK_SYM ? ldexp(1.0, b) + 1.0 : 1.0;
+        double l1 = taps * (double)Q / 3.0 * kscale;
+        double l2 = sqrt((double)Wb) * (double)Q / 3.0;
+        double E = C * l1 * l2;
+        if (ldexp(E, digit_shift(blk, b)) < 0.25) return Q;
+    }
+    return 0;
+}
+
+Cand make_cand(int blk, int S, int K, int Nodd, int Wb) {
+    Cand c;
+    memset(&c, 0, sizeof c);
+    c.blk = blk;
+    c.M = blk == APX_BLK_SYM ? 1 : (blk == APX_BLK_ASYM2 ? 2 : 3);
+    c.S = S; c.K = K;
+    c.Rmax = (long long)Nodd * S * K;
+    c.b = bits_for(c.Rmax);
+    c.sc = digit_shift(blk, c.b);
+    c.nk = blk == APX_BLK_SYM ? (Nodd + 1) / 2 : Nodd;
+    c.log2n = fft_log2n(blk, Wb);
+    c.fftc = fft_const(c.log2n);
+    return c;
+}
+
+struct Plan {
+    int Nodd, W, head, fft;
+    long long P;
+};
+
+int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
+    if (L < 1 || N < 1) return APX_ERR_ARG;
+    if ((mode & 0xFu) > APX_OP_XCORR || ((mode >> 4) & 0xFu) > 1u || ((mode >> 8) & 0xFu) > 4u ||
+        (mode & ~0xFFFu))
+        return APX_ERR_ARG;
+    int fft = (mode & 0xF0u) == APX_CORE_FFT;
+    int Nodd = (N % 2) ? N : N + 1;
+    if (Wb < 4 || (Wb % 2) || Wb > kMaxWblock) return APX_ERR_WBLOCK;
+    int W = Wb - Nodd - 1;
+    if (W < 2) return APX_ERR_WBLOCK;
+    if (fft && (Wb & (Wb - 1))) return APX_ERR_WBLOCK;
+    long long span = L + N - Nodd;
+    long long P = (span + W - 1) / W;
+    if (P < 1) P = 1;
+    p->Nodd = Nodd; p->W = W; p->fft = fft;
+    p->head = fft ? (Nodd - 1 + W - 1) / W : 0;
+    p->P = P + p->head;
+    if (p->P > 0x7fffffffll) return APX_ERR_ARG;
+    return APX_OK;
+}
+
+int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+// Direct core shared-memory layout for the candidate set.
+size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl) {
+    dl->padF = round_up(Nodd, 8);
+    size_t xs_bytes = (size_t)4 * (dl->padF + Wb + 8);
+    int padS = 0, body = 0, nT = 0;
+    for (int i = 0; i < nc; ++i) {
+        int nkp = round_up(c[i].nk, 4);
+        if (nkp > padS) padS = nkp;
+        if (c[i].blk == APX_BLK_SYM) {
+            body = body > Wb / 2 + 4 ? body : Wb / 2 + 4;
+            nT = nT > Wb / 2 ? nT : Wb / 2;
+        } else {
+            int Ls = (Wb + c[i].M - 1) / c[i].M;
+            int bb = Ls + Nodd + 4;
+            body = body > bb ? body : bb;
+            int t = Ls + Nodd - 1 < Wb ? Ls + Nodd - 1 : Wb;
+            nT = nT > t ? nT : t;
+        }
+    }
+    dl->offS = (int)((xs_bytes + 15) / 16 * 16);
+    dl->padS = padS;
+    dl->nS = nc ? padS + body : 0;
+    dl->offT = (int)(((size_t)dl->offS + (size_t)8 * dl->nS + 15) / 16 * 16);
+    return (size_t)dl->offT + (size_t)8 * nT;
+}
+
+// exp(-2 pi i t / Wb), t in [0, Wb), from long double arithmetic.
+int ensure_twiddles(apx_ctx* c, int Wb, cudaStream_t st) {
+    if (c->tw_wb == Wb) return APX_OK;
+    int rc = ensure(c, c->tw64, sizeof(double2) * Wb);
+    if (!rc) rc = ensure(c, c->tw32, sizeof(float2) * Wb);
+    if (rc) return rc;
+    std::vector<double2> t64(Wb);
+    std::vector<float2> t32(Wb);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int t = 0; t < Wb; ++t) {
+        long double a = two_pi * (long double)t / (long double)Wb;
+        t64[t].x = (double)cosl(a);
+        t64[t].y = (double)-sinl(a);
+        t32[t].x = (float)t64[t].x;
+        t32[t].y = (float)t64[t].y;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->tw64.p, t64.data(), sizeof(double2) * Wb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tw32.p, t32.data(), sizeof(float2) * Wb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->tw_wb = Wb;
+    return APX_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
+int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
+        int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
+        apx_block_stats* st, cudaStream_t stream) {
+    if (!ctx || !s || !k || !r) return APX_ERR_ARG;
+    Plan pl;
+    int rc = plan(L, N, Wb, mode, &pl);
+    if (rc) return rc;
+    const uint32_t pack = mode & 0xF00u;
+    if (sel_kind == 0 && pack == APX_PACK_NONE) sel_kind = 2;
+    if (sel_kind == 1 && (pack == APX_PACK_AUTO || pack == APX_PACK_NONE)) return APX_ERR_ARG;
+    if (sel_kind == 0 && pack != APX_PACK_AUTO) {
+        // forced packing, largest S_q = K_q its exactness bound admits
+        int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
+        int Q = pl.fft ? qmax_fft(blk, pl.Nodd, Wb) : qmax_direct(blk, pl.Nodd);
+        if (Q < 1) return APX_ERR_RANGE;
+        S = K = Q;
+        sel_kind = 1;
+    }
+    DeviceGuard dg(ctx->device);
+
+    Params p;
+    memset(&p, 0, sizeof p);
+    p.s = s; p.L = L; p.N = N; p.Nodd = pl.Nodd; p.Wb = Wb; p.W = pl.W; p.head = pl.head; p.fft = pl.fft;
+    p.P = pl.P; p.out_len = L + N - 1;
+    p.r = r; p.rq = rq; p.st = st;
+    p.autosel = sel_kind == 0;
+    p.thr = pow(10.0, snr_db / 10.0);
+    int nc = 0;
+    if (sel_kind == 0) {
+        const int order[3] = {APX_BLK_SYM, APX_BLK_ASYM3, APX_BLK_ASYM2};  // Table 1 ranking
+        for (int j = 0; j < 3; ++j) {
+            int Q = pl.fft ? qmax_fft(order[j], pl.Nodd, Wb) : qmax_direct(order[j], pl.Nodd);
+            if (Q >= 1) p.cand[nc++] = make_cand(order[j], Q, Q, pl.Nodd, Wb);
+        }
+    } else if (sel_kind == 1) {
+        int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
+        if (S < 1 || K < 1 || S > (1 << 20) || K > (1 << 20)) return APX_ERR_ARG;
+        if (!exact_ok(blk, pl.Nodd, S, K)) return APX_ERR_RANGE;
+        p.cand[nc++] = make_cand(blk, S, K, pl.Nodd, Wb);
+    }
+
+    // Shared memory of the block kernel for this candidate set.
+    size_t smem;
+    if (!pl.fft) {
+        smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
+        while (smem > (size_t)kMaxSmem && nc > 0 && sel_kind == 0) {
+            // drop the widest asymmetric candidate that does not fit
+            int drop = -1;
+            for (int j = 0; j < nc; ++j) if (p.cand[j].blk != APX_BLK_SYM) drop = j;
+            if (drop < 0) drop = nc - 1;
+            for (int j = drop; j + 1 < nc; ++j) p.cand[j] = p.cand[j + 1];
+            --nc;
+            smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
+        }
+        if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
+    } else {
+        bool asym = false;
+        for (int j = 0; j < nc; ++j) asym |= p.cand[j].blk != APX_BLK_SYM;
+        smem = (size_t)4 * Wb + (asym ? (size_t)8 * Wb : (size_t)4 * Wb);
+    }
+    p.ncand = nc;
+
+    // Workspace.
+    const int nkp32 = round_up(pl.Nodd, 8);
+    rc = ensure(ctx, ctx->ki, sizeof(KInfo));
+    if (!rc) rc = ensure(ctx, ctx->kfull, sizeof(float) * nkp32);
+    if (!rc) rc = ensure(ctx, ctx->flags, 2 * sizeof(unsigned));
+    for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->kbar[j], sizeof(double) * round_up(p.cand[j].nk, 4));
+    if (!rc && pl.fft) {
+        const size_t m1 = (size_t)Wb / 2 + 1;
+        rc = ensure(ctx, ctx->sel, sizeof(Sel) * pl.P);
+        if (!rc) rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
+        for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->Hc[j], sizeof(double2) * m1);
+        if (!rc) rc = ensure_twiddles(ctx, Wb, stream);
+    }
+    if (rc) return rc;
+
+    double* kb[kMaxCand] = {nullptr, nullptr, nullptr};
+    for (int j = 0; j < nc; ++j) {
+        kb[j] = (double*)ctx->kbar[j].p;
+        p.cand[j].kbar = kb[j];
+        p.cand[j].H = (const double2*)ctx->Hc[j].p;
+    }
+    for (int j = nc; j < kMaxCand; ++j) kb[j] = kb[0] ? kb[0] : (double*)ctx->kfull.p;
+    p.kfull = (const float*)ctx->kfull.p;
+    p.ki = (const KInfo*)ctx->ki.p;
+    p.status = (unsigned*)ctx->flags.p;
+    p.used = (unsigned*)ctx->flags.p + 1;
+    p.sel = (Sel*)ctx->sel.p;
+    p.Hfull = (const float2*)ctx->Hfull.p;
+    p.tw64 = (const double2*)ctx->tw64.p;
+    p.tw32 = (const float2*)ctx->tw32.p;
+
+    const int xcorr = (mode & 0xFu) == APX_OP_XCORR;
+    cudaError_t e = launch_prep(p, k, xcorr, kb, (KInfo*)ctx->ki.p, (float*)ctx->kfull.p, stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess) {
+        if (!pl.fft) {
+            e = launch_direct(p, smem, stream);
+            ctx->launches += 1;
+        } else {
+            e = launch_select(p, stream);
+            if (e == cudaSuccess) {
+                double2* Hc[kMaxCand] = {(double2*)ctx->Hc[0].p, (double2*)ctx->Hc[1].p, (double2*)ctx->Hc[2].p};
+                for (int j = 0; j < kMaxCand; ++j) if (!Hc[j]) Hc[j] = (double2*)ctx->Hfull.p;
+                e = launch_spectra(p, (float2*)ctx->Hfull.p, Hc, stream);
+            }
+            if (e == cudaSuccess) e = launch_fft(p, smem, stream);
+            ctx->launches += 3;
+        }
+    }
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int apx_create(apx_ctx** out, int device, size_t mem_budget_bytes) {
+    if (!out) return APX_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (device < 0 || device >= n) return APX_ERR_ARG;
+    apx_ctx* c = new apx_ctx();
+    c->device = device;
+    c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
+    DeviceGuard dg(device);
+    int rc = ensure(c, c->flags, 2 * sizeof(unsigned));
+    if (!rc) rc = cuda_status(cudaMemset(c->flags.p, 0, 2 * sizeof(unsigned)));
+    if (rc) { apx_destroy(c); return rc; }
+    *out = c;
+    return APX_OK;
+}
+
+void apx_destroy(apx_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        cudaDeviceSynchronize();
+        DevBuf* all[] = {&c->ki, &c->kfull, &c->kbar[0], &c->kbar[1], &c->kbar[2], &c->flags, &c->sel,
+                         &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32, &c->hs, &c->hk, &c->hr};
+        for (DevBuf* b : all) release(c, *b);
+    }
+    delete c;
+}
+
+int apx_plan_blocks(int64_t L, int32_t N, int32_t W_block, uint32_t mode, int64_t* P, int32_t* W) {
+    Plan p;
+    int rc = plan(L, N, W_block, mode, &p);
+    if (rc) return rc;
+    if (P) *P = p.P;
+    if (W) *W = p.W;
+    return APX_OK;
+}
+
+int apx_conv(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
+             uint32_t mode, double snr_target_db, float* r_out, int32_t* rq_out, apx_block_stats* stats,
+             void* stream) {
+    return run(ctx, s_in, L, k, N, W_block, mode, 0, snr_target_db, 0, 0, r_out, rq_out, stats,
+               (cudaStream_t)stream);
+}
+
+int apx_conv_fixed(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
+                   uint32_t mode, int32_t S_q, int32_t K_q, float* r_out, int32_t* rq_out,
+                   apx_block_stats* stats, void* stream) {
+    return run(ctx, s_in, L, k, N, W_block, mode, 1, 0.0, S_q, K_q, r_out, rq_out, stats, (cudaStream_t)stream);
+}
+
+int apx_conv_full(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
+                  uint32_t mode, float* r_out, void* stream) {
+    return run(ctx, s_in, L, k, N, W_block, (mode & 0xFFu) | APX_PACK_NONE, 2, 0.0, 0, 0, r_out, nullptr,
+               nullptr, (cudaStream_t)stream);
+}
+
+int apx_sync(apx_ctx* ctx, void* stream) {
+    if (!ctx) return APX_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    unsigned h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->flags.p, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess && h) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return (h & 1u) ? APX_ERR_NONFINITE : APX_OK;
+}
+
+int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, int32_t N, int32_t W_block,
+                  uint32_t mode, double snr_target_db, int32_t S_q, int32_t K_q, float* r_h, void* stream) {
+    if (!ctx || !s_h || !k_h || !r_h || L < 1 || N < 1) return APX_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    int rc = ensure(ctx, ctx->hs, sizeof(float) * (size_t)L);
+    if (!rc) rc = ensure(ctx, ctx->hk, sizeof(float) * (size_t)N);
+    if (!rc) rc = ensure(ctx, ctx->hr, sizeof(float) * (size_t)(L + N - 1));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->hs.p, s_h, sizeof(float) * (size_t)L, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hk.p, k_h, sizeof(float) * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint32_t pack = mode & 0xF00u;
+    if (S_q > 0 && K_q > 0 && pack != APX_PACK_AUTO && pack != APX_PACK_NONE)
+        rc = apx_conv_fixed(ctx, (const float*)ctx->hs.p, L, (const float*)ctx->hk.p, N, W_block, mode, S_q, K_q,
+                            (float*)ctx->hr.p, nullptr, nullptr, stream);
+    else
+        rc = apx_conv(ctx, (const float*)ctx->hs.p, L, (const float*)ctx->hk.p, N, W_block, mode, snr_target_db,
+                      (float*)ctx->hr.p, nullptr, nullptr, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(r_h, ctx->hr.p, sizeof(float) * (size_t)(L + N - 1), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return apx_sync(ctx, stream);
+}
+
+int64_t apx_launch_count(const apx_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* apx_strerror(int s) {
+    switch (s) {
+        case APX_OK: return "ok";
+        case APX_ERR_ARG: return "invalid argument";
+        case APX_ERR_WBLOCK: return "invalid W_block for this kernel length and core";
+        case APX_ERR_RANGE: return "companding range exceeds the packing's exactness bound";
+        case APX_ERR_NONFINITE: return "non-finite input or kernel";
+        case APX_ERR_OOM: return "device memory allocation failed";
+        case APX_ERR_BUDGET: return "workspace budget exceeded";
+        case APX_ERR_CUDA: return "CUDA runtime error";
+        case APX_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

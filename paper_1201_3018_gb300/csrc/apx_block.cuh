@@ -1,0 +1,147 @@
+// apx_block.cuh -- per-block prologue and epilogue shared by the direct and
+// FFT cores: window load, block statistics (a3), the Section IV.D selector
+// (a4), integer digit extraction (Eqs. 11-15 and the asymmetric "successive
+// iterations"), inverse companding (Eq. 16) and output placement (Eq. 17).
+#pragma once
+
+#include "apx_internal.cuh"
+
+namespace apx {
+
+struct BlockGeom {
+    long long start;  // input index of window element 0
+    int lo, hi;       // local outputs kept: [lo, hi)
+    int wstart;       // W_start of Eq. (10)
+};
+
+// Section III / Eq. (17): block origin and kept outputs.  Direct core: block 0
+// starts at 0 and keeps [0, W+N'-1); block w >= 1 starts at wW-2 and keeps
+// [N'+1, W_block).  FFT core: `head` leading blocks, all of the second kind.
+__device__ __forceinline__ BlockGeom block_geom(const Params& p, long long i) {
+    BlockGeom g;
+    if (p.fft) {
+        g.start = (i - p.head) * (long long)p.W - 2;
+        g.lo = p.Nodd + 1; g.hi = p.Wb; g.wstart = (p.Nodd - 1) / 2;
+    } else if (i == 0) {
+        g.start = 0; g.lo = 0; g.hi = p.Wb - 2; g.wstart = 0;
+    } else {
+        g.start = i * (long long)p.W - 2;
+        g.lo = p.Nodd + 1; g.hi = p.Wb; g.wstart = (p.Nodd - 1) / 2;
+    }
+    return g;
+}
+
+// Coalesced window load, zeros outside [0, L).
+__device__ __forceinline__ void load_window(const Params& p, const BlockGeom& g, float* xs) {
+    const float* __restrict__ s = p.s;
+    for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) {
+        long long gi = g.start + t;
+        xs[t] = (gi >= 0 && gi < p.L) ? __ldg(&s[gi]) : 0.f;
+    }
+    __syncthreads();
+}
+
+struct Shared {
+    float redf[32];
+    int redi[32];
+    long long redl[32];
+};
+
+// Fill every kept output of the block with `v` (zero block or non-finite).
+__device__ __forceinline__ void store_constant(const Params& p, const BlockGeom& g, float v) {
+    for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
+        long long o = g.start + j;
+        if (o < 0 || o >= p.out_len) continue;
+        p.r[o] = v;
+        if (p.rq) p.rq[o] = 0;
+    }
+}
+
+__device__ __forceinline__ void write_stats(const Params& p, long long i, int mode, const Cand* c, float cs,
+                                            float Ms, double sig2, double snr_db, double ferr) {
+    if (!p.st || threadIdx.x != 0) return;
+    apx_block_stats s;
+    s.mode = mode;
+    s.Sq = c ? c->S : 0;
+    s.Kq = c ? c->K : 0;
+    s.b = c ? c->b : 0;
+    s.cs = cs;
+    s.maxabs = Ms;
+    s.sigma2 = sig2;
+    s.snr_pred_db = snr_db;
+    s.fft_err = ferr;
+    p.st[i] = s;
+}
+
+// Prologue result.
+struct Pro {
+    int kind;     // 0 full / packed decided later, 2 zero, 3 non-finite
+    float Ms;
+    double sig2;
+};
+
+__device__ __forceinline__ Pro block_prologue(const Params& p, const float* xs, Shared& sh) {
+    Pro r;
+    r.Ms = block_maxabs(xs, p.Wb, sh.redf, sh.redi);
+    r.sig2 = 0.0;
+    const KInfo& ki = *p.ki;
+    if (!(r.Ms <= 3.402823466e38f) || ki.nonfinite) { r.kind = 3; return r; }  // NaN or inf
+    if (r.Ms == 0.f || ki.Mk == 0.f) { r.kind = 2; return r; }
+    r.sig2 = block_second_moment(xs, p.Wb, r.Ms, sh.redl);
+    r.kind = 0;
+    return r;
+}
+
+__device__ __forceinline__ void handle_trivial(const Params& p, long long i, const BlockGeom& g, const Pro& pr) {
+    if (pr.kind == 3) {
+        store_constant(p, g, __int_as_float(0x7fc00000));
+        if (threadIdx.x == 0) atomicOr(p.status, 1u);
+        write_stats(p, i, APX_BLK_NONFINITE, nullptr, 0.f, pr.Ms, 0.0, __longlong_as_double(0x7ff8000000000000ll), 0.0);
+    } else {
+        store_constant(p, g, 0.f);
+        write_stats(p, i, APX_BLK_ZERO, nullptr, 0.f, pr.Ms, 0.0, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+    }
+}
+
+// ------------------------------------------------------------------ digit extraction
+// Finest-digit scaled packed output T = rbar * 2^sc as an integer.  Exact for
+// the direct core; nearest for the FFT core (error bound below 1/4 digit).
+__device__ __forceinline__ long long scaled(double rbar, int sc) { return __double2ll_rn(ldexp(rbar, sc)); }
+
+// Eqs. (11)-(15) for output j of a symmetric-packed block, on u scaled by 2^b:
+//   U = T + R_max (2^2b + 2^b + 1)                     (11)
+//   side_eps^-1 = U >> 2b                                 (13)
+//   side_eps    = R_max (m = W_start) or U[m-1] mod 2^b   (12)
+//   r~[2m]   = side_eps^-1 + side_eps - 2 R_max          (14)
+//   r~[2m+1] = (U >> b) - 2^b side_eps^-1 - R_max         (15)
+template <typename F>
+__device__ __forceinline__ long long unpack_sym(const Cand& c, int j, int wstart, F Tat) {
+    const int m = j >> 1;
+    const long long one = 1;
+    const long long Rs = c.Rmax * ((one << (2 * c.b)) + (one << c.b) + 1);
+    const long long U = Tat(m) + Rs;
+    const long long sinv = U >> (2 * c.b);
+    if (j & 1) return (U >> c.b) - (sinv << c.b) - c.Rmax;
+    const long long se = (m == wstart) ? c.Rmax : ((Tat(m - 1) + Rs) & ((one << c.b) - 1));
+    return sinv + se - 2 * c.Rmax;
+}
+
+// Asymmetric unpacking: digit q of T[i] offset by R_max, overlap-added over the
+// M segments: r~[j] = sum_q c_q[j - q Ls], with packed outputs i < nr.
+template <typename F>
+__device__ __forceinline__ long long unpack_asym(const Cand& c, int j, int Ls, int nr, F Tat) {
+    const long long one = 1;
+    const long long mask = (one << c.b) - 1;
+    long long off = 0;
+    for (int q = 0; q < c.M; ++q) off += c.Rmax << (c.b * q);
+    long long acc = 0;
+    for (int q = 0; q < c.M; ++q) {
+        const int i = j - q * Ls;
+        if (i < 0 || i >= nr) continue;
+        const long long U = Tat(i) + off;
+        acc += ((U >> (c.b * (c.M - 1 - q))) & mask) - c.Rmax;
+    }
+    return acc;
+}
+
+}  // namespace apx

@@ -1,0 +1,189 @@
+// apx_direct.cu -- fused per-block kernel of the time-domain (direct) core.
+//
+// One CTA per overlap-save block: load the W_block window, block statistics,
+// Section IV.D selection, companding (Eq. 2), packing (Eqs. 4 / 7) into shared
+// memory, the packed FP64 convolution (Eqs. 8-9) with a register sliding
+// window, digit extraction (Eqs. 11-15), inverse companding (Eq. 16) and the
+// Eq. (17) store.  Blocks without an admissible packing run the FP32 full
+// precision convolution in the same CTA.
+#include "apx_block.cuh"
+#include "apx_launch.h"
+
+namespace apx {
+
+constexpr int kRf = 8;  // FP32 outputs per thread (taps padded to a multiple of 8)
+constexpr int kRd = 4;  // FP64 outputs per thread (taps padded to a multiple of 4)
+
+// acc[r] = sum_{n < nkp} sig[j0 + r - n] taps[n]; sig is zero-padded by >= nkp
+// in front.  Register ring: slot (t mod R) holds sig[j0 + t - n].
+template <int R>
+__device__ __forceinline__ void conv_f32(const float* sig, const float* __restrict__ taps, int nkp, int j0,
+                                         float (&acc)[R]) {
+    float w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc[r] = 0.f; w[r] = sig[j0 + r]; }
+    for (int n = 0; n < nkp; n += R) {
+        float t[R];
+#pragma unroll
+        for (int v = 0; v < R; v += 4) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(taps + n + v));
+            t[v] = q.x; t[v + 1] = q.y; t[v + 2] = q.z; t[v + 3] = q.w;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fmaf(w[(r - u + R) % R], t[u], acc[r]);
+            w[R - 1 - u] = sig[j0 - n - u - 1];
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void conv_f64(const double* sig, const double* __restrict__ taps, int nkp, int j0,
+                                         double (&acc)[R]) {
+    double w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc[r] = 0.0; w[r] = sig[j0 + r]; }
+    for (int n = 0; n < nkp; n += R) {
+        double t[R];
+#pragma unroll
+        for (int v = 0; v < R; v += 2) {
+            double2 q = __ldg(reinterpret_cast<const double2*>(taps + n + v));
+            t[v] = q.x; t[v + 1] = q.y;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(w[(r - u + R) % R], t[u], acc[r]);
+            w[R - 1 - u] = sig[j0 - n - u - 1];
+        }
+    }
+}
+
+__device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+__global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    const long long i = blockIdx.x;
+    const BlockGeom g = block_geom(p, i);
+    const DirectLayout& dl = p.dl;
+
+    float* xs = reinterpret_cast<float*>(smem) + dl.padF;
+    for (int t = threadIdx.x; t < dl.padF; t += blockDim.x) xs[t - dl.padF] = 0.f;
+    for (int t = threadIdx.x; t < kRf; t += blockDim.x) xs[p.Wb + t] = 0.f;
+    load_window(p, g, xs);
+
+    const Pro pr = block_prologue(p, xs, sh);
+    if (pr.kind != 0) { handle_trivial(p, i, g, pr); return; }
+
+    // Section IV.D: first candidate (in the Table 1 order) whose model SNR meets
+    // the target; with a fixed quantiser the single candidate is taken.
+    const KInfo& ki = *p.ki;
+    int ci = -1;
+    for (int c = 0; c < p.ncand; ++c) {
+        if (!p.autosel || snr_feasible(pr.sig2, pr.Ms, ki.sig2k, ki.Mk, p.cand[c].S, p.cand[c].K, p.thr)) {
+            ci = c;
+            break;
+        }
+    }
+
+    if (ci < 0) {
+        // Full precision (FP32), Eq. (1) over the window.
+        const int nkp = round_up(p.Nodd, kRf);
+        const int nout = g.hi - g.lo;
+        for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
+            const int j0 = g.lo + ch * kRf;
+            float acc[kRf];
+            conv_f32<kRf>(xs, p.kfull, nkp, j0, acc);
+#pragma unroll
+            for (int r = 0; r < kRf; ++r) {
+                const int j = j0 + r;
+                const long long o = g.start + j;
+                if (j < g.hi && o >= 0 && o < p.out_len) {
+                    p.r[o] = acc[r];
+                    if (p.rq) p.rq[o] = 0;
+                }
+            }
+        }
+        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        return;
+    }
+
+    const Cand& c = p.cand[ci];
+    const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
+    const double eps = ldexp(1.0, -c.b);
+    double* sb = reinterpret_cast<double*>(smem + dl.offS) + dl.padS;
+    double* tb = reinterpret_cast<double*>(smem + dl.offT);
+    const int nkp = round_up(c.nk, kRd);
+    int nsb, Ls = 0;
+    if (c.blk == APX_BLK_SYM) {
+        nsb = p.Wb / 2;
+        for (int m = threadIdx.x; m < nsb; m += blockDim.x) {          // Eq. (4)
+            const double e = (double)compand(cs, xs[2 * m]);
+            const double o = (double)compand(cs, xs[2 * m + 1]);
+            sb[m] = __dadd_rn(e, __dmul_rn(eps, o));
+        }
+    } else {
+        Ls = (p.Wb + c.M - 1) / c.M;
+        nsb = Ls;
+        for (int m = threadIdx.x; m < Ls; m += blockDim.x) {            // Eq. (7)
+            double acc = 0.0, ep = 1.0;
+            for (int q = 0; q < c.M; ++q) {
+                const int t = m + q * Ls;
+                if (t < p.Wb) acc = __dadd_rn(acc, __dmul_rn(ep, (double)compand(cs, xs[t])));
+                ep = __dmul_rn(ep, eps);
+            }
+            sb[m] = acc;
+        }
+    }
+    for (int t = threadIdx.x; t < dl.padS; t += blockDim.x) sb[t - dl.padS] = 0.0;
+    for (int t = nsb + threadIdx.x; t < dl.nS - dl.padS; t += blockDim.x) sb[t] = 0.0;
+    __syncthreads();
+
+    // Packed FP64 block convolution (Eq. 9 / Eq. 8): exact by the c5 bound.
+    int olo, ohi, nr = 0;
+    if (c.blk == APX_BLK_SYM) {
+        olo = g.wstart; ohi = g.hi / 2;
+    } else {
+        nr = Ls + p.Nodd - 1;
+        olo = max(0, g.lo - (c.M - 1) * Ls);
+        ohi = min(g.hi, nr);
+    }
+    for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
+        const int j0 = olo + ch * kRd;
+        double acc[kRd];
+        conv_f64<kRd>(sb, c.kbar, nkp, j0, acc);
+#pragma unroll
+        for (int r = 0; r < kRd; ++r)
+            if (j0 + r < ohi) tb[j0 + r] = acc[r];
+    }
+    __syncthreads();
+
+    // Unpack, inverse compand (Eq. 16), place (Eq. 17).
+    const float inv = (float)(1.0 / ((double)cs * (double)ki.ck[ci]));
+    auto Tat = [&](int m) { return scaled(tb[m], c.sc); };
+    for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
+        const long long o = g.start + j;
+        if (o < 0 || o >= p.out_len) continue;
+        long long rt = c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat) : unpack_asym(c, j, Ls, nr, Tat);
+        p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
+        if (p.rq) p.rq[o] = (int)rt;
+    }
+    if (threadIdx.x == 0)
+        write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ki.sig2k, ki.Mk, c.S, c.K), 0.0);
+}
+
+cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (p.P <= 0) return cudaSuccess;
+    k_direct<<<(unsigned)p.P, kDirectThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace apx

@@ -1,0 +1,345 @@
+// apx_internal.cuh -- device-side building blocks of libapx (sm_103a).
+//
+// Block statistics, the per-block selector arithmetic, companding, packing,
+// digit extraction and an in-shared-memory radix-8/4/2 Stockham FFT.  Every
+// floating-point decision that selects an integer (a quantised code, a mode)
+// is taken with one IEEE operation at a time (__fmul_rn, __dmul_rn, ...) so
+// that it does not depend on contraction or summation order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/apx.h"
+
+namespace apx {
+
+constexpr int kMaxWblock = 16384;
+constexpr int kMaxCand = 3;
+
+// One packing candidate.  Static part set by the host from (N', W_block);
+// dynamic part (c_k, ||kbar||_1) written by the kernel-preparation launch.
+struct Cand {
+    int blk;          // APX_BLK_SYM / ASYM2 / ASYM3
+    int M;            // 1 for symmetric, 2 or 3 for asymmetric
+    int S, K, b;      // companding ranges and eps = 2^-b
+    int sc;           // exponent of the finest digit: b (sym, asym2) or 2b (asym3)
+    long long Rmax;   // N' S K (Eq. 3)
+    int nk;           // packed taps: (N'+1)/2 (sym) or N' (asym)
+    int log2n;        // FFT core: log2 of the real transform length
+    double fftc;      // FFT core: (3 phi + 16 u) for log2n (error-bound constant)
+    const double* kbar;   // packed taps in the workspace
+    const double2* H;     // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries
+};
+
+// Kernel statistics written by the preparation launch.
+struct KInfo {
+    float Mk;         // ||k||_inf
+    int nonfinite;    // kernel has NaN/Inf
+    double sig2k;     // second moment of the kernel (24-bit fixed point)
+    float ck[kMaxCand];
+    float pad_;
+    double l1[kMaxCand];  // ||kbar||_1, exact integer
+};
+
+// Shared-memory layout of the direct kernel (byte offsets; element pads).
+struct DirectLayout {
+    int padF;         // zero floats in front of the window
+    int offS, padS;   // packed-signal buffer: byte offset, zero doubles in front
+    int nS;           // packed-signal buffer length in doubles (pads included)
+    int offT;         // packed-output buffer: byte offset
+};
+
+// Per-block decision of the FFT core's selection pass.
+struct Sel {
+    int ci;           // candidate index, -1: full precision, -2 zero block, -3 non-finite
+    float cs;         // c_s of the chosen candidate
+    float Ms;         // ||s||_inf of the window
+    int pad_;
+    double sig2;      // second moment of the window
+    double ferr;      // FFT error bound in digits of the chosen candidate
+};
+
+struct Params {
+    const float* s;       // input, L samples
+    long long L;
+    int N, Nodd, Wb, W, head, fft;
+    long long P, out_len;
+    float* r;             // output, out_len
+    int* rq;              // integer-domain output or null
+    apx_block_stats* st;  // per-block stats or null
+    const float* kfull;   // FP32 taps (reversed for xcorr), N' entries
+    const float2* Hfull;  // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
+    const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
+    const float2* tw32;
+    const KInfo* ki;
+    unsigned* status;     // bit 0: non-finite input seen
+    int autosel;          // 1: per-block selection under thr
+    int ncand;
+    double thr;           // 10^(target/10)
+    Cand cand[kMaxCand];
+    DirectLayout dl;      // direct core
+    Sel* sel;             // FFT core: per-block decisions (P entries)
+    unsigned* used;       // FFT core: bit c set when candidate c is used, bit 3 for full precision
+};
+
+// ------------------------------------------------------------------ reductions
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide reduction; `red` is shared scratch of >= 32 elements of T.
+template <typename T, bool IS_MAX>
+__device__ T block_reduce(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = IS_MAX ? warp_max(v) : warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < nw ? red[lane] : (IS_MAX ? red[0] : T(0));
+        t = IS_MAX ? warp_max(t) : warp_sum(t);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    T out = red[0];
+    __syncthreads();
+    return out;
+}
+
+// ||x||_inf over n samples in shared memory; returns NaN if any sample is NaN
+// and +inf if any is infinite.
+__device__ inline float block_maxabs(const float* x, int n, float* redf, int* redi) {
+    float m = 0.f;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float a = fabsf(x[i]);
+        if (a != a) bad = 1;
+        m = fmaxf(m, a);
+    }
+    m = block_reduce<float, true>(m, redf);
+    bad = block_reduce<int, true>(bad, redi);
+    return bad ? __int_as_float(0x7fc00000) : m;
+}
+
+// Second moment in 24-bit fixed point relative to ||x||_inf (exact integer sum).
+__device__ inline double block_second_moment(const float* x, int n, float maxabs, long long* redl) {
+    int e;
+    (void)frexpf(maxabs, &e);
+    const int sh = 24 - e;
+    long long acc = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        long long q = __float2ll_rz(ldexpf(x[i], sh));
+        acc += q * q;
+    }
+    acc = block_reduce<long long, false>(acc, redl);
+    return __ddiv_rn(ldexp(__ll2double_rn(acc), -2 * sh), (double)n);
+}
+
+// Table 1 model (derived from Eqs. 18-19), one IEEE operation at a time:
+//   144 s2s s2k S^2 K^2 >= thr (12 (s2s S^2 Mk^2 + s2k K^2 Ms^2) + Ms^2 Mk^2)
+__device__ inline bool snr_feasible(double s2s, float Ms, double s2k, float Mk, int S, int K, double thr) {
+    double S2 = __dmul_rn((double)S, (double)S), K2 = __dmul_rn((double)K, (double)K);
+    double Ms2 = __dmul_rn((double)Ms, (double)Ms), Mk2 = __dmul_rn((double)Mk, (double)Mk);
+    double num = __dmul_rn(__dmul_rn(144.0, __dmul_rn(s2s, s2k)), __dmul_rn(S2, K2));
+    double a = __dmul_rn(__dmul_rn(s2s, S2), Mk2);
+    double c = __dmul_rn(__dmul_rn(s2k, K2), Ms2);
+    double den = __dadd_rn(__dmul_rn(12.0, __dadd_rn(a, c)), __dmul_rn(Ms2, Mk2));
+    return num >= __dmul_rn(thr, den);
+}
+
+__device__ inline double snr_model_db(double s2s, float Ms, double s2k, float Mk, int S, int K) {
+    double S2 = (double)S * S, K2 = (double)K * K, Ms2 = (double)Ms * Ms, Mk2 = (double)Mk * Mk;
+    double num = 144.0 * (s2s * s2k) * (S2 * K2);
+    double den = 12.0 * (s2s * S2 * Mk2 + s2k * K2 * Ms2) + Ms2 * Mk2;
+    return 10.0 * log10(num / den);
+}
+
+// Eq. (2): c = Q / ||x||_inf (correctly rounded FP32) and x~ = rint(c x).
+__device__ __forceinline__ float compand_factor(int Q, float m) { return __fdiv_rn((float)Q, m); }
+__device__ __forceinline__ int compand(float c, float x) { return __float2int_rn(__fmul_rn(c, x)); }
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R> struct cpx;
+template <> struct cpx<float> { using T = float2; };
+template <> struct cpx<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// multiply by -i (forward) or +i (inverse): exact
+template <typename C, bool INV> __device__ __forceinline__ C mul_mi(C a) {
+    C r;
+    if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+template <typename C, bool INV> __device__ __forceinline__ C mul_w8(C a) {  // exp(-+ i pi/4)
+    using R = decltype(a.x);
+    const R h = (R)0.70710678118654752440;
+    C r;
+    if (INV) { r.x = (a.x - a.y) * h; r.y = (a.x + a.y) * h; }
+    else     { r.x = (a.x + a.y) * h; r.y = (a.y - a.x) * h; }
+    return r;
+}
+template <typename C, bool INV> __device__ __forceinline__ C mul_w83(C a) {  // exp(-+ 3 i pi/4)
+    using R = decltype(a.x);
+    const R h = (R)0.70710678118654752440;
+    C r;
+    if (INV) { r.x = (-a.x - a.y) * h; r.y = (a.x - a.y) * h; }
+    else     { r.x = (a.y - a.x) * h; r.y = (-a.x - a.y) * h; }
+    return r;
+}
+
+// In-register DFTs (natural order in, natural order out), built from radix-2
+// butterflies so the standard radix-2 error analysis applies.
+template <typename C, bool INV> __device__ __forceinline__ void dft2(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+}
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C* v) {
+    C e0 = cadd(v[0], v[2]), e1 = csub(v[0], v[2]);
+    C o0 = cadd(v[1], v[3]), o1 = mul_mi<C, INV>(csub(v[1], v[3]));
+    v[0] = cadd(e0, o0); v[2] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[3] = csub(e1, o1);
+}
+template <typename C, bool INV> __device__ __forceinline__ void dft8(C* v) {
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<C, INV>(e);
+    dft4<C, INV>(o);
+    o[1] = mul_w8<C, INV>(o[1]);
+    o[2] = mul_mi<C, INV>(o[2]);
+    o[3] = mul_w83<C, INV>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { v[k] = cadd(e[k], o[k]); v[k + 4] = csub(e[k], o[k]); }
+}
+template <int RAD, typename C, bool INV> __device__ __forceinline__ void dft_small(C* v) {
+    if constexpr (RAD == 8) dft8<C, INV>(v);
+    else if constexpr (RAD == 4) dft4<C, INV>(v);
+    else dft2<C, INV>(v);
+}
+
+// One Stockham autosort pass of a length-m complex FFT held in shared memory.
+// Ns is the size of the sub-transforms already done.  Twiddles come from a
+// table of exp(-2 pi i t / ntab) with ntab a multiple of m (stride ntab/m).
+template <typename C, int RAD, bool INV, int MAXB>
+__device__ void fft_pass(C* data, int m, int Ns, const C* __restrict__ tw, int tws) {
+    const int nb = m / RAD;
+    C v[MAXB][RAD];
+    int jj[MAXB];
+    const int span = Ns * RAD;
+    const int tstep = (m / span) * tws;
+#pragma unroll
+    for (int bi = 0; bi < MAXB; ++bi) {
+        int j = threadIdx.x + bi * blockDim.x;
+        jj[bi] = j;
+        if (j < nb) {
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) {
+                C a = data[j + r * nb];
+                if (r > 0 && Ns > 1) {
+                    C w = __ldg(&tw[r * k * tstep]);
+                    if (INV) w.y = -w.y;
+                    a = cmul(a, w);
+                }
+                v[bi][r] = a;
+            }
+            dft_small<RAD, C, INV>(v[bi]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int bi = 0; bi < MAXB; ++bi) {
+        const int j = jj[bi];
+        if (j < nb) {
+            const int k = j & (Ns - 1);
+            const int o = (j - k) * RAD + k;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) data[o + r * Ns] = v[bi][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Length-m (power of two, 2..8192) complex FFT in shared memory, unnormalised.
+// Radix-8 passes, then one radix-4 or radix-2 pass for the remainder.
+template <typename C, bool INV, int MAXB>
+__device__ void fft_smem(C* data, int m, const C* __restrict__ tw, int tws) {
+    int Ns = 1;
+    while (Ns * 8 <= m) { fft_pass<C, 8, INV, MAXB>(data, m, Ns, tw, tws); Ns *= 8; }
+    if (Ns * 4 == m) fft_pass<C, 4, INV, MAXB * 2>(data, m, Ns, tw, tws);
+    else if (Ns * 2 == m) fft_pass<C, 2, INV, MAXB * 4>(data, m, Ns, tw, tws);
+}
+
+// Real-signal spectral step shared by the block convolution and the kernel
+// preparation.  Z holds FFT_m of z[j] = x[2j] + i x[2j+1] (n = 2m real
+// samples).  With W = exp(-2 pi i / n):
+//   X2[k] = (Z[k] + conj Z[m-k]) - i W^k (Z[k] - conj Z[m-k]) = 2 X[k].
+template <typename C>
+__device__ __forceinline__ void real_post(C a, C b, C w, C& Xk, C& Xmk) {
+    // a = Z[k], b = Z[m-k], w = W^k;  W^(m-k) = -conj(w)
+    C cb = cconj(b), ca = cconj(a);
+    C d1 = csub(a, cb), d2 = csub(b, ca);
+    Xk = cadd(cadd(a, cb), mul_mi<C, false>(cmul(w, d1)));
+    C wm = w; wm.x = -w.x;  // -conj(w)
+    Xmk = cadd(cadd(b, ca), mul_mi<C, false>(cmul(wm, d2)));
+}
+// Inverse: from Y2 (spectrum of the real result, times 2) build
+//   Z'[k] = (Y[k] + conj Y[m-k]) + i conj(W^k) (Y[k] - conj Y[m-k])
+template <typename C>
+__device__ __forceinline__ void real_pre(C yk, C ymk, C w, C& Zk, C& Zmk) {
+    C cym = cconj(ymk), cyk = cconj(yk);
+    C wc = cconj(w);
+    C wmc; wmc.x = -w.x; wmc.y = -w.y;  // conj(W^(m-k)) = conj(-conj(w)) = -w
+    Zk = cadd(cadd(yk, cym), mul_mi<C, true>(cmul(wc, csub(yk, cym))));
+    Zmk = cadd(cadd(ymk, cyk), mul_mi<C, true>(cmul(wmc, csub(ymk, cyk))));
+}
+
+// Z (length m, FFT of the packed real block) -> Z' ready for the inverse FFT,
+// multiplying by the kernel spectrum H = FFT_n(k) / (4m) (m+1 entries).  The
+// factor 2 of X2, the missing 1/2 of the inverse step and the 1/m of the
+// inverse FFT all fold into that power-of-two scale, which is exact.
+template <typename C>
+__device__ void spectral_multiply(C* Z, int m, const C* __restrict__ H, const C* __restrict__ tw, int twn) {
+    // twn: table index stride for W_n^k (ntab / n)
+    for (int k = threadIdx.x; k <= m / 2; k += blockDim.x) {
+        if (k == 0) {
+            C z0 = Z[0];
+            C X0, Xm;
+            X0.x = 2 * (z0.x + z0.y); X0.y = 0;
+            Xm.x = 2 * (z0.x - z0.y); Xm.y = 0;
+            C Y0 = cmul(X0, H[0]), Ym = cmul(Xm, H[m]);
+            C cym = cconj(Ym);
+            Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
+        } else {
+            C a = Z[k], b = Z[m - k];
+            C w = __ldg(&tw[k * twn]);
+            C Xk, Xmk;
+            real_post(a, b, w, Xk, Xmk);
+            C Yk = cmul(Xk, H[k]);
+            C Ymk = cmul(Xmk, H[m - k]);
+            C Zk, Zmk;
+            real_pre(Yk, Ymk, w, Zk, Zmk);
+            Z[k] = Zk;
+            if (k != m - k) Z[m - k] = Zmk;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace apx

@@ -1,0 +1,82 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every
+function include/apx.h declares, and its host-only planner agrees with the
+oracle's block geometry.  No compute call runs here (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libapx():
+    from paper_1201_3018_gb300 import build as b
+    b.build()
+    from paper_1201_3018_gb300 import apx
+    return apx
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(apx_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(libapx):
+    L = C.CDLL(libapx.LIB_PATH)
+    declared = _declared()
+    assert "apx_conv" in declared and "apx_conv_full" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(declared) == set(libapx.SIGNATURES), "binding and header disagree"
+
+
+def test_strerror(libapx):
+    for code in range(0, -9, -1):
+        msg = libapx.strerror(code)
+        assert msg and msg != "unknown status"
+    assert libapx.strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("fft", [False, True])
+@pytest.mark.parametrize("L,N,Wb", [(1, 1, 4), (100, 7, 32), (1000, 64, 256), (513, 8, 64), (10, 29, 32),
+                                    (65536, 64, 1024), (1 << 20, 4096, 8192), (999, 1, 8)])
+def test_plan_matches_oracle(libapx, fft, L, N, Wb):
+    mode = libapx.CORE_FFT if fft else libapx.CORE_DIRECT
+    P, W = libapx.plan_blocks(L, N, Wb, mode)
+    p = O.plan(L, N, Wb, fft)
+    assert (P, W) == (p.P, p.W)
+
+
+def test_plan_errors(libapx):
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_blocks(100, 3, 31, 0)
+    assert e.value.status == libapx.APX_ERR_WBLOCK
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_blocks(100, 3, 24, libapx.CORE_FFT)
+    assert e.value.status == libapx.APX_ERR_WBLOCK
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_blocks(0, 3, 16, 0)
+    assert e.value.status == libapx.APX_ERR_ARG
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_blocks(100, 3, 16, 0x7000)
+    assert e.value.status == libapx.APX_ERR_ARG
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_blocks(100, 3, 32768, 0)
+    assert e.value.status == libapx.APX_ERR_WBLOCK
+
+
+def test_null_arguments_rejected_without_gpu(libapx):
+    L = libapx.lib()
+    assert L.apx_conv(None, None, 10, None, 3, 16, 0, 30.0, None, None, None, None) == libapx.APX_ERR_ARG
+    assert L.apx_sync(None, None) == libapx.APX_ERR_ARG
+    assert L.apx_create(None, 0, 0) == libapx.APX_ERR_ARG

@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer-domain outputs of packed blocks must match bit for bit; the per-block
+decisions (mode, S_q, K_q, b, c_s, statistics, FFT error bound) must match
+exactly; dequantised outputs within 1e-6 relative (FP32 inverse companding);
+full-precision outputs within 1e-5 relative L2 of the FP64 definition."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1201_3018_gb300 import apx
+from paper_1201_3018_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+PACKED = (apx.BLK_SYM, apx.BLK_ASYM2, apx.BLK_ASYM3)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = apx.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_both(ctx, s, k, Wb, mode, snr=None, Sq=None, Kq=None, want=None):
+    r, rq, st = ctx.conv(dev(s), dev(k), Wb, mode, snr_db=snr, Sq=Sq, Kq=Kq, want_int=True, want_stats=True)
+    ctx.apx_sync()
+    ro, rqo, sto, rc = O.apx_conv(s, k, Wb, mode, snr_db=snr or 0.0, Sq=Sq or 0, Kq=Kq or 0, nthreads=0,
+                                  want=want)
+    assert rc == 0
+    return r.cpu().numpy(), rq.cpu().numpy().astype(np.int64), st, ro, rqo, O.stats_arrays(sto)
+
+
+def check(r, rq, st, ro, rqo, so, s, k, mode, Wb, want=None):
+    # per-block decisions
+    np.testing.assert_array_equal(st["mode"], so["mode"])
+    for f in ("Sq", "Kq", "b"):
+        np.testing.assert_array_equal(st[f], so[f])
+    np.testing.assert_array_equal(st["cs"].view(np.uint32), so["cs"].astype(np.float32).view(np.uint32))
+    np.testing.assert_array_equal(st["maxabs"].view(np.uint32), so["maxabs"].astype(np.float32).view(np.uint32))
+    live = (st["mode"] != apx.BLK_ZERO) & (st["mode"] != apx.BLK_NONFINITE)
+    np.testing.assert_array_equal(st["sigma2"][live], so["sigma2"][live])
+    np.testing.assert_array_equal(st["fft_err"], so["fft_err"])
+    # integer domain: exact everywhere (zero outside packed blocks)
+    np.testing.assert_array_equal(rq, rqo)
+    # outputs by block kind
+    xcorr = (mode & 0xF) == apx.OP_XCORR
+    fft = (mode & 0xF0) == apx.CORE_FFT
+    p = O.plan(len(s), len(k), Wb, fft)
+    packed_mask = np.zeros(len(r), bool)
+    full_mask = np.zeros(len(r), bool)
+    for i in range(p.P):
+        st0 = O.block_start(p, i)
+        lo, hi = O.block_out_range(p, i)
+        g = np.arange(st0 + lo, st0 + hi)
+        g = g[(g >= 0) & (g < len(r))]
+        if st["mode"][i] in PACKED:
+            packed_mask[g] = True
+        elif st["mode"][i] == apx.BLK_FULL:
+            full_mask[g] = True
+    if want is not None:
+        full_mask &= want
+    np.testing.assert_allclose(r[packed_mask], ro[packed_mask], rtol=1e-6, atol=0)
+    if full_mask.any():
+        kk = k[::-1] if xcorr else k
+        idx = np.nonzero(full_mask)[0]
+        ref = O.conv_ref_at(s, kk, idx)
+        err = np.linalg.norm(r[idx] - ref) / max(np.linalg.norm(ref), 1e-300)
+        assert err <= 1e-5, err
+    return packed_mask, full_mask
+
+
+SHAPES = [(1000, 64, 256), (513, 8, 64), (5, 3, 16), (3000, 1, 64), (20000, 65, 1024), (40, 29, 32),
+          (40000, 257, 2048), (9000, 1024, 4096)]
+
+
+def q_for(blk, nodd, Q):
+    return max(1, min(Q, O.qmax_direct(blk, nodd)))
+
+
+@pytest.mark.parametrize("core", [apx.CORE_DIRECT, apx.CORE_FFT])
+@pytest.mark.parametrize("op", [apx.OP_CONV, apx.OP_XCORR])
+@pytest.mark.parametrize("L,N,Wb", SHAPES)
+def test_full_precision(ctx, core, op, L, N, Wb):
+    s = wl.random_signal(L + 1, L, "normal")
+    k = wl.random_signal(N + 2, N, "uniform")
+    mode = op | core | apx.PACK_NONE
+    check(*run_both(ctx, s, k, Wb, mode), s, k, mode, Wb)
+
+
+@pytest.mark.parametrize("core", [apx.CORE_DIRECT, apx.CORE_FFT])
+@pytest.mark.parametrize("pack,blk,Q", [(apx.PACK_SYM, apx.BLK_SYM, 6), (apx.PACK_ASYM2, apx.BLK_ASYM2, 150),
+                                        (apx.PACK_ASYM3, apx.BLK_ASYM3, 6), (apx.PACK_ASYM2, apx.BLK_ASYM2, 10)])
+@pytest.mark.parametrize("L,N,Wb", SHAPES)
+def test_fixed_packing(ctx, core, pack, blk, Q, L, N, Wb):
+    s = wl.random_signal(L + 3, L, "laplace", 0.1)
+    k = wl.random_signal(N + 4, N, "uniform")
+    nodd = N | 1
+    S = q_for(blk, nodd, Q)
+    mode = apx.OP_CONV | core | pack
+    r, rq, st, ro, rqo, so = run_both(ctx, s, k, Wb, mode, Sq=S, Kq=S)
+    pm, fm = check(r, rq, st, ro, rqo, so, s, k, mode, Wb)
+    if core == apx.CORE_DIRECT:
+        assert np.all((st["mode"] == blk) | (st["mode"] == apx.BLK_ZERO))
+
+
+@pytest.mark.parametrize("core", [apx.CORE_DIRECT, apx.CORE_FFT])
+@pytest.mark.parametrize("target", [12.0, 25.0, 35.0, 45.0, 60.0])
+@pytest.mark.parametrize("L,N,Wb,op", [(20000, 65, 1024, apx.OP_CONV), (40000, 257, 2048, apx.OP_XCORR),
+                                       (3000, 7, 64, apx.OP_XCORR), (60000, 64, 4096, apx.OP_CONV)])
+def test_auto_selection(ctx, core, target, L, N, Wb, op):
+    s = wl.random_signal(L + 5, L, "laplace", 0.1)
+    # vary the block statistics along the signal so that blocks choose differently
+    s = (s * np.linspace(0.2, 3.0, L) ** 2).astype(np.float32)
+    k = wl.random_signal(N + 6, N, "uniform")
+    mode = op | core | apx.PACK_AUTO
+    r, rq, st, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=target)
+    pm, fm = check(r, rq, st, ro, rqo, so, s, k, mode, Wb)
+    packed = np.isin(st["mode"], PACKED)
+    assert np.all(st["snr_pred_db"][packed] >= target)
+    if pm.any():
+        kk = k[::-1] if op == apx.OP_XCORR else k
+        idx = np.nonzero(pm)[0]
+        ref = O.conv_ref_at(s, kk, idx)
+        snr_gpu = 10 * math.log10(np.sum(ref ** 2) / np.sum((r[idx] - ref) ** 2))
+        snr_or = 10 * math.log10(np.sum(ref ** 2) / np.sum((ro[idx] - ref) ** 2))
+        assert abs(snr_gpu - snr_or) < 0.1
+        assert snr_gpu >= target - 1.0
+
+
+def test_zero_blocks_and_zero_kernel(ctx):
+    s = np.zeros(5000, np.float32)
+    s[3000:3100] = wl.random_signal(9, 100, "normal")
+    k = wl.random_signal(10, 33, "uniform")
+    for core in (apx.CORE_DIRECT, apx.CORE_FFT):
+        mode = core | apx.PACK_AUTO
+        check(*run_both(ctx, s, k, 256, mode, snr=30.0), s, k, mode, 256)
+        r, rq, st, ro, rqo, so = run_both(ctx, s, np.zeros(33, np.float32), 256, mode, snr=30.0)
+        assert np.all(r == 0) and np.all(st["mode"] == apx.BLK_ZERO)
+
+
+def test_nonfinite_input_reported(ctx):
+    s = wl.random_signal(11, 4000, "normal")
+    s[1234] = np.nan
+    k = wl.random_signal(12, 31, "uniform")
+    for core in (apx.CORE_DIRECT, apx.CORE_FFT):
+        mode = core | apx.PACK_AUTO
+        r, rq, st = ctx.conv(dev(s), dev(k), 256, mode, snr_db=30.0, want_int=True, want_stats=True)
+        with pytest.raises(apx.ApxError) as e:
+            ctx.apx_sync()
+        assert e.value.status == apx.APX_ERR_NONFINITE
+        ro, rqo, sto, rc = O.apx_conv(s, k, 256, mode, snr_db=30.0)
+        np.testing.assert_array_equal(np.isnan(r.cpu().numpy()), np.isnan(ro))
+        np.testing.assert_array_equal(st["mode"], O.stats_arrays(sto)["mode"])
+        ctx.apx_sync()  # cleared
+
+
+def test_error_codes(ctx):
+    s, k = dev(np.ones(100, np.float32)), dev(np.ones(65, np.float32))
+    r = torch.empty(164, device="cuda")
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv_fixed(s, k, 256, apx.PACK_SYM, 100, 100, r)
+    assert e.value.status == apx.APX_ERR_RANGE
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv(s, k, 255, 0, 30.0, r)
+    assert e.value.status == apx.APX_ERR_WBLOCK
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv(s, k, 96, 0, 30.0, r)  # W = 96 - 65 - 1 = 30 fine; FFT needs a power of two
+        ctx.apx_conv(s, k, 96, apx.CORE_FFT, 30.0, r)
+    assert e.value.status == apx.APX_ERR_WBLOCK
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv_fixed(s, k, 256, apx.PACK_ASYM2, 0, 5, r)
+    assert e.value.status == apx.APX_ERR_ARG
+
+
+def test_max_wblock(ctx):
+    s = wl.random_signal(13, 70000, "laplace", 0.1)
+    k = wl.random_signal(14, 8191, "uniform")
+    for core, mode_pack in ((apx.CORE_FFT, apx.PACK_AUTO), (apx.CORE_DIRECT, apx.PACK_NONE)):
+        mode = apx.OP_XCORR | core | mode_pack
+        want = np.zeros(len(s) + len(k) - 1, bool)
+        want[np.random.default_rng(0).choice(len(want), 3000, replace=False)] = True
+        check(*run_both(ctx, s, k, 16384, mode, snr=20.0, want=want), s, k, mode, 16384, want=want)
+
+
+def test_host_entry_point_matches_device_path(ctx):
+    case = wl.single_conv(L=30000)
+    sh = torch.from_numpy(case.s).pin_memory()
+    kh = torch.from_numpy(case.k).pin_memory()
+    out = torch.empty(len(case.s) + len(case.k) - 1).pin_memory()
+    ctx.apx_conv_host(sh, kh, case.Wblock, apx.PACK_ASYM2, Sq=191, Kq=191, r_host=out)
+    r, _, _ = ctx.conv(dev(case.s), dev(case.k), case.Wblock, apx.PACK_ASYM2, Sq=191, Kq=191)
+    np.testing.assert_array_equal(out.numpy(), r.cpu().numpy())
+
+
+def test_single_conv_full_size(ctx):
+    """65,536-sample N(0,1) input, 64-tap U[-1,1] kernel, W_block 1024, direct
+    core: full precision and the fixed ~45 dB quantiser (asym2, S_q=K_q=191)."""
+    case = wl.single_conv()
+    for mode, Q in ((apx.PACK_NONE, None), (apx.PACK_ASYM2, 191)):
+        r, rq, st, ro, rqo, so = run_both(ctx, case.s, case.k, case.Wblock, mode, Sq=Q, Kq=Q)
+        check(r, rq, st, ro, rqo, so, case.s, case.k, mode, case.Wblock)
+        if Q:
+            ref = O.conv_ref(case.s, case.k)
+            snr = 10 * math.log10(np.sum(ref ** 2) / np.sum((r - ref) ** 2))
+            assert 44.0 < snr < 47.0, snr
+
+
+def test_matching_xcorr_full_size(ctx):
+    """2^20-sample Laplacian signal, 4096-tap template, FFT core W_block 8192,
+    per-block selection at 45 dB: decisions exact, sampled outputs."""
+    case = wl.matching_xcorr()
+    mode = apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    want = np.zeros(len(case.s) + len(case.k) - 1, bool)
+    want[np.random.default_rng(1).choice(len(want), 4000, replace=False)] = True
+    for target in (45.0, 20.0):
+        r, rq, st, ro, rqo, so = run_both(ctx, case.s, case.k, case.Wblock, mode, snr=target, want=want)
+        check(r, rq, st, ro, rqo, so, case.s, case.k, mode, case.Wblock, want=want)
