@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the approximate overlap-save cross-correlation on GB300.
+
+Workload (one step): cross-correlate a 2^20-sample Laplacian(0, 0.1) signal with
+a 4096-tap template cut from it plus N(0, 0.01) noise, FFT core, W_block = 8192,
+per-block companding/packing selection at SNR >= 45 dB (Section IV.D), through
+the C ABI (apx_conv).  The full-precision twin (apx_conv_full) is timed beside
+it.  value = output samples per second of the selected path, whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Multi-GPU (torchrun, one process per GPU): independent replicas of the same
+workload (overlap-save blocks need no exchange), weak scaling, max over ranks.
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload (the paper's own code is not available; the oracle is the baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1201_3018_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "Gsamples/s packed vs full-precision conv at SNR≥45 dB; serving p50/p99 ms"
+UNIT = "Gsamples/s"
+TARGET_DB = 45.0
+SMS, FP32_LANES, FP64_PER_SM_CLK = 152, 128, 4.0   # FP64: 1.25 TFLOP/s nominal at 2.07 GHz
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._th = threading.Thread(target=self._read, daemon=True)
+        self._th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        parsed = []
+        for t, line in self.rows:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                parsed.append((t, float(f[2]), float(f[3]), f[6:10]))
+            except ValueError:
+                continue
+        inwin = [p for p in parsed if self.t0 and self.t1 and self.t0 - 0.15 <= p[0] <= self.t1 + 0.15]
+        use = inwin or parsed
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in use for i, v in enumerate(p[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([p[1] for p in use])), "sm_max_mhz": max(p[2] for p in use),
+                "reasons": reasons, "samples": len(use), "in_timed_window": bool(inwin)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1201_3018_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
+
+
+def fft_flops(n):
+    """Algorithmic FLOPs of one real block convolution through FFTs of length n:
+    forward and inverse real FFT (2.5 n log2 n each, the 5 m log2 m count of a
+    length-m complex FFT with m = n/2 plus its real-signal step) and the
+    pointwise complex product on n/2 + 1 bins (6 each)."""
+    return 5.0 * n * math.log2(n) + 3.0 * n
+
+
+def peaks():
+    pk = {"hbm_gbs": 6800.0, "source": "fallback"}
+    if os.path.exists(PEAKS_FILE):
+        try:
+            pk = dict(json.load(open(PEAKS_FILE)))
+            pk["source"] = "measured"
+        except (OSError, ValueError):
+            pass
+    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    pk["fp32_tflops"] = SMS * FP32_LANES * 2 * clk / 1e12
+    pk["fp64_tflops"] = SMS * FP64_PER_SM_CLK * clk / 1e12
+    return pk
+
+
+def time_steps(step, K, flush, stream):
+    """K steps, each bracketed by CUDA events on `stream`, L2 flushed between."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.fill_(float(i & 7))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    case = wl.matching_xcorr(snr_db=TARGET_DB)
+    Ls = 1 << 16
+    s = case.s[:Ls]
+    mode = O.OP_XCORR | O.CORE_FFT | O.PACK_AUTO
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        O.apx_conv(s, case.k, case.Wblock, mode, snr_db=TARGET_DB, nthreads=cores, want_int=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apx_conv(s, case.k, case.Wblock, mode, snr_db=TARGET_DB, nthreads=cores, want_int=False)
+    dt = (time.perf_counter() - t0) / args.steps
+    out = Ls + len(case.k) - 1
+    v = out / dt / 1e9
+    sample = "first %d samples of the 2^20-sample signal, same template and W_block (%d outputs per step)" % (Ls, out)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(case),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(case):
+    return {"workload": "matching_xcorr: L=2^20 Laplacian(0,0.1) signal, N=4096 template (signal cut + "
+                        "N(0,0.01) noise), FFT core, W_block=8192, per-block selection at SNR>=45 dB",
+            "L": int(len(case.s)), "N": int(len(case.k)), "W_block": case.Wblock, "snr_target_db": TARGET_DB,
+            "op": "xcorr", "core": "fft", "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def cpu_baseline(case, mode_bits):
+    """The oracle as it stands on the host cores, on a bounded sample (~10 s)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    mode = O.OP_XCORR | O.CORE_FFT | O.PACK_AUTO
+    Ls = 1 << 15
+    while True:
+        t0 = time.perf_counter()
+        O.apx_conv(case.s[:Ls], case.k, case.Wblock, mode, snr_db=TARGET_DB, nthreads=cores, want_int=False)
+        dt = time.perf_counter() - t0
+        if dt > 5.0 or Ls >= len(case.s):
+            break
+        Ls = min(len(case.s), Ls * 2 if dt < 2.5 else Ls + Ls // 2)
+    out = Ls + len(case.k) - 1
+    return {"value": out / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d samples of the signal (%d outputs), same template, W_block and target; "
+                      "%.1f s wall on %d threads" % (Ls, out, dt, cores)}
+
+
+# ---------------------------------------------------------------------------- main arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if (args.impl == "mine" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_1201_3018_gb300 import apx
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = apx.Context(local)
+    stream = torch.cuda.current_stream()
+    case = wl.matching_xcorr(snr_db=TARGET_DB)
+    L, N, Wb = len(case.s), len(case.k), case.Wblock
+    out_len = L + N - 1
+    s = torch.from_numpy(case.s).to(dev)
+    k = torch.from_numpy(case.k).to(dev)
+    r = torch.empty(out_len, dtype=torch.float32, device=dev)
+    r_full = torch.empty(out_len, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > 129 MB L2
+    mode = apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    mode_full = apx.OP_XCORR | apx.CORE_FFT | apx.PACK_NONE
+
+    def step():
+        ctx.apx_conv(s, k, Wb, mode, TARGET_DB, r, stream=stream)
+
+    def step_full():
+        ctx.apx_conv_full(s, k, Wb, mode_full, r_full, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        step_full()
+    ctx.apx_sync(stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    n0 = ctx.launch_count()
+    clocks.mark("t0")
+    t_ms = time_steps(step, args.steps, flush, stream)
+    clocks.mark("t1")
+    launches = ctx.launch_count() - n0
+    barrier()
+    t_full_ms = time_steps(step_full, args.steps, flush, stream)
+    barrier()
+    clocks.stop()
+    ctx.apx_sync(stream)
+
+    # per-kernel device time (profiled pass, same steps)
+    ctx.profile(True)
+    time_steps(step, args.steps, flush, stream)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+
+    # per-block modes and SNR against the full-precision twin
+    P, _ = apx.plan_blocks(L, N, Wb, mode)
+    st_buf = torch.empty(P * apx.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    ctx.apx_conv(s, k, Wb, mode, TARGET_DB, r, None, st_buf, stream=stream)
+    ctx.apx_conv_full(s, k, Wb, mode_full, r_full, stream=stream)
+    ctx.apx_sync(stream)
+    st = np.frombuffer(st_buf.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)
+    hist = np.bincount(st["mode"], minlength=6).tolist()
+    diff = (r - r_full).double()
+    noise = float((diff * diff).sum())
+    sig = float((r_full.double() ** 2).sum())
+    snr_vs_full = float("inf") if noise == 0 else 10 * math.log10(sig / noise)
+
+    # end to end through the host entry point (pinned host buffers)
+    sh = torch.from_numpy(case.s).pin_memory()
+    kh = torch.from_numpy(case.k).pin_memory()
+    rh = torch.empty(out_len, dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        ctx.apx_conv_host(sh, kh, Wb, mode, TARGET_DB, 0, 0, rh, stream=stream)
+
+    for _ in range(3):
+        step_e2e()
+    barrier()
+    t_e2e_ms = time_steps(step_e2e, args.steps, flush, stream)
+    barrier()
+
+    # max over ranks
+    times = torch.tensor([t_ms, t_full_ms, t_e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_ms, t_full_ms, t_e2e_ms = [float(x) for x in times.tolist()]
+    per_step = t_ms / args.steps
+    value = world * out_len / (per_step * 1e-3) / 1e9
+    full_value = world * out_len / (t_full_ms / args.steps * 1e-3) / 1e9
+    e2e_value = world * out_len / (t_e2e_ms / args.steps * 1e-3) / 1e9
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    pk = peaks()
+    dom = max(prof, key=lambda ph: prof[ph][0])
+    dom_ms, dom_n = prof[dom]
+    avg_ms = dom_ms / max(dom_n, 1)
+    roof = {"kernel": dom, "avg_launch_us": avg_ms * 1e3}
+    packed_blocks = int(sum(hist[1:4]))
+    if dom == "fft":
+        flops = sum(fft_flops(Wb) if m == apx.BLK_FULL else 0.0 for m in st["mode"])
+        fp64 = sum(fft_flops(Wb // 2 if m == apx.BLK_SYM else Wb) for m in st["mode"] if m in (1, 2, 3))
+        if fp64 > flops:
+            roof.update(bound="alu", achieved=fp64 / (avg_ms * 1e-3) / 1e12, peak=pk["fp64_tflops"],
+                        unit="TFLOP/s", peak_source="FP64 nominal 1.25 TFLOP/s scaled to max SM clock")
+        else:
+            roof.update(bound="alu", achieved=flops / (avg_ms * 1e-3) / 1e12, peak=pk["fp32_tflops"],
+                        unit="TFLOP/s", peak_source="152 SMs x 128 FP32 lanes x 2 x max SM clock")
+        roof["algorithmic_flops_per_launch"] = flops + fp64
+    else:
+        byts = 4.0 * (P * Wb + out_len)
+        roof.update(bound="hbm", achieved=byts / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=pk["source"])
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        try:
+            tf = json.load(open(TRAFFIC_FILE))
+            ent = tf.get(dom)
+            if ent and ent.get("source_sha") == kernel_source_sha():
+                traffic = ent.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+    roof["traffic"] = traffic
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if packed_blocks == 0 else "f64+f32", "data": "synthetic",
+        "config": dict(config_dict(case), parallelism="replicas" if world > 1 else "single"),
+        "full_precision": {"value": full_value, "unit": UNIT, "ms_per_step": t_full_ms / args.steps},
+        "speedup_vs_full_precision": value / full_value,
+        "block_modes": {"full": hist[0], "sym": hist[1], "asym2": hist[2], "asym3": hist[3], "zero": hist[4],
+                        "nonfinite": hist[5]},
+        "snr_vs_full_db": snr_vs_full,
+        "serving": {"p50_ms": None, "p99_ms": None},
+        "kernel_ms_per_step": {ph: prof[ph][0] / args.steps for ph in prof},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (L + N),
+                "d2h_bytes_per_step": 4 * out_len},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case, mode)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

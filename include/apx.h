@@ -142,6 +142,21 @@ int apx_sync(apx_ctx* ctx, void* stream);
 /* Number of CUDA kernel launches this context has issued since creation. */
 int64_t apx_launch_count(const apx_ctx* ctx);
 
+/* ---- tracing: per-kernel device time ------------------------------------
+ * With profiling enabled the context records a CUDA event pair on the
+ * launching stream around every kernel it launches.  apx_profile_read waits
+ * for the recorded events, writes the summed milliseconds and the launch count
+ * per kernel kind (APX_PHASE_*) into ms[APX_NPHASES] and n[APX_NPHASES] (either
+ * may be NULL), and clears the record.  Errors: APX_ERR_ARG, APX_ERR_CUDA. */
+#define APX_PHASE_PREP    0   /* kernel statistics, companding, packing of the taps */
+#define APX_PHASE_SELECT  1   /* FFT core: per-block statistics and selection        */
+#define APX_PHASE_SPECTRA 2   /* FFT core: kernel spectra of the selected packings   */
+#define APX_PHASE_DIRECT  3   /* direct core block kernel                            */
+#define APX_PHASE_FFT     4   /* FFT core block kernel                               */
+#define APX_NPHASES       5
+int apx_profile(apx_ctx* ctx, int enable);
+int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
+
 /* Static string naming a status code. */
 const char* apx_strerror(int status);
 

@@ -43,7 +43,10 @@ SIGNATURES = {
     "apx_sync": (C.c_int, [_vp, _vp]),
     "apx_launch_count": (_i64, [_vp]),
     "apx_strerror": (C.c_char_p, [C.c_int]),
+    "apx_profile": (C.c_int, [_vp, C.c_int]),
+    "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
 }
+PHASES = ("prep", "select", "spectra", "direct", "fft")
 
 
 class ApxError(RuntimeError):
@@ -128,6 +131,16 @@ class Context:
 
     def launch_count(self) -> int:
         return lib().apx_launch_count(self._h)
+
+    def profile(self, enable: bool = True):
+        _check("apx_profile", lib().apx_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{phase: (total_ms, launches)} since the previous read."""
+        ms = (C.c_double * len(PHASES))()
+        n = (C.c_int64 * len(PHASES))()
+        _check("apx_profile_read", lib().apx_profile_read(self._h, ms, n))
+        return {ph: (ms[i], n[i]) for i, ph in enumerate(PHASES)}
 
     # ---------------------------------------------------------------- raw entry points
     def apx_conv(self, s, k, W_block, mode, snr_db, r, rq=None, stats=None, stream=None):

@@ -30,6 +30,11 @@ struct apx_ctx {
     int64_t launches = 0;
     DevBuf ki, kfull, kbar[kMaxCand], flags, sel, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     int tw_wb = 0;  // W_block the twiddle tables were built for
+    // tracing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;          // event pool, pairs
+    std::vector<int> ev_phase;            // phase of each recorded pair
+    size_t ev_used = 0;                   // pairs recorded since the last read
 };
 
 namespace {
@@ -239,6 +244,30 @@ int ensure_twiddles(apx_ctx* c, int Wb, cudaStream_t st) {
     return APX_OK;
 }
 
+// Record an event pair around one launch when profiling is on.
+struct Trace {
+    apx_ctx* c;
+    cudaStream_t st;
+    size_t pair = (size_t)-1;
+    Trace(apx_ctx* c_, cudaStream_t st_, int phase) : c(c_), st(st_) {
+        if (!c->profiling) return;
+        if (2 * (c->ev_used + 1) > c->ev.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            c->ev.push_back(a);
+            c->ev.push_back(b);
+            c->ev_phase.push_back(phase);
+        }
+        pair = c->ev_used++;
+        c->ev_phase[pair] = phase;
+        cudaEventRecord(c->ev[2 * pair], st);
+    }
+    ~Trace() {
+        if (pair != (size_t)-1) cudaEventRecord(c->ev[2 * pair + 1], st);
+    }
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -307,12 +336,9 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
             smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
         }
         if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
-    } else {
-        bool asym = false;
-        for (int j = 0; j < nc; ++j) asym |= p.cand[j].blk != APX_BLK_SYM;
-        smem = (size_t)4 * Wb + (asym ? (size_t)8 * Wb : (size_t)4 * Wb);
     }
     p.ncand = nc;
+    if (pl.fft) smem = fft_smem_bytes(p);
 
     // Workspace.
     const int nkp32 = round_up(pl.Nodd, 8);
@@ -346,21 +372,33 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     p.tw32 = (const float2*)ctx->tw32.p;
 
     const int xcorr = (mode & 0xFu) == APX_OP_XCORR;
-    cudaError_t e = launch_prep(p, k, xcorr, kb, (KInfo*)ctx->ki.p, (float*)ctx->kfull.p, stream);
-    ctx->launches += 1;
-    if (e == cudaSuccess) {
-        if (!pl.fft) {
-            e = launch_direct(p, smem, stream);
-            ctx->launches += 1;
-        } else {
+    cudaError_t e;
+    {
+        Trace t(ctx, stream, APX_PHASE_PREP);
+        e = launch_prep(p, k, xcorr, kb, (KInfo*)ctx->ki.p, (float*)ctx->kfull.p, stream);
+        ctx->launches += 1;
+    }
+    if (e == cudaSuccess && !pl.fft) {
+        Trace t(ctx, stream, APX_PHASE_DIRECT);
+        e = launch_direct(p, smem, stream);
+        ctx->launches += 1;
+    } else if (e == cudaSuccess) {
+        {
+            Trace t(ctx, stream, APX_PHASE_SELECT);
             e = launch_select(p, stream);
-            if (e == cudaSuccess) {
-                double2* Hc[kMaxCand] = {(double2*)ctx->Hc[0].p, (double2*)ctx->Hc[1].p, (double2*)ctx->Hc[2].p};
-                for (int j = 0; j < kMaxCand; ++j) if (!Hc[j]) Hc[j] = (double2*)ctx->Hfull.p;
-                e = launch_spectra(p, (float2*)ctx->Hfull.p, Hc, stream);
-            }
-            if (e == cudaSuccess) e = launch_fft(p, smem, stream);
-            ctx->launches += 3;
+            ctx->launches += 1;
+        }
+        if (e == cudaSuccess) {
+            Trace t(ctx, stream, APX_PHASE_SPECTRA);
+            double2* Hc[kMaxCand] = {(double2*)ctx->Hc[0].p, (double2*)ctx->Hc[1].p, (double2*)ctx->Hc[2].p};
+            for (int j = 0; j < kMaxCand; ++j) if (!Hc[j]) Hc[j] = (double2*)ctx->Hfull.p;
+            e = launch_spectra(p, (float2*)ctx->Hfull.p, Hc, stream);
+            ctx->launches += 1;
+        }
+        if (e == cudaSuccess) {
+            Trace t(ctx, stream, APX_PHASE_FFT);
+            e = launch_fft(p, smem, stream);
+            ctx->launches += 1;
         }
     }
     return cuda_status(e);
@@ -396,6 +434,7 @@ void apx_destroy(apx_ctx* c) {
         DevBuf* all[] = {&c->ki, &c->kfull, &c->kbar[0], &c->kbar[1], &c->kbar[2], &c->flags, &c->sel,
                          &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32, &c->hs, &c->hk, &c->hr};
         for (DevBuf* b : all) release(c, *b);
+        for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }
     delete c;
 }
@@ -467,6 +506,34 @@ int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, i
 }
 
 int64_t apx_launch_count(const apx_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int apx_profile(apx_ctx* ctx, int enable) {
+    if (!ctx) return APX_ERR_ARG;
+    ctx->profiling = enable != 0;
+    return APX_OK;
+}
+
+int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n) {
+    if (!ctx) return APX_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    double acc[APX_NPHASES] = {0, 0, 0, 0, 0};
+    int64_t cnt[APX_NPHASES] = {0, 0, 0, 0, 0};
+    for (size_t i = 0; i < ctx->ev_used; ++i) {
+        cudaError_t e = cudaEventSynchronize(ctx->ev[2 * i + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]);
+        if (e != cudaSuccess) { ctx->ev_used = 0; return cuda_status(e); }
+        int ph = ctx->ev_phase[i];
+        acc[ph] += t;
+        cnt[ph] += 1;
+    }
+    ctx->ev_used = 0;
+    for (int i = 0; i < APX_NPHASES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (n) n[i] = cnt[i];
+    }
+    return APX_OK;
+}
 
 const char* apx_strerror(int s) {
     switch (s) {

@@ -31,12 +31,23 @@ __device__ __forceinline__ BlockGeom block_geom(const Params& p, long long i) {
     return g;
 }
 
-// Coalesced window load, zeros outside [0, L).
+// Coalesced window load into shared memory, zeros outside [0, L); pairs of
+// samples per load when the window start is 8-byte aligned (W_block and the
+// block origins are even).
 __device__ __forceinline__ void load_window(const Params& p, const BlockGeom& g, float* xs) {
     const float* __restrict__ s = p.s;
-    for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) {
-        long long gi = g.start + t;
-        xs[t] = (gi >= 0 && gi < p.L) ? __ldg(&s[gi]) : 0.f;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(s + g.start) & 7u) == 0);
+    for (int t = 2 * threadIdx.x; t < p.Wb; t += 2 * blockDim.x) {
+        const long long gi = g.start + t;
+        float2 v;
+        if (aligned && gi >= 0 && gi + 1 < p.L) {
+            v = __ldg(reinterpret_cast<const float2*>(s + gi));
+        } else {
+            v.x = (gi >= 0 && gi < p.L) ? __ldg(&s[gi]) : 0.f;
+            v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? __ldg(&s[gi + 1]) : 0.f;
+        }
+        xs[t] = v.x;
+        xs[t + 1] = v.y;
     }
     __syncthreads();
 }

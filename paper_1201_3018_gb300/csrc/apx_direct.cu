@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
     for (int t = threadIdx.x; t < kRf; t += blockDim.x) xs[p.Wb + t] = 0.f;
     load_window(p, g, xs);
 
+    pdl_wait();  // packed taps and kernel statistics from the preparation launch
     const Pro pr = block_prologue(p, xs, sh);
     if (pr.kind != 0) { handle_trivial(p, i, g, pr); return; }
 
@@ -175,15 +176,16 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
 }
 
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static int attr_dev = -1;
+    int dev;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr_dev = dev;
     }
     if (p.P <= 0) return cudaSuccess;
-    k_direct<<<(unsigned)p.P, kDirectThreads, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_k(k_direct, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, true, p);
 }
 
 }  // namespace apx

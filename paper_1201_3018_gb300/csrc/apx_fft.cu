@@ -1,65 +1,136 @@
 // apx_fft.cu -- the frequency-domain (FFT) core.
 //
-// Pass 1 (k_select): one CTA per block computes the block statistics and runs
-// the Section IV.D selection; for a packing candidate it also companded the
-// block and checks the FFT error bound (reading c7) with the exact integer
-// norm sum(s~^2), so the packed digits are recovered by rounding.
-// Pass 2 (k_spectra, apx_prep.cu): kernel spectra of the candidates in use.
-// Pass 3 (k_fft): one CTA per block: compand + pack into a complex buffer
-// (two real samples per complex word), forward real FFT, product with the
-// kernel spectrum, inverse FFT, digit extraction, inverse companding, store.
+// k_select (one CTA per block): window statistics and the Section IV.D
+// selection; for a packing candidate it also companded the block and checks
+// the FFT error bound (reading c7) with the exact integer norm sum(s~^2), so
+// that rounding recovers the packed digits exactly.
+// k_spectra (apx_prep.cu): kernel spectra of the candidates in use.
+// k_fft (one CTA per block): compand + pack into a complex buffer (two real
+// words per complex entry), forward real FFT, product with the kernel
+// spectrum, inverse FFT, digit extraction, inverse companding, store.
+//
+// Each kernel is launched as a programmatic dependent of the previous one: the
+// window is fetched into registers before griddepcontrol.wait, so the load
+// overlaps the tail of the previous kernel.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
 namespace apx {
 
-__global__ void __launch_bounds__(kFftThreads) k_select(const Params p) {
-    extern __shared__ __align__(16) unsigned char smem[];
+constexpr int kVals = 32;  // window samples per thread (W_block / threads)
+
+// Thread t holds window samples 2(t + i NT) and 2(t + i NT) + 1 (pair t + i NT)
+// for pairs below W_block/2; other slots hold zeros, which leave the maximum,
+// the second moment and the companded norm unchanged.
+__device__ __forceinline__ bool pair_ok(const Params& p, int i) { return threadIdx.x + i * blockDim.x < p.Wb / 2; }
+
+__device__ __forceinline__ void load_window_regs(const Params& p, long long start, float (&xv)[kVals]) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(p.s + start) & 7u) == 0);
+#pragma unroll
+    for (int i = 0; i < kVals / 2; ++i) {
+        xv[2 * i] = 0.f;
+        xv[2 * i + 1] = 0.f;
+        if (pair_ok(p, i)) {
+            const long long gi = start + 2ll * (threadIdx.x + i * blockDim.x);
+            float2 v;
+            if (aligned && gi >= 0 && gi + 1 < p.L) {
+                v = __ldg(reinterpret_cast<const float2*>(p.s + gi));
+            } else {
+                v.x = (gi >= 0 && gi < p.L) ? __ldg(p.s + gi) : 0.f;
+                v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? __ldg(p.s + gi + 1) : 0.f;
+            }
+            xv[2 * i] = v.x;
+            xv[2 * i + 1] = v.y;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512) k_select(const Params p) {
     __shared__ Shared sh;
+    pdl_trigger();
     const long long i = blockIdx.x;
     const BlockGeom g = block_geom(p, i);
-    float* xs = reinterpret_cast<float*>(smem);
-    load_window(p, g, xs);
-    const Pro pr = block_prologue(p, xs, sh);
-    Sel s;
-    s.cs = 0.f; s.Ms = pr.Ms; s.sig2 = pr.sig2; s.ferr = 0.0; s.pad_ = 0;
-    if (pr.kind != 0) {
-        s.ci = pr.kind == 3 ? -3 : -2;
-        if (threadIdx.x == 0) p.sel[i] = s;
-        return;
+    float xv[kVals];
+    load_window_regs(p, g.start, xv);
+
+    // ||s||_inf and the fixed-point second moment, from registers
+    float m = 0.f;
+    int bad = 0;
+#pragma unroll
+    for (int v = 0; v < kVals; ++v) {
+        float a = fabsf(xv[v]);
+        if (a != a) bad = 1;
+        m = fmaxf(m, a);
     }
-    const KInfo& ki = *p.ki;
-    s.ci = -1;
-    for (int c = 0; c < p.ncand; ++c) {
-        const Cand& cd = p.cand[c];
-        if (p.autosel && !snr_feasible(pr.sig2, pr.Ms, ki.sig2k, ki.Mk, cd.S, cd.K, p.thr)) continue;
-        const float cs = compand_factor(cd.S, pr.Ms);
-        long long ss = 0;
-        for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) {
-            long long q = compand(cs, xs[t]);
-            ss += q * q;
+    m = block_reduce<float, true>(m, sh.redf);
+    bad = block_reduce<int, true>(bad, sh.redi);
+    Sel s;
+    s.cs = 0.f; s.Ms = bad ? __int_as_float(0x7fc00000) : m; s.sig2 = 0.0; s.ferr = 0.0; s.pad_ = 0;
+    const bool finite = !bad && m <= 3.402823466e38f;
+    double sig2 = 0.0;
+    if (finite && m > 0.f) {
+        int e;
+        (void)frexpf(m, &e);
+        const int sh2 = 24 - e, a = sh2 / 2, b = sh2 - a;
+        const float fa = __int_as_float((a + 127) << 23), fb = __int_as_float((b + 127) << 23);
+        long long acc = 0;
+#pragma unroll
+        for (int v = 0; v < kVals; ++v) {
+            const long long q = __float2int_rz(__fmul_rn(__fmul_rn(xv[v], fa), fb));
+            acc += q * q;
         }
-        ss = block_reduce<long long, false>(ss, sh.redl);
-        const double eps = ldexp(1.0, -cd.b);
-        const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
-        const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
-        const double E = ldexp(__dmul_rn(__dmul_rn(cd.fftc, ki.l1[c]), l2), cd.sc);
-        if (E < 0.25) {
-            s.ci = c; s.cs = cs; s.ferr = E;
-            break;
+        acc = block_reduce<long long, false>(acc, sh.redl);
+        sig2 = __ddiv_rn(ldexp(__ll2double_rn(acc), -2 * sh2), (double)p.Wb);
+    }
+    s.sig2 = sig2;
+
+    pdl_wait();  // kernel statistics from the preparation launch
+    const KInfo& ki = *p.ki;
+    if (!finite || ki.nonfinite) s.ci = -3;
+    else if (m == 0.f || ki.Mk == 0.f) s.ci = -2;
+    else {
+        s.ci = -1;
+        for (int c = 0; c < p.ncand; ++c) {
+            const Cand& cd = p.cand[c];
+            if (p.autosel && !snr_feasible(sig2, m, ki.sig2k, ki.Mk, cd.S, cd.K, p.thr)) continue;
+            const float cs = compand_factor(cd.S, m);
+            long long ss = 0;
+#pragma unroll
+            for (int v = 0; v < kVals; ++v) {
+                const long long q = compand(cs, xv[v]);
+                ss += q * q;
+            }
+            ss = block_reduce<long long, false>(ss, sh.redl);
+            const double eps = ldexp(1.0, -cd.b);
+            const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
+            const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
+            const double E = ldexp(__dmul_rn(__dmul_rn(cd.fftc, ki.l1[c]), l2), cd.sc);
+            if (E < 0.25) {
+                s.ci = c; s.cs = cs; s.ferr = E;
+                break;
+            }
         }
     }
     if (threadIdx.x == 0) {
         p.sel[i] = s;
-        atomicOr(p.used, s.ci >= 0 ? (1u << s.ci) : 8u);
+        if (s.ci >= -1) atomicOr(p.used, s.ci >= 0 ? (1u << s.ci) : 8u);
     }
 }
 
-template <int MAXB>
-__global__ void __launch_bounds__(kFftThreads) k_fft(const Params p) {
+// real word w of a padded complex buffer
+template <typename R, typename C>
+__device__ __forceinline__ R& word(C* Z, int w) {
+    return reinterpret_cast<R*>(Z)[2 * pad16(w >> 1) + (w & 1)];
+}
+
+__global__ void __launch_bounds__(512) k_fft(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long i = blockIdx.x;
     const BlockGeom g = block_geom(p, i);
+    float xv[kVals];
+    load_window_regs(p, g.start, xv);
+
+    pdl_wait();  // spectra (and, through it, the selection) complete
     const Sel s = p.sel[i];
     if (s.ci <= -2) {
         Pro pr;
@@ -69,24 +140,22 @@ __global__ void __launch_bounds__(kFftThreads) k_fft(const Params p) {
         handle_trivial(p, i, g, pr);
         return;
     }
-    float* xs = reinterpret_cast<float*>(smem);
-    unsigned char* cbuf = smem + (size_t)4 * p.Wb;
-    load_window(p, g, xs);
 
     if (s.ci < 0) {
         // Full precision: real FFT of length W_block in FP32.
         const int m = p.Wb / 2;
-        float2* z = reinterpret_cast<float2*>(cbuf);
-        for (int j = threadIdx.x; j < m; j += blockDim.x) z[j] = make_float2(xs[2 * j], xs[2 * j + 1]);
+        float2* Z = reinterpret_cast<float2*>(smem);
+#pragma unroll
+        for (int v = 0; v < kVals / 2; ++v)
+            if (pair_ok(p, v)) Z[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
         __syncthreads();
-        fft_smem<float2, false, MAXB>(z, m, p.tw32, 2);
-        spectral_multiply(z, m, p.Hfull, p.tw32, 1);
-        fft_smem<float2, true, MAXB>(z, m, p.tw32, 2);
-        const float* y = reinterpret_cast<const float*>(z);
+        fft_smem<float2, false>(Z, m, p.tw32, p.Wb);
+        spectral_multiply(Z, m, p.Hfull, p.tw32, 1);
+        fft_smem<float2, true>(Z, m, p.tw32, p.Wb);
         for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
             const long long o = g.start + j;
             if (o < 0 || o >= p.out_len) continue;
-            p.r[o] = y[j];
+            p.r[o] = word<float>(Z, j);
             if (p.rq) p.rq[o] = 0;
         }
         write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, s.Ms, s.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
@@ -96,41 +165,53 @@ __global__ void __launch_bounds__(kFftThreads) k_fft(const Params p) {
     const Cand& c = p.cand[s.ci];
     const float cs = s.cs;
     const double eps = ldexp(1.0, -c.b);
-    double2* z = reinterpret_cast<double2*>(cbuf);
-    double* zr = reinterpret_cast<double*>(cbuf);  // packed real words, two per complex entry
+    double2* Z = reinterpret_cast<double2*>(smem);
     int n, Ls = 0, nr = 0;
     if (c.blk == APX_BLK_SYM) {
+        // Eq. (4): word w = s~[2w] + eps s~[2w+1]; this thread holds pair w
         n = p.Wb / 2;
-        for (int m = threadIdx.x; m < n; m += blockDim.x) {              // Eq. (4)
-            const double e = (double)compand(cs, xs[2 * m]);
-            const double o = (double)compand(cs, xs[2 * m + 1]);
-            zr[m] = __dadd_rn(e, __dmul_rn(eps, o));
-        }
+#pragma unroll
+        for (int v = 0; v < kVals / 2; ++v)
+            if (pair_ok(p, v)) {
+                const int w = threadIdx.x + v * blockDim.x;
+                word<double>(Z, w) = __dadd_rn((double)compand(cs, xv[2 * v]),
+                                               __dmul_rn(eps, (double)compand(cs, xv[2 * v + 1])));
+            }
     } else {
+        // Eq. (7): word w = sum_q eps^q s~[w + q Ls], zero past Ls
         n = p.Wb;
         Ls = (p.Wb + c.M - 1) / c.M;
         nr = Ls + p.Nodd - 1;
-        for (int m = threadIdx.x; m < n; m += blockDim.x) {              // Eq. (7), zero past Ls
+        int* sq = reinterpret_cast<int*>(smem + sizeof(double2) * padded_len(p.Wb / 2));
+#pragma unroll
+        for (int v = 0; v < kVals / 2; ++v)
+            if (pair_ok(p, v)) {
+                const int e = 2 * (threadIdx.x + v * blockDim.x);
+                sq[e] = compand(cs, xv[2 * v]);
+                sq[e + 1] = compand(cs, xv[2 * v + 1]);
+            }
+        __syncthreads();
+        for (int w = threadIdx.x; w < n; w += blockDim.x) {
             double acc = 0.0, ep = 1.0;
-            if (m < Ls) {
+            if (w < Ls) {
                 for (int q = 0; q < c.M; ++q) {
-                    const int t = m + q * Ls;
-                    if (t < p.Wb) acc = __dadd_rn(acc, __dmul_rn(ep, (double)compand(cs, xs[t])));
+                    const int t = w + q * Ls;
+                    if (t < p.Wb) acc = __dadd_rn(acc, __dmul_rn(ep, (double)sq[t]));
                     ep = __dmul_rn(ep, eps);
                 }
             }
-            zr[m] = acc;
+            word<double>(Z, w) = acc;
         }
     }
     __syncthreads();
     const int m = n / 2;
-    fft_smem<double2, false, MAXB>(z, m, p.tw64, p.Wb / m);
-    spectral_multiply(z, m, c.H, p.tw64, p.Wb / n);
-    fft_smem<double2, true, MAXB>(z, m, p.tw64, p.Wb / m);
+    fft_smem<double2, false>(Z, m, p.tw64, p.Wb);
+    spectral_multiply(Z, m, c.H, p.tw64, p.Wb / n);
+    fft_smem<double2, true>(Z, m, p.tw64, p.Wb);
 
     const KInfo& ki = *p.ki;
     const float inv = (float)(1.0 / ((double)cs * (double)ki.ck[s.ci]));
-    auto Tat = [&](int idx) { return scaled(zr[idx], c.sc); };
+    auto Tat = [&](int idx) { return scaled(word<double>(Z, idx), c.sc); };
     for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
         if (o < 0 || o >= p.out_len) continue;
@@ -143,40 +224,30 @@ __global__ void __launch_bounds__(kFftThreads) k_fft(const Params p) {
 }
 
 cudaError_t launch_select(const Params& p, cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev;
-    cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
     if (p.P <= 0) return cudaSuccess;
-    k_select<<<(unsigned)p.P, kFftThreads, (size_t)4 * p.Wb, st>>>(p);
-    return cudaGetLastError();
+    return launch_k(k_select, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), 0, st, true, p);
 }
 
-template <int MAXB>
-static cudaError_t fft_t(const Params& p, size_t smem, cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev;
-    cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_fft<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
-    k_fft<MAXB><<<(unsigned)p.P, kFftThreads, smem, st>>>(p);
-    return cudaGetLastError();
+size_t fft_smem_bytes(const Params& p) {
+    bool asym = false, packed = p.ncand > 0;
+    for (int j = 0; j < p.ncand; ++j) asym |= p.cand[j].blk != APX_BLK_SYM;
+    size_t z32 = sizeof(float2) * padded_len(p.Wb / 2);
+    size_t z64 = packed ? sizeof(double2) * padded_len(asym ? p.Wb / 2 : p.Wb / 4) : 0;
+    size_t sq = asym ? sizeof(int) * (size_t)p.Wb : 0;
+    return (z32 > z64 + sq ? z32 : z64 + sq);
 }
 
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
     if (p.P <= 0) return cudaSuccess;
-    switch (fft_maxb(p.Wb)) {
-        case 1: return fft_t<1>(p, smem, st);
-        case 2: return fft_t<2>(p, smem, st);
-        default: return fft_t<4>(p, smem, st);
+    static int attr_dev = -1;
+    int dev;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
     }
+    return launch_k(k_fft, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
 }
 
 }  // namespace apx

@@ -227,68 +227,157 @@ template <typename C, bool INV> __device__ __forceinline__ void dft8(C* v) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) { v[k] = cadd(e[k], o[k]); v[k + 4] = csub(e[k], o[k]); }
 }
+// exp(-+ 2 pi i e / 16) for the exponents that occur inside a 4x4 DFT16
+template <typename C, bool INV> __device__ __forceinline__ C mul_w16(C a, int e) {
+    using R = decltype(a.x);
+    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+    R wr, wi;  // forward value cos - i sin
+    switch (e) {
+        case 1: wr = c1; wi = -s1; break;
+        case 2: wr = h; wi = -h; break;
+        case 3: wr = s1; wi = -c1; break;
+        case 4: return mul_mi<C, INV>(a);
+        case 6: wr = -h; wi = -h; break;
+        default: wr = -c1; wi = s1; break;  // e = 9
+    }
+    if (INV) wi = -wi;
+    C r;
+    r.x = a.x * wr - a.y * wi;
+    r.y = a.x * wi + a.y * wr;
+    return r;
+}
+// DFT16 as 4 x 4: X[b + 4d] = sum_a W4^(ad) W16^(ab) sum_c x[a + 4c] W4^(cb)
+template <typename C, bool INV> __device__ __forceinline__ void dft16(C* v) {
+    C t[16];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        C u[4] = {v[a], v[a + 4], v[a + 8], v[a + 12]};
+        dft4<C, INV>(u);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) t[4 * a + b] = (a && b) ? mul_w16<C, INV>(u[b], a * b) : u[b];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        C u[4] = {t[b], t[4 + b], t[8 + b], t[12 + b]};
+        dft4<C, INV>(u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) v[b + 4 * d] = u[d];
+    }
+}
 template <int RAD, typename C, bool INV> __device__ __forceinline__ void dft_small(C* v) {
-    if constexpr (RAD == 8) dft8<C, INV>(v);
+    if constexpr (RAD == 16) dft16<C, INV>(v);
+    else if constexpr (RAD == 8) dft8<C, INV>(v);
     else if constexpr (RAD == 4) dft4<C, INV>(v);
     else dft2<C, INV>(v);
 }
 
-// One Stockham autosort pass of a length-m complex FFT held in shared memory.
-// Ns is the size of the sub-transforms already done.  Twiddles come from a
-// table of exp(-2 pi i t / ntab) with ntab a multiple of m (stride ntab/m).
-template <typename C, int RAD, bool INV, int MAXB>
-__device__ void fft_pass(C* data, int m, int Ns, const C* __restrict__ tw, int tws) {
-    const int nb = m / RAD;
-    C v[MAXB][RAD];
-    int jj[MAXB];
-    const int span = Ns * RAD;
-    const int tstep = (m / span) * tws;
+// Shared-memory slot of complex element i: one pad element per 16 makes every
+// pass below use the minimum number of shared-memory wavefronts.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int m) { return m + (m >> 4) + 1; }
+
+// Twiddles w[r] = W_M^(r j), r < RAD, from a table of exp(-2 pi i t / ntab).
+// FP32: one table load and products (at most four deep); FP64: one load each,
+// so that every twiddle carries only the table's rounding (the FFT error bound
+// assumes that).
+template <typename C, int RAD, bool INV>
+__device__ __forceinline__ void twiddles(C (&w)[RAD], const C* __restrict__ tw, int step) {
+    using R = decltype(w[0].x);
+    w[0].x = (R)1; w[0].y = (R)0;
+    if constexpr (sizeof(R) == 8) {
 #pragma unroll
-    for (int bi = 0; bi < MAXB; ++bi) {
-        int j = threadIdx.x + bi * blockDim.x;
-        jj[bi] = j;
-        if (j < nb) {
-            const int k = j & (Ns - 1);
+        for (int r = 1; r < RAD; ++r) w[r] = __ldg(&tw[r * step]);
+    } else {
+        if constexpr (RAD > 1) w[1] = __ldg(&tw[step]);
+        if constexpr (RAD > 2) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[2], w[1]); }
+        if constexpr (RAD > 4) {
+            w[4] = cmul(w[2], w[2]);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) {
-                C a = data[j + r * nb];
-                if (r > 0 && Ns > 1) {
-                    C w = __ldg(&tw[r * k * tstep]);
-                    if (INV) w.y = -w.y;
-                    a = cmul(a, w);
-                }
-                v[bi][r] = a;
+            for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+        }
+        if constexpr (RAD > 8) {
+            w[8] = cmul(w[4], w[4]);
+#pragma unroll
+            for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+        }
+    }
+    if (INV) {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) w[r].y = -w[r].y;
+    }
+}
+
+// One in-place pass over sub-transforms of length M with radix RAD (stride
+// S = M/RAD).  Forward (decimation in frequency): DFT then twiddle W_M^(r j).
+// Inverse (decimation in time, the exact reverse): conjugate twiddle then
+// inverse DFT.  Each thread reads and writes the same slots, so a pass needs
+// no barrier inside; callers separate passes with __syncthreads().
+template <typename C, int RAD, bool INV>
+__device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab) {
+    const int S = M / RAD, nbf = m / RAD;
+    const int tstep = ntab / M;
+    constexpr int BPT = 16 / RAD;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * blockDim.x;
+        if (b < nbf) {
+            const int g = b / S, j = b - g * S;
+            const int base = g * M + j;
+            C v[RAD], w[RAD];
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) v[q] = Z[pad16(base + q * S)];
+            twiddles<C, RAD, INV>(w, tw, j * tstep);
+            if (!INV) {
+                dft_small<RAD, C, false>(v);
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
+                dft_small<RAD, C, true>(v);
             }
-            dft_small<RAD, C, INV>(v[bi]);
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) Z[pad16(base + q * S)] = v[q];
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int bi = 0; bi < MAXB; ++bi) {
-        const int j = jj[bi];
-        if (j < nb) {
-            const int k = j & (Ns - 1);
-            const int o = (j - k) * RAD + k;
-#pragma unroll
-            for (int r = 0; r < RAD; ++r) data[o + r * Ns] = v[bi][r];
-        }
+}
+
+// Length-m (power of two) complex FFT of the padded buffer Z.  Forward:
+// natural order in, digit-reversed order out (see fft_perm).  Inverse: that
+// order in, natural order out, unnormalised.  Needs blockDim.x >= m / 16.
+template <typename C, bool INV>
+__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
+    int a = 0, t = m;
+    while (t >= 16) { t >>= 4; ++a; }   // m = 16^a * t, t in {1, 2, 4, 8}
+    if (!INV) {
+        int M = m;
+        for (int s = 0; s < a; ++s) { fft_pass<C, 16, false>(Z, m, M, tw, ntab); __syncthreads(); M >>= 4; }
+        if (t == 8) fft_pass<C, 8, false>(Z, m, 8, tw, ntab);
+        else if (t == 4) fft_pass<C, 4, false>(Z, m, 4, tw, ntab);
+        else if (t == 2) fft_pass<C, 2, false>(Z, m, 2, tw, ntab);
+        if (t > 1) __syncthreads();
+    } else {
+        if (t == 8) fft_pass<C, 8, true>(Z, m, 8, tw, ntab);
+        else if (t == 4) fft_pass<C, 4, true>(Z, m, 4, tw, ntab);
+        else if (t == 2) fft_pass<C, 2, true>(Z, m, 2, tw, ntab);
+        if (t > 1) __syncthreads();
+        int M = t * 16;
+        for (int s = 0; s < a; ++s) { fft_pass<C, 16, true>(Z, m, M, tw, ntab); __syncthreads(); M <<= 4; }
     }
-    __syncthreads();
 }
 
-// Length-m (power of two, 2..8192) complex FFT in shared memory, unnormalised.
-// Radix-8 passes, then one radix-4 or radix-2 pass for the remainder.
-template <typename C, bool INV, int MAXB>
-__device__ void fft_smem(C* data, int m, const C* __restrict__ tw, int tws) {
-    int Ns = 1;
-    while (Ns * 8 <= m) { fft_pass<C, 8, INV, MAXB>(data, m, Ns, tw, tws); Ns *= 8; }
-    if (Ns * 4 == m) fft_pass<C, 4, INV, MAXB * 2>(data, m, Ns, tw, tws);
-    else if (Ns * 2 == m) fft_pass<C, 2, INV, MAXB * 4>(data, m, Ns, tw, tws);
+// Slot of frequency k after the forward FFT: k = r1 + R1 r2 + R1 R2 r3 + ...
+// (r_s the output digit of pass s) sits at r1 S1 + r2 S2 + ..., S_s the
+// stride of pass s.
+__device__ __forceinline__ int fft_perm(int k, int m) {
+    int pos = 0, S = m;
+    while (S >= 16) { S >>= 4; pos += (k & 15) * S; k >>= 4; }
+    if (S > 1) pos += k & (S - 1);   // last pass: stride 1
+    return pos;
 }
 
-// Real-signal spectral step shared by the block convolution and the kernel
-// preparation.  Z holds FFT_m of z[j] = x[2j] + i x[2j+1] (n = 2m real
-// samples).  With W = exp(-2 pi i / n):
+// Real-signal step.  Z holds FFT_m of z[j] = x[2j] + i x[2j+1] (n = 2m real
+// samples) in fft_perm order.  With W = exp(-2 pi i / n):
 //   X2[k] = (Z[k] + conj Z[m-k]) - i W^k (Z[k] - conj Z[m-k]) = 2 X[k].
 template <typename C>
 __device__ __forceinline__ void real_post(C a, C b, C w, C& Xk, C& Xmk) {
@@ -299,7 +388,7 @@ __device__ __forceinline__ void real_post(C a, C b, C w, C& Xk, C& Xmk) {
     C wm = w; wm.x = -w.x;  // -conj(w)
     Xmk = cadd(cadd(b, ca), mul_mi<C, false>(cmul(wm, d2)));
 }
-// Inverse: from Y2 (spectrum of the real result, times 2) build
+// Inverse: from Y (spectrum of the real result) build
 //   Z'[k] = (Y[k] + conj Y[m-k]) + i conj(W^k) (Y[k] - conj Y[m-k])
 template <typename C>
 __device__ __forceinline__ void real_pre(C yk, C ymk, C w, C& Zk, C& Zmk) {
@@ -310,36 +399,41 @@ __device__ __forceinline__ void real_pre(C yk, C ymk, C w, C& Zk, C& Zmk) {
     Zmk = cadd(cadd(ymk, cyk), mul_mi<C, true>(cmul(wmc, csub(ymk, cyk))));
 }
 
-// Z (length m, FFT of the packed real block) -> Z' ready for the inverse FFT,
-// multiplying by the kernel spectrum H = FFT_n(k) / (4m) (m+1 entries).  The
-// factor 2 of X2, the missing 1/2 of the inverse step and the 1/m of the
-// inverse FFT all fold into that power-of-two scale, which is exact.
+// Z (forward FFT of the packed real block, fft_perm order) -> Z' ready for the
+// inverse FFT, multiplying by the kernel spectrum H = FFT_n(k) / (4m) (m+1
+// entries, natural order).  The factor 2 of X2, the missing 1/2 of the inverse
+// step and the 1/m of the inverse FFT fold into that power-of-two scale.
 template <typename C>
 __device__ void spectral_multiply(C* Z, int m, const C* __restrict__ H, const C* __restrict__ tw, int twn) {
-    // twn: table index stride for W_n^k (ntab / n)
     for (int k = threadIdx.x; k <= m / 2; k += blockDim.x) {
         if (k == 0) {
             C z0 = Z[0];
             C X0, Xm;
             X0.x = 2 * (z0.x + z0.y); X0.y = 0;
             Xm.x = 2 * (z0.x - z0.y); Xm.y = 0;
-            C Y0 = cmul(X0, H[0]), Ym = cmul(Xm, H[m]);
+            C Y0 = cmul(X0, __ldg(&H[0])), Ym = cmul(Xm, __ldg(&H[m]));
             C cym = cconj(Ym);
             Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
         } else {
-            C a = Z[k], b = Z[m - k];
+            const int pk = pad16(fft_perm(k, m)), pmk = pad16(fft_perm(m - k, m));
+            C a = Z[pk], b = Z[pmk];
             C w = __ldg(&tw[k * twn]);
             C Xk, Xmk;
             real_post(a, b, w, Xk, Xmk);
-            C Yk = cmul(Xk, H[k]);
-            C Ymk = cmul(Xmk, H[m - k]);
+            C Yk = cmul(Xk, __ldg(&H[k]));
+            C Ymk = cmul(Xmk, __ldg(&H[m - k]));
             C Zk, Zmk;
             real_pre(Yk, Ymk, w, Zk, Zmk);
-            Z[k] = Zk;
-            if (k != m - k) Z[m - k] = Zmk;
+            Z[pk] = Zk;
+            if (k != m - k) Z[pmk] = Zmk;
         }
     }
     __syncthreads();
 }
+
+// Programmatic dependent launch: let the next kernel in the stream start, and
+// wait for the previous one's results.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 }  // namespace apx

@@ -8,9 +8,30 @@
 namespace apx {
 
 constexpr int kDirectThreads = 256;
-constexpr int kFftThreads = 256;
 constexpr int kPrepThreads = 1024;
 constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (static shared memory needs the rest)
+
+// FFT core: one thread per 16 complex points of the largest transform (W_block/2).
+__host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 32 > 32 ? Wb / 32 : 32; }
+
+// Launch through cudaLaunchKernelEx; `pdl` marks the launch as a programmatic
+// dependent of the previous kernel in the stream (the kernel calls
+// griddepcontrol.wait before it reads that kernel's results).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 cudaError_t launch_prep(const Params& p, const float* k, int xcorr, double* kbar_out[kMaxCand], KInfo* ki,
                         float* kfull, cudaStream_t st);
@@ -18,7 +39,6 @@ cudaError_t launch_select(const Params& p, cudaStream_t st);
 cudaError_t launch_spectra(const Params& p, float2* Hfull, double2* Hc[kMaxCand], cudaStream_t st);
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
-
-int fft_maxb(int Wb);
+size_t fft_smem_bytes(const Params& p);
 
 }  // namespace apx
