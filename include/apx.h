@@ -148,12 +148,11 @@ int64_t apx_launch_count(const apx_ctx* ctx);
  * for the recorded events, writes the summed milliseconds and the launch count
  * per kernel kind (APX_PHASE_*) into ms[APX_NPHASES] and n[APX_NPHASES] (either
  * may be NULL), and clears the record.  Errors: APX_ERR_ARG, APX_ERR_CUDA. */
-#define APX_PHASE_PREP    0   /* kernel statistics, companding, packing of the taps */
-#define APX_PHASE_SELECT  1   /* FFT core: per-block statistics and selection        */
-#define APX_PHASE_SPECTRA 2   /* FFT core: kernel spectra of the selected packings   */
-#define APX_PHASE_DIRECT  3   /* direct core block kernel                            */
-#define APX_PHASE_FFT     4   /* FFT core block kernel                               */
-#define APX_NPHASES       5
+#define APX_PHASE_DIRECT  0   /* direct core: the single fused block kernel            */
+#define APX_PHASE_SELECT  1   /* FFT core: kernel and block statistics, selection     */
+#define APX_PHASE_SPECTRA 2   /* FFT core: kernel spectra (FP32, and packings in use) */
+#define APX_PHASE_FFT     3   /* FFT core: block kernel                               */
+#define APX_NPHASES       4
 int apx_profile(apx_ctx* ctx, int enable);
 int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
 

@@ -28,8 +28,9 @@ struct apx_ctx {
     size_t budget = 0;
     size_t in_use = 0;
     int64_t launches = 0;
-    DevBuf ki, kfull, kbar[kMaxCand], flags, sel, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
-    int tw_wb = 0;  // W_block the twiddle tables were built for
+    DevBuf ki, flags, sel, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    int tw_wb = 0;          // W_block the twiddle tables were built for
+    int64_t fft_calls = 0;  // selects the `used` slot of an FFT-core call
     // tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;          // event pool, pairs
@@ -193,14 +194,19 @@ int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
 
 int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
-// Direct core shared-memory layout for the candidate set.
+// Direct core shared-memory layout for the candidate set: window (zero front
+// pad), FP32 taps, and for packed blocks the packed signal, the packed outputs
+// and the packed taps.
 size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl) {
     dl->padF = round_up(Nodd, 8);
-    size_t xs_bytes = (size_t)4 * (dl->padF + Wb + 8);
-    int padS = 0, body = 0, nT = 0;
+    size_t off = (size_t)4 * (dl->padF + Wb + 8);
+    dl->offK = (int)((off + 15) / 16 * 16);
+    off = (size_t)dl->offK + (size_t)4 * round_up(Nodd, 8);
+    int padS = 0, body = 0, nT = 0, nkb = 0;
     for (int i = 0; i < nc; ++i) {
         int nkp = round_up(c[i].nk, 4);
         if (nkp > padS) padS = nkp;
+        if (nkp > nkb) nkb = nkp;
         if (c[i].blk == APX_BLK_SYM) {
             body = body > Wb / 2 + 4 ? body : Wb / 2 + 4;
             nT = nT > Wb / 2 ? nT : Wb / 2;
@@ -212,11 +218,12 @@ size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl) 
             nT = nT > t ? nT : t;
         }
     }
-    dl->offS = (int)((xs_bytes + 15) / 16 * 16);
+    dl->offS = (int)((off + 15) / 16 * 16);
     dl->padS = padS;
     dl->nS = nc ? padS + body : 0;
     dl->offT = (int)(((size_t)dl->offS + (size_t)8 * dl->nS + 15) / 16 * 16);
-    return (size_t)dl->offT + (size_t)8 * nT;
+    dl->offKb = (int)(((size_t)dl->offT + (size_t)8 * nT + 15) / 16 * 16);
+    return (size_t)dl->offKb + (size_t)8 * nkb;
 }
 
 // exp(-2 pi i t / Wb), t in [0, Wb), from long double arithmetic.
@@ -341,48 +348,37 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     if (pl.fft) smem = fft_smem_bytes(p);
 
     // Workspace.
-    const int nkp32 = round_up(pl.Nodd, 8);
-    rc = ensure(ctx, ctx->ki, sizeof(KInfo));
-    if (!rc) rc = ensure(ctx, ctx->kfull, sizeof(float) * nkp32);
-    if (!rc) rc = ensure(ctx, ctx->flags, 2 * sizeof(unsigned));
-    for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->kbar[j], sizeof(double) * round_up(p.cand[j].nk, 4));
+    rc = ensure(ctx, ctx->flags, 3 * sizeof(unsigned));
     if (!rc && pl.fft) {
         const size_t m1 = (size_t)Wb / 2 + 1;
-        rc = ensure(ctx, ctx->sel, sizeof(Sel) * pl.P);
+        rc = ensure(ctx, ctx->ki, sizeof(KInfo));
+        if (!rc) rc = ensure(ctx, ctx->sel, sizeof(Sel) * pl.P);
         if (!rc) rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
         for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->Hc[j], sizeof(double2) * m1);
         if (!rc) rc = ensure_twiddles(ctx, Wb, stream);
     }
     if (rc) return rc;
 
-    double* kb[kMaxCand] = {nullptr, nullptr, nullptr};
-    for (int j = 0; j < nc; ++j) {
-        kb[j] = (double*)ctx->kbar[j].p;
-        p.cand[j].kbar = kb[j];
-        p.cand[j].H = (const double2*)ctx->Hc[j].p;
-    }
-    for (int j = nc; j < kMaxCand; ++j) kb[j] = kb[0] ? kb[0] : (double*)ctx->kfull.p;
-    p.kfull = (const float*)ctx->kfull.p;
-    p.ki = (const KInfo*)ctx->ki.p;
+    for (int j = 0; j < nc; ++j) p.cand[j].H = (const double2*)ctx->Hc[j].p;
+    p.k = k;
+    p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
+    p.ki = (KInfo*)ctx->ki.p;
     p.status = (unsigned*)ctx->flags.p;
-    p.used = (unsigned*)ctx->flags.p + 1;
+    const int slot = (int)(ctx->fft_calls & 1);
+    p.used = (unsigned*)ctx->flags.p + 1 + slot;
+    p.used_next = (unsigned*)ctx->flags.p + 2 - slot;
     p.sel = (Sel*)ctx->sel.p;
     p.Hfull = (const float2*)ctx->Hfull.p;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
 
-    const int xcorr = (mode & 0xFu) == APX_OP_XCORR;
     cudaError_t e;
-    {
-        Trace t(ctx, stream, APX_PHASE_PREP);
-        e = launch_prep(p, k, xcorr, kb, (KInfo*)ctx->ki.p, (float*)ctx->kfull.p, stream);
-        ctx->launches += 1;
-    }
-    if (e == cudaSuccess && !pl.fft) {
+    if (!pl.fft) {
         Trace t(ctx, stream, APX_PHASE_DIRECT);
         e = launch_direct(p, smem, stream);
         ctx->launches += 1;
-    } else if (e == cudaSuccess) {
+    } else {
+        ctx->fft_calls += 1;
         {
             Trace t(ctx, stream, APX_PHASE_SELECT);
             e = launch_select(p, stream);
@@ -391,7 +387,6 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         if (e == cudaSuccess) {
             Trace t(ctx, stream, APX_PHASE_SPECTRA);
             double2* Hc[kMaxCand] = {(double2*)ctx->Hc[0].p, (double2*)ctx->Hc[1].p, (double2*)ctx->Hc[2].p};
-            for (int j = 0; j < kMaxCand; ++j) if (!Hc[j]) Hc[j] = (double2*)ctx->Hfull.p;
             e = launch_spectra(p, (float2*)ctx->Hfull.p, Hc, stream);
             ctx->launches += 1;
         }
@@ -419,8 +414,8 @@ int apx_create(apx_ctx** out, int device, size_t mem_budget_bytes) {
     c->device = device;
     c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
     DeviceGuard dg(device);
-    int rc = ensure(c, c->flags, 2 * sizeof(unsigned));
-    if (!rc) rc = cuda_status(cudaMemset(c->flags.p, 0, 2 * sizeof(unsigned)));
+    int rc = ensure(c, c->flags, 3 * sizeof(unsigned));
+    if (!rc) rc = cuda_status(cudaMemset(c->flags.p, 0, 3 * sizeof(unsigned)));
     if (rc) { apx_destroy(c); return rc; }
     *out = c;
     return APX_OK;
@@ -431,8 +426,8 @@ void apx_destroy(apx_ctx* c) {
     {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
-        DevBuf* all[] = {&c->ki, &c->kfull, &c->kbar[0], &c->kbar[1], &c->kbar[2], &c->flags, &c->sel,
-                         &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32, &c->hs, &c->hk, &c->hr};
+        DevBuf* all[] = {&c->ki, &c->flags, &c->sel, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
+                         &c->tw32, &c->hs, &c->hk, &c->hr};
         for (DevBuf* b : all) release(c, *b);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }
@@ -516,8 +511,8 @@ int apx_profile(apx_ctx* ctx, int enable) {
 int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n) {
     if (!ctx) return APX_ERR_ARG;
     DeviceGuard dg(ctx->device);
-    double acc[APX_NPHASES] = {0, 0, 0, 0, 0};
-    int64_t cnt[APX_NPHASES] = {0, 0, 0, 0, 0};
+    double acc[APX_NPHASES] = {};
+    int64_t cnt[APX_NPHASES] = {};
     for (size_t i = 0; i < ctx->ev_used; ++i) {
         cudaError_t e = cudaEventSynchronize(ctx->ev[2 * i + 1]);
         float t = 0.f;

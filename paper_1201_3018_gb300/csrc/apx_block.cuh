@@ -56,7 +56,93 @@ struct Shared {
     float redf[32];
     int redi[32];
     long long redl[32];
+    double bcast[4];
 };
+
+// Tap n of the convolution kernel: reversed for cross-correlation (reading c9),
+// zero past N (the odd-length pad of Section III).
+__device__ __forceinline__ float ktap(const Params& p, int n) {
+    return n < p.N ? __ldg(&p.k[p.xcorr ? p.N - 1 - n : n]) : 0.f;
+}
+
+// Fixed-point second-moment sum: q = trunc(x 2^sh) with ||x||_inf 2^sh in
+// [2^23, 2^24); 2^sh is applied as two exact power-of-two products.
+struct FxScale {
+    int sh;
+    float fa, fb;
+};
+__device__ __forceinline__ FxScale fx_scale(float maxabs) {
+    int e;
+    (void)frexpf(maxabs, &e);
+    FxScale f;
+    f.sh = 24 - e;
+    const int a = f.sh / 2, b = f.sh - a;
+    f.fa = __int_as_float((a + 127) << 23);
+    f.fb = __int_as_float((b + 127) << 23);
+    return f;
+}
+__device__ __forceinline__ long long fx_sq(const FxScale& f, float x) {
+    const long long q = __float2int_rz(__fmul_rn(__fmul_rn(x, f.fa), f.fb));
+    return q * q;
+}
+// sum q^2 * 2^(-2 sh) / n, one thread, broadcast through shared memory
+__device__ __forceinline__ double fx_moment(long long sum, const FxScale& f, int n, Shared& sh) {
+    if (threadIdx.x == 0) sh.bcast[0] = __ddiv_rn(ldexp(__ll2double_rn(sum), -2 * f.sh), (double)n);
+    __syncthreads();
+    const double v = sh.bcast[0];
+    __syncthreads();
+    return v;
+}
+
+struct KStats {
+    float Mk;
+    int bad;
+    double sig2k;
+};
+
+// ||k||_inf and the kernel's second moment over its N taps (block-wide).
+__device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
+    float m = 0.f;
+    int bad = 0;
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
+        const float a = fabsf(ktap(p, n));
+        if (!(a <= 3.402823466e38f)) bad = 1;
+        m = fmaxf(m, a);
+    }
+    KStats k;
+    k.Mk = block_reduce<float, true>(m, sh.redf);
+    k.bad = block_reduce<int, true>(bad, sh.redi);
+    k.sig2k = 0.0;
+    if (!k.bad && k.Mk > 0.f) {
+        const FxScale f = fx_scale(k.Mk);
+        long long acc = 0;
+        for (int n = threadIdx.x; n < p.N; n += blockDim.x) acc += fx_sq(f, ktap(p, n));
+        acc = block_reduce<long long, false>(acc, sh.redl);
+        k.sig2k = fx_moment(acc, f, p.N, sh);
+    }
+    return k;
+}
+
+// Companded tap k~[n] = rint(c_k k[n]) (Eq. 2); zero past N.
+__device__ __forceinline__ long long kq(const Params& p, float ck, int n) {
+    return n < p.N ? (long long)compand(ck, ktap(p, n)) : 0ll;
+}
+// Packed tap n of candidate c as an exact integer: symmetric (Eq. 5, reading
+// c2) k~[2n+1] + 2^b k~[2n]; asymmetric k~[n].
+__device__ __forceinline__ long long kbar_int(const Params& p, const Cand& c, float ck, int n) {
+    if (n >= c.nk) return 0ll;
+    if (c.blk == APX_BLK_SYM) return kq(p, ck, 2 * n + 1) + (kq(p, ck, 2 * n) << c.b);
+    return kq(p, ck, n);
+}
+// ||kbar||_1, exact (block-wide).
+__device__ inline long long kbar_l1(const Params& p, const Cand& c, float ck, Shared& sh) {
+    long long l1 = 0;
+    for (int n = threadIdx.x; n < c.nk; n += blockDim.x) {
+        const long long v = kbar_int(p, c, ck, n);
+        l1 += v < 0 ? -v : v;
+    }
+    return block_reduce<long long, false>(l1, sh.redl);
+}
 
 // Fill every kept output of the block with `v` (zero block or non-finite).
 __device__ __forceinline__ void store_constant(const Params& p, const BlockGeom& g, float v) {
@@ -91,14 +177,17 @@ struct Pro {
     double sig2;
 };
 
-__device__ __forceinline__ Pro block_prologue(const Params& p, const float* xs, Shared& sh) {
+__device__ __forceinline__ Pro block_prologue(const Params& p, const float* xs, const KStats& ks, Shared& sh) {
     Pro r;
     r.Ms = block_maxabs(xs, p.Wb, sh.redf, sh.redi);
     r.sig2 = 0.0;
-    const KInfo& ki = *p.ki;
-    if (!(r.Ms <= 3.402823466e38f) || ki.nonfinite) { r.kind = 3; return r; }  // NaN or inf
-    if (r.Ms == 0.f || ki.Mk == 0.f) { r.kind = 2; return r; }
-    r.sig2 = block_second_moment(xs, p.Wb, r.Ms, sh.redl);
+    if (!(r.Ms <= 3.402823466e38f) || ks.bad) { r.kind = 3; return r; }  // NaN or inf
+    if (r.Ms == 0.f || ks.Mk == 0.f) { r.kind = 2; return r; }
+    const FxScale f = fx_scale(r.Ms);
+    long long acc = 0;
+    for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) acc += fx_sq(f, xs[t]);
+    acc = block_reduce<long long, false>(acc, sh.redl);
+    r.sig2 = fx_moment(acc, f, p.Wb, sh);
     r.kind = 0;
     return r;
 }

@@ -1,11 +1,12 @@
 // apx_direct.cu -- fused per-block kernel of the time-domain (direct) core.
 //
-// One CTA per overlap-save block: load the W_block window, block statistics,
-// Section IV.D selection, companding (Eq. 2), packing (Eqs. 4 / 7) into shared
-// memory, the packed FP64 convolution (Eqs. 8-9) with a register sliding
-// window, digit extraction (Eqs. 11-15), inverse companding (Eq. 16) and the
-// Eq. (17) store.  Blocks without an admissible packing run the FP32 full
-// precision convolution in the same CTA.
+// One launch per call, one CTA per overlap-save block: load the W_block window,
+// kernel and block statistics, Section IV.D selection, companding (Eq. 2) and
+// packing (Eqs. 4, 5, 7) of block and taps into shared memory, the packed FP64
+// convolution (Eqs. 8-9) with a register sliding window, digit extraction
+// (Eqs. 11-15), inverse companding (Eq. 16) and the Eq. (17) store.  Blocks
+// without an admissible packing run the FP32 full-precision convolution in the
+// same CTA.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
@@ -14,11 +15,11 @@ namespace apx {
 constexpr int kRf = 8;  // FP32 outputs per thread (taps padded to a multiple of 8)
 constexpr int kRd = 4;  // FP64 outputs per thread (taps padded to a multiple of 4)
 
-// acc[r] = sum_{n < nkp} sig[j0 + r - n] taps[n]; sig is zero-padded by >= nkp
-// in front.  Register ring: slot (t mod R) holds sig[j0 + t - n].
+// acc[r] = sum_{n < nkp} sig[j0 + r - n] taps[n] with signal and taps in shared
+// memory; sig is zero-padded by >= nkp in front.  Register ring: slot (t mod R)
+// holds sig[j0 + t - n].
 template <int R>
-__device__ __forceinline__ void conv_f32(const float* sig, const float* __restrict__ taps, int nkp, int j0,
-                                         float (&acc)[R]) {
+__device__ __forceinline__ void conv_f32(const float* sig, const float* taps, int nkp, int j0, float (&acc)[R]) {
     float w[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc[r] = 0.f; w[r] = sig[j0 + r]; }
@@ -26,7 +27,7 @@ __device__ __forceinline__ void conv_f32(const float* sig, const float* __restri
         float t[R];
 #pragma unroll
         for (int v = 0; v < R; v += 4) {
-            float4 q = __ldg(reinterpret_cast<const float4*>(taps + n + v));
+            float4 q = *reinterpret_cast<const float4*>(taps + n + v);
             t[v] = q.x; t[v + 1] = q.y; t[v + 2] = q.z; t[v + 3] = q.w;
         }
 #pragma unroll
@@ -39,8 +40,7 @@ __device__ __forceinline__ void conv_f32(const float* sig, const float* __restri
 }
 
 template <int R>
-__device__ __forceinline__ void conv_f64(const double* sig, const double* __restrict__ taps, int nkp, int j0,
-                                         double (&acc)[R]) {
+__device__ __forceinline__ void conv_f64(const double* sig, const double* taps, int nkp, int j0, double (&acc)[R]) {
     double w[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc[r] = 0.0; w[r] = sig[j0 + r]; }
@@ -48,7 +48,7 @@ __device__ __forceinline__ void conv_f64(const double* sig, const double* __rest
         double t[R];
 #pragma unroll
         for (int v = 0; v < R; v += 2) {
-            double2 q = __ldg(reinterpret_cast<const double2*>(taps + n + v));
+            double2 q = *reinterpret_cast<const double2*>(taps + n + v);
             t[v] = q.x; t[v + 1] = q.y;
         }
 #pragma unroll
@@ -65,6 +65,7 @@ __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m *
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
+    __shared__ int s_ci;
     const long long i = blockIdx.x;
     const BlockGeom g = block_geom(p, i);
     const DirectLayout& dl = p.dl;
@@ -74,29 +75,36 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
     for (int t = threadIdx.x; t < kRf; t += blockDim.x) xs[p.Wb + t] = 0.f;
     load_window(p, g, xs);
 
-    pdl_wait();  // packed taps and kernel statistics from the preparation launch
-    const Pro pr = block_prologue(p, xs, sh);
+    // Kernel initialisation of Section IV, done by every CTA from the raw taps.
+    const KStats ks = kernel_stats(p, sh);
+    const Pro pr = block_prologue(p, xs, ks, sh);
     if (pr.kind != 0) { handle_trivial(p, i, g, pr); return; }
 
     // Section IV.D: first candidate (in the Table 1 order) whose model SNR meets
     // the target; with a fixed quantiser the single candidate is taken.
-    const KInfo& ki = *p.ki;
-    int ci = -1;
-    for (int c = 0; c < p.ncand; ++c) {
-        if (!p.autosel || snr_feasible(pr.sig2, pr.Ms, ki.sig2k, ki.Mk, p.cand[c].S, p.cand[c].K, p.thr)) {
-            ci = c;
-            break;
-        }
+    if (threadIdx.x == 0) {
+        int ci = -1;
+        for (int c = 0; c < p.ncand; ++c)
+            if (!p.autosel || snr_feasible(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, p.cand[c].S, p.cand[c].K, p.thr)) {
+                ci = c;
+                break;
+            }
+        s_ci = ci;
     }
+    __syncthreads();
+    const int ci = s_ci;
 
     if (ci < 0) {
-        // Full precision (FP32), Eq. (1) over the window.
+        // Full precision (FP32), Eq. (1) over the window, taps staged in shared memory.
         const int nkp = round_up(p.Nodd, kRf);
+        float* kf = reinterpret_cast<float*>(smem + dl.offK);
+        for (int n = threadIdx.x; n < nkp; n += blockDim.x) kf[n] = ktap(p, n);
+        __syncthreads();
         const int nout = g.hi - g.lo;
         for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
             const int j0 = g.lo + ch * kRf;
             float acc[kRf];
-            conv_f32<kRf>(xs, p.kfull, nkp, j0, acc);
+            conv_f32<kRf>(xs, kf, nkp, j0, acc);
 #pragma unroll
             for (int r = 0; r < kRf; ++r) {
                 const int j = j0 + r;
@@ -113,10 +121,13 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
 
     const Cand& c = p.cand[ci];
     const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
+    const float ck = compand_factor(c.K, ks.Mk);
     const double eps = ldexp(1.0, -c.b);
     double* sb = reinterpret_cast<double*>(smem + dl.offS) + dl.padS;
     double* tb = reinterpret_cast<double*>(smem + dl.offT);
+    double* kb = reinterpret_cast<double*>(smem + dl.offKb);
     const int nkp = round_up(c.nk, kRd);
+    for (int n = threadIdx.x; n < nkp; n += blockDim.x) kb[n] = (double)kbar_int(p, c, ck, n);  // Eq. (5) / k~
     int nsb, Ls = 0;
     if (c.blk == APX_BLK_SYM) {
         nsb = p.Wb / 2;
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
     for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
         const int j0 = olo + ch * kRd;
         double acc[kRd];
-        conv_f64<kRd>(sb, c.kbar, nkp, j0, acc);
+        conv_f64<kRd>(sb, kb, nkp, j0, acc);
 #pragma unroll
         for (int r = 0; r < kRd; ++r)
             if (j0 + r < ohi) tb[j0 + r] = acc[r];
@@ -162,7 +173,9 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
     __syncthreads();
 
     // Unpack, inverse compand (Eq. 16), place (Eq. 17).
-    const float inv = (float)(1.0 / ((double)cs * (double)ki.ck[ci]));
+    if (threadIdx.x == 0) sh.bcast[0] = 1.0 / ((double)cs * (double)ck);
+    __syncthreads();
+    const float inv = (float)sh.bcast[0];
     auto Tat = [&](int m) { return scaled(tb[m], c.sc); };
     for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
         if (p.rq) p.rq[o] = (int)rt;
     }
     if (threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ki.sig2k, ki.Mk, c.S, c.K), 0.0);
+        write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
@@ -185,7 +198,7 @@ cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
         attr_dev = dev;
     }
     if (p.P <= 0) return cudaSuccess;
-    return launch_k(k_direct, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, true, p);
+    return launch_k(k_direct, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p);
 }
 
 }  // namespace apx

@@ -1,17 +1,18 @@
 // apx_fft.cu -- the frequency-domain (FFT) core.
 //
-// k_select (one CTA per block): window statistics and the Section IV.D
-// selection; for a packing candidate it also companded the block and checks
-// the FFT error bound (reading c7) with the exact integer norm sum(s~^2), so
-// that rounding recovers the packed digits exactly.
-// k_spectra (apx_prep.cu): kernel spectra of the candidates in use.
+// k_select (one CTA per block): kernel and window statistics and the Section
+// IV.D selection; for a packing candidate it also companded the block and
+// checks the FFT error bound (reading c7) with the exact integer norms
+// sum(s~^2) and ||kbar||_1, so that rounding recovers the packed digits.
+// k_spectra (apx_spectra.cu): kernel spectra; the FP32 one runs concurrently
+// with k_select, the packed ones only for candidates some block selected.
 // k_fft (one CTA per block): compand + pack into a complex buffer (two real
 // words per complex entry), forward real FFT, product with the kernel
 // spectrum, inverse FFT, digit extraction, inverse companding, store.
 //
-// Each kernel is launched as a programmatic dependent of the previous one: the
-// window is fetched into registers before griddepcontrol.wait, so the load
-// overlaps the tail of the previous kernel.
+// k_spectra and k_fft are programmatic dependents of the kernel before them:
+// k_fft fetches its window into registers before griddepcontrol.wait, so the
+// load overlaps the spectra.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
@@ -45,9 +46,10 @@ __device__ __forceinline__ void load_window_regs(const Params& p, long long star
     }
 }
 
-__global__ void __launch_bounds__(512) k_select(const Params p) {
+__global__ void __launch_bounds__(512, 1) k_select(const Params p) {
     __shared__ Shared sh;
-    pdl_trigger();
+    __shared__ int s_go;
+    pdl_trigger();  // the spectrum of the FP32 taps needs nothing from this pass
     const long long i = blockIdx.x;
     const BlockGeom g = block_geom(p, i);
     float xv[kVals];
@@ -64,36 +66,44 @@ __global__ void __launch_bounds__(512) k_select(const Params p) {
     }
     m = block_reduce<float, true>(m, sh.redf);
     bad = block_reduce<int, true>(bad, sh.redi);
-    Sel s;
-    s.cs = 0.f; s.Ms = bad ? __int_as_float(0x7fc00000) : m; s.sig2 = 0.0; s.ferr = 0.0; s.pad_ = 0;
     const bool finite = !bad && m <= 3.402823466e38f;
     double sig2 = 0.0;
     if (finite && m > 0.f) {
-        int e;
-        (void)frexpf(m, &e);
-        const int sh2 = 24 - e, a = sh2 / 2, b = sh2 - a;
-        const float fa = __int_as_float((a + 127) << 23), fb = __int_as_float((b + 127) << 23);
+        const FxScale f = fx_scale(m);
         long long acc = 0;
 #pragma unroll
-        for (int v = 0; v < kVals; ++v) {
-            const long long q = __float2int_rz(__fmul_rn(__fmul_rn(xv[v], fa), fb));
-            acc += q * q;
-        }
+        for (int v = 0; v < kVals; ++v) acc += fx_sq(f, xv[v]);
         acc = block_reduce<long long, false>(acc, sh.redl);
-        sig2 = __ddiv_rn(ldexp(__ll2double_rn(acc), -2 * sh2), (double)p.Wb);
+        sig2 = fx_moment(acc, f, p.Wb, sh);
     }
-    s.sig2 = sig2;
+    // Kernel initialisation of Section IV, from the raw taps in every CTA.
+    const KStats ks = kernel_stats(p, sh);
+    if (i == 0 && threadIdx.x == 0) {
+        KInfo o;
+        o.Mk = ks.Mk;
+        o.nonfinite = ks.bad;
+        o.sig2k = ks.sig2k;
+        *p.ki = o;
+    }
 
-    pdl_wait();  // kernel statistics from the preparation launch
-    const KInfo& ki = *p.ki;
-    if (!finite || ki.nonfinite) s.ci = -3;
-    else if (m == 0.f || ki.Mk == 0.f) s.ci = -2;
+    Sel s;
+    s.cs = 0.f; s.Ms = bad ? __int_as_float(0x7fc00000) : m; s.inv = 0.f;
+    s.sig2 = sig2; s.ferr = 0.0; s.snr_db = __longlong_as_double(0x7ff0000000000000ll);
+    if (!finite || ks.bad) s.ci = -3;
+    else if (m == 0.f || ks.Mk == 0.f) s.ci = -2;
     else {
         s.ci = -1;
         for (int c = 0; c < p.ncand; ++c) {
             const Cand& cd = p.cand[c];
-            if (p.autosel && !snr_feasible(sig2, m, ki.sig2k, ki.Mk, cd.S, cd.K, p.thr)) continue;
+            if (threadIdx.x == 0)
+                s_go = !p.autosel || snr_feasible(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K, p.thr);
+            __syncthreads();
+            const int go = s_go;
+            __syncthreads();
+            if (!go) continue;
+            // FFT exactness (reading c7) with the exact norms of this block and kernel
             const float cs = compand_factor(cd.S, m);
+            const float ck = compand_factor(cd.K, ks.Mk);
             long long ss = 0;
 #pragma unroll
             for (int v = 0; v < kVals; ++v) {
@@ -101,14 +111,23 @@ __global__ void __launch_bounds__(512) k_select(const Params p) {
                 ss += q * q;
             }
             ss = block_reduce<long long, false>(ss, sh.redl);
-            const double eps = ldexp(1.0, -cd.b);
-            const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
-            const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
-            const double E = ldexp(__dmul_rn(__dmul_rn(cd.fftc, ki.l1[c]), l2), cd.sc);
+            const long long l1 = kbar_l1(p, cd, ck, sh);
+            if (threadIdx.x == 0) {
+                const double eps = ldexp(1.0, -cd.b);
+                const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
+                const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
+                const double E = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ll2double_rn(l1)), l2), cd.sc);
+                sh.bcast[1] = E;
+                sh.bcast[2] = 1.0 / ((double)cs * (double)ck);
+            }
+            __syncthreads();
+            const double E = sh.bcast[1];
             if (E < 0.25) {
-                s.ci = c; s.cs = cs; s.ferr = E;
+                s.ci = c; s.cs = cs; s.ferr = E; s.inv = (float)sh.bcast[2];
+                if (threadIdx.x == 0) s.snr_db = snr_model_db(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K);
                 break;
             }
+            __syncthreads();
         }
     }
     if (threadIdx.x == 0) {
@@ -209,8 +228,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
     spectral_multiply(Z, m, c.H, p.tw64, p.Wb / n);
     fft_smem<double2, true>(Z, m, p.tw64, p.Wb);
 
-    const KInfo& ki = *p.ki;
-    const float inv = (float)(1.0 / ((double)cs * (double)ki.ck[s.ci]));
+    const float inv = s.inv;
     auto Tat = [&](int idx) { return scaled(word<double>(Z, idx), c.sc); };
     for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
@@ -220,12 +238,12 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         if (p.rq) p.rq[o] = (int)rt;
     }
     if (threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, s.Ms, s.sig2, snr_model_db(s.sig2, s.Ms, ki.sig2k, ki.Mk, c.S, c.K), s.ferr);
+        write_stats(p, i, c.blk, &c, cs, s.Ms, s.sig2, s.snr_db, s.ferr);
 }
 
 cudaError_t launch_select(const Params& p, cudaStream_t st) {
     if (p.P <= 0) return cudaSuccess;
-    return launch_k(k_select, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), 0, st, true, p);
+    return launch_k(k_select, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), 0, st, false, p);
 }
 
 size_t fft_smem_bytes(const Params& p) {

@@ -17,8 +17,7 @@ namespace apx {
 constexpr int kMaxWblock = 16384;
 constexpr int kMaxCand = 3;
 
-// One packing candidate.  Static part set by the host from (N', W_block);
-// dynamic part (c_k, ||kbar||_1) written by the kernel-preparation launch.
+// One packing candidate (set by the host from N' and W_block).
 struct Cand {
     int blk;          // APX_BLK_SYM / ASYM2 / ASYM3
     int M;            // 1 for symmetric, 2 or 3 for asymmetric
@@ -28,26 +27,25 @@ struct Cand {
     int nk;           // packed taps: (N'+1)/2 (sym) or N' (asym)
     int log2n;        // FFT core: log2 of the real transform length
     double fftc;      // FFT core: (3 phi + 16 u) for log2n (error-bound constant)
-    const double* kbar;   // packed taps in the workspace
-    const double2* H;     // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries
+    const double2* H; // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries
 };
 
-// Kernel statistics written by the preparation launch.
+// Kernel statistics; every CTA derives them from the raw taps (the same bits
+// everywhere), and the FFT core's first CTA also publishes them here.
 struct KInfo {
     float Mk;         // ||k||_inf
     int nonfinite;    // kernel has NaN/Inf
     double sig2k;     // second moment of the kernel (24-bit fixed point)
-    float ck[kMaxCand];
-    float pad_;
-    double l1[kMaxCand];  // ||kbar||_1, exact integer
 };
 
 // Shared-memory layout of the direct kernel (byte offsets; element pads).
 struct DirectLayout {
     int padF;         // zero floats in front of the window
+    int offK;         // FP32 taps: byte offset (nkp32 floats)
     int offS, padS;   // packed-signal buffer: byte offset, zero doubles in front
     int nS;           // packed-signal buffer length in doubles (pads included)
     int offT;         // packed-output buffer: byte offset
+    int offKb;        // packed taps: byte offset
 };
 
 // Per-block decision of the FFT core's selection pass.
@@ -55,32 +53,34 @@ struct Sel {
     int ci;           // candidate index, -1: full precision, -2 zero block, -3 non-finite
     float cs;         // c_s of the chosen candidate
     float Ms;         // ||s||_inf of the window
-    int pad_;
+    float inv;        // 1 / (c_s c_k) as FP32 (Eq. 16)
     double sig2;      // second moment of the window
     double ferr;      // FFT error bound in digits of the chosen candidate
+    double snr_db;    // model SNR of the chosen candidate
 };
 
 struct Params {
     const float* s;       // input, L samples
     long long L;
-    int N, Nodd, Wb, W, head, fft;
+    const float* k;       // kernel taps as given (the template for cross-correlation)
+    int N, Nodd, Wb, W, head, fft, xcorr;
     long long P, out_len;
     float* r;             // output, out_len
     int* rq;              // integer-domain output or null
     apx_block_stats* st;  // per-block stats or null
-    const float* kfull;   // FP32 taps (reversed for xcorr), N' entries
     const float2* Hfull;  // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
     const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
     const float2* tw32;
-    const KInfo* ki;
+    KInfo* ki;            // FFT core: kernel statistics published by CTA 0 of the selection pass
     unsigned* status;     // bit 0: non-finite input seen
+    unsigned* used;       // FFT core: bit c set when candidate c is used, bit 3 for full precision
+    unsigned* used_next;  // the other slot, cleared for the next call
     int autosel;          // 1: per-block selection under thr
     int ncand;
     double thr;           // 10^(target/10)
     Cand cand[kMaxCand];
     DirectLayout dl;      // direct core
     Sel* sel;             // FFT core: per-block decisions (P entries)
-    unsigned* used;       // FFT core: bit c set when candidate c is used, bit 3 for full precision
 };
 
 // ------------------------------------------------------------------ reductions
@@ -129,20 +129,6 @@ __device__ inline float block_maxabs(const float* x, int n, float* redf, int* re
     m = block_reduce<float, true>(m, redf);
     bad = block_reduce<int, true>(bad, redi);
     return bad ? __int_as_float(0x7fc00000) : m;
-}
-
-// Second moment in 24-bit fixed point relative to ||x||_inf (exact integer sum).
-__device__ inline double block_second_moment(const float* x, int n, float maxabs, long long* redl) {
-    int e;
-    (void)frexpf(maxabs, &e);
-    const int sh = 24 - e;
-    long long acc = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        long long q = __float2ll_rz(ldexpf(x[i], sh));
-        acc += q * q;
-    }
-    acc = block_reduce<long long, false>(acc, redl);
-    return __ddiv_rn(ldexp(__ll2double_rn(acc), -2 * sh), (double)n);
 }
 
 // Table 1 model (derived from Eqs. 18-19), one IEEE operation at a time:
