@@ -136,7 +136,8 @@ int apx_conv_host(apx_ctx* ctx, const float* s_in_host, int64_t L, const float* 
                   float* r_out_host, void* stream);
 
 /* Wait for `stream` and return the data-dependent status of the calls issued
- * since the previous apx_sync (APX_OK or APX_ERR_NONFINITE), then clear it. */
+ * since the previous apx_sync (APX_OK, APX_ERR_NONFINITE, or APX_ERR_TIMEOUT when
+ * a bounded device-side wait gave up), then clear it. */
 int apx_sync(apx_ctx* ctx, void* stream);
 
 /* Number of CUDA kernel launches this context has issued since creation. */
@@ -148,11 +149,10 @@ int64_t apx_launch_count(const apx_ctx* ctx);
  * for the recorded events, writes the summed milliseconds and the launch count
  * per kernel kind (APX_PHASE_*) into ms[APX_NPHASES] and n[APX_NPHASES] (either
  * may be NULL), and clears the record.  Errors: APX_ERR_ARG, APX_ERR_CUDA. */
-#define APX_PHASE_DIRECT  0   /* direct core: the single fused block kernel            */
-#define APX_PHASE_SELECT  1   /* FFT core: kernel and block statistics, selection     */
-#define APX_PHASE_SPECTRA 2   /* FFT core: kernel spectra (FP32, and packings in use) */
-#define APX_PHASE_FFT     3   /* FFT core: block kernel                               */
-#define APX_NPHASES       4
+#define APX_PHASE_DIRECT  0   /* direct core: the single fused block kernel        */
+#define APX_PHASE_SPECTRA 1   /* FFT core: FP32 kernel spectrum (direct DFT)       */
+#define APX_PHASE_FFT     2   /* FFT core: block kernel (packed spectra on demand) */
+#define APX_NPHASES       3
 int apx_profile(apx_ctx* ctx, int enable);
 int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
 

@@ -46,7 +46,7 @@ SIGNATURES = {
     "apx_profile": (C.c_int, [_vp, C.c_int]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
 }
-PHASES = ("direct", "select", "spectra", "fft")
+PHASES = ("direct", "spectra", "fft")
 
 
 class ApxError(RuntimeError):

@@ -23,14 +23,16 @@ struct DevBuf {
 
 }  // namespace
 
+constexpr int kFlagWords = 1 + 2 * kMaxCand;  // status, claim[3], ready[3]
+
 struct apx_ctx {
     int device = 0;
     size_t budget = 0;
     size_t in_use = 0;
     int64_t launches = 0;
-    DevBuf ki, flags, sel, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    DevBuf flags, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     int tw_wb = 0;          // W_block the twiddle tables were built for
-    int64_t fft_calls = 0;  // selects the `used` slot of an FFT-core call
+    unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     // tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;          // event pool, pairs
@@ -347,28 +349,23 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     p.ncand = nc;
     if (pl.fft) smem = fft_smem_bytes(p);
 
-    // Workspace.
-    rc = ensure(ctx, ctx->flags, 3 * sizeof(unsigned));
+    // Workspace: status word, per-candidate claim and ready words, spectra, twiddles.
+    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
     if (!rc && pl.fft) {
         const size_t m1 = (size_t)Wb / 2 + 1;
-        rc = ensure(ctx, ctx->ki, sizeof(KInfo));
-        if (!rc) rc = ensure(ctx, ctx->sel, sizeof(Sel) * pl.P);
-        if (!rc) rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
+        rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
         for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->Hc[j], sizeof(double2) * m1);
         if (!rc) rc = ensure_twiddles(ctx, Wb, stream);
     }
     if (rc) return rc;
 
-    for (int j = 0; j < nc; ++j) p.cand[j].H = (const double2*)ctx->Hc[j].p;
+    for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
     p.k = k;
     p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
-    p.ki = (KInfo*)ctx->ki.p;
     p.status = (unsigned*)ctx->flags.p;
-    const int slot = (int)(ctx->fft_calls & 1);
-    p.used = (unsigned*)ctx->flags.p + 1 + slot;
-    p.used_next = (unsigned*)ctx->flags.p + 2 - slot;
-    p.sel = (Sel*)ctx->sel.p;
-    p.Hfull = (const float2*)ctx->Hfull.p;
+    p.claim = (unsigned*)ctx->flags.p + 1;
+    p.ready = (unsigned*)ctx->flags.p + 1 + kMaxCand;
+    p.Hfull = (float2*)ctx->Hfull.p;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
 
@@ -378,16 +375,11 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         e = launch_direct(p, smem, stream);
         ctx->launches += 1;
     } else {
-        ctx->fft_calls += 1;
+        if (++ctx->epoch == 0) ctx->epoch = 1;  // 0 marks "never"
+        p.epoch = ctx->epoch;
         {
-            Trace t(ctx, stream, APX_PHASE_SELECT);
-            e = launch_select(p, stream);
-            ctx->launches += 1;
-        }
-        if (e == cudaSuccess) {
             Trace t(ctx, stream, APX_PHASE_SPECTRA);
-            double2* Hc[kMaxCand] = {(double2*)ctx->Hc[0].p, (double2*)ctx->Hc[1].p, (double2*)ctx->Hc[2].p};
-            e = launch_spectra(p, (float2*)ctx->Hfull.p, Hc, stream);
+            e = launch_spec(p, stream);
             ctx->launches += 1;
         }
         if (e == cudaSuccess) {
@@ -414,8 +406,8 @@ int apx_create(apx_ctx** out, int device, size_t mem_budget_bytes) {
     c->device = device;
     c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
     DeviceGuard dg(device);
-    int rc = ensure(c, c->flags, 3 * sizeof(unsigned));
-    if (!rc) rc = cuda_status(cudaMemset(c->flags.p, 0, 3 * sizeof(unsigned)));
+    int rc = ensure(c, c->flags, kFlagWords * sizeof(unsigned));
+    if (!rc) rc = cuda_status(cudaMemset(c->flags.p, 0, kFlagWords * sizeof(unsigned)));
     if (rc) { apx_destroy(c); return rc; }
     *out = c;
     return APX_OK;
@@ -426,8 +418,8 @@ void apx_destroy(apx_ctx* c) {
     {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
-        DevBuf* all[] = {&c->ki, &c->flags, &c->sel, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
-                         &c->tw32, &c->hs, &c->hk, &c->hr};
+        DevBuf* all[] = {&c->flags, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32, &c->hs,
+                         &c->hk, &c->hr};
         for (DevBuf* b : all) release(c, *b);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }
@@ -472,6 +464,7 @@ int apx_sync(apx_ctx* ctx, void* stream) {
     if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->flags.p, 0, sizeof(unsigned), st);
     if (e == cudaSuccess && h) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
+    if (h & 2u) return APX_ERR_TIMEOUT;
     return (h & 1u) ? APX_ERR_NONFINITE : APX_OK;
 }
 

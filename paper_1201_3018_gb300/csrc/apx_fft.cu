@@ -1,24 +1,29 @@
-// apx_fft.cu -- the frequency-domain (FFT) core.
+// apx_fft.cu -- the frequency-domain (FFT) block kernel.
 //
-// k_select (one CTA per block): kernel and window statistics and the Section
-// IV.D selection; for a packing candidate it also companded the block and
-// checks the FFT error bound (reading c7) with the exact integer norms
-// sum(s~^2) and ||kbar||_1, so that rounding recovers the packed digits.
-// k_spectra (apx_spectra.cu): kernel spectra; the FP32 one runs concurrently
-// with k_select, the packed ones only for candidates some block selected.
-// k_fft (one CTA per block): compand + pack into a complex buffer (two real
-// words per complex entry), forward real FFT, product with the kernel
-// spectrum, inverse FFT, digit extraction, inverse companding, store.
-//
-// k_spectra and k_fft are programmatic dependents of the kernel before them:
-// k_fft fetches its window into registers before griddepcontrol.wait, so the
-// load overlaps the spectra.
+// One CTA per overlap-save block, launched as the programmatic dependent of
+// k_spec (the FP32 kernel spectrum).  Each CTA:
+//   1. fetches its W_block window into registers,
+//   2. derives the kernel statistics from the raw taps and the block
+//      statistics from the window (identical bits in every CTA),
+//   3. runs the Section IV.D selection; for a packing candidate it companded
+//      the block and checks the FFT error bound (reading c7) with the exact
+//      integer norms sum(s~^2) and ||kbar||_1, so rounding recovers the digits,
+//   4. companded and packs (Eqs. 2, 4, 7) into a complex buffer (two real words
+//      per complex entry) and runs the forward real FFT,
+//   5. waits for the kernel spectrum, multiplies, runs the inverse FFT,
+//   6. extracts the digits (Eqs. 11-15), inverse-companded (Eq. 16), stores
+//      (Eq. 17).
+// The FP32 spectrum comes from k_spec (griddepcontrol.wait).  A packed
+// candidate's FP64 spectrum is built on demand by the first CTA that selects
+// it; later CTAs wait for it with a bounded spin and report a timeout in the
+// status word instead of hanging.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
 namespace apx {
 
 constexpr int kVals = 32;  // window samples per thread (W_block / threads)
+constexpr int kSpinLimit = 1 << 22;
 
 // Thread t holds window samples 2(t + i NT) and 2(t + i NT) + 1 (pair t + i NT)
 // for pairs below W_block/2; other slots hold zeros, which leave the maximum,
@@ -46,10 +51,46 @@ __device__ __forceinline__ void load_window_regs(const Params& p, long long star
     }
 }
 
-__global__ void __launch_bounds__(512, 1) k_select(const Params p) {
+// real word w of a padded complex buffer
+template <typename R, typename C>
+__device__ __forceinline__ R& word(C* Z, int w) {
+    return reinterpret_cast<R*>(Z)[2 * pad16(w >> 1) + (w & 1)];
+}
+
+// H = FFT_n(taps) / (4m), k in [0, m], natural order, through the block FFT;
+// tap(j) gives tap j.  Z is scratch of padded_len(n/2) entries.
+template <typename R, typename C, typename F>
+__device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H, C* Z) {
+    const int m = n / 2;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        C v;
+        v.x = tap(2 * j);
+        v.y = tap(2 * j + 1);
+        Z[pad16(j)] = v;
+    }
+    __syncthreads();
+    fft_smem<C, false>(Z, m, tw, Wb);
+    const R scale = (R)1 / (R)(8 * m);
+    for (int k = threadIdx.x; k <= m; k += blockDim.x) {
+        C X;
+        if (k == 0 || k == m) {
+            const C z0 = Z[0];
+            X.x = 2 * (k == 0 ? z0.x + z0.y : z0.x - z0.y);
+            X.y = 0;
+        } else {
+            C Xmk;
+            real_post(Z[pad16(fft_perm(k, m))], Z[pad16(fft_perm(m - k, m))], __ldg(&tw[k * (Wb / n)]), X, Xmk);
+        }
+        X.x *= scale; X.y *= scale;
+        H[k] = X;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_fft(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
-    __shared__ int s_go;
-    pdl_trigger();  // the spectrum of the FP32 taps needs nothing from this pass
+    __shared__ int s_flag;
     const long long i = blockIdx.x;
     const BlockGeom g = block_geom(p, i);
     float xv[kVals];
@@ -78,117 +119,100 @@ __global__ void __launch_bounds__(512, 1) k_select(const Params p) {
     }
     // Kernel initialisation of Section IV, from the raw taps in every CTA.
     const KStats ks = kernel_stats(p, sh);
-    if (i == 0 && threadIdx.x == 0) {
-        KInfo o;
-        o.Mk = ks.Mk;
-        o.nonfinite = ks.bad;
-        o.sig2k = ks.sig2k;
-        *p.ki = o;
-    }
-
-    Sel s;
-    s.cs = 0.f; s.Ms = bad ? __int_as_float(0x7fc00000) : m; s.inv = 0.f;
-    s.sig2 = sig2; s.ferr = 0.0; s.snr_db = __longlong_as_double(0x7ff0000000000000ll);
-    if (!finite || ks.bad) s.ci = -3;
-    else if (m == 0.f || ks.Mk == 0.f) s.ci = -2;
-    else {
-        s.ci = -1;
-        for (int c = 0; c < p.ncand; ++c) {
-            const Cand& cd = p.cand[c];
-            if (threadIdx.x == 0)
-                s_go = !p.autosel || snr_feasible(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K, p.thr);
-            __syncthreads();
-            const int go = s_go;
-            __syncthreads();
-            if (!go) continue;
-            // FFT exactness (reading c7) with the exact norms of this block and kernel
-            const float cs = compand_factor(cd.S, m);
-            const float ck = compand_factor(cd.K, ks.Mk);
-            long long ss = 0;
-#pragma unroll
-            for (int v = 0; v < kVals; ++v) {
-                const long long q = compand(cs, xv[v]);
-                ss += q * q;
-            }
-            ss = block_reduce<long long, false>(ss, sh.redl);
-            const long long l1 = kbar_l1(p, cd, ck, sh);
-            if (threadIdx.x == 0) {
-                const double eps = ldexp(1.0, -cd.b);
-                const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
-                const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
-                const double E = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ll2double_rn(l1)), l2), cd.sc);
-                sh.bcast[1] = E;
-                sh.bcast[2] = 1.0 / ((double)cs * (double)ck);
-            }
-            __syncthreads();
-            const double E = sh.bcast[1];
-            if (E < 0.25) {
-                s.ci = c; s.cs = cs; s.ferr = E; s.inv = (float)sh.bcast[2];
-                if (threadIdx.x == 0) s.snr_db = snr_model_db(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K);
-                break;
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x == 0) {
-        p.sel[i] = s;
-        if (s.ci >= -1) atomicOr(p.used, s.ci >= 0 ? (1u << s.ci) : 8u);
-    }
-}
-
-// real word w of a padded complex buffer
-template <typename R, typename C>
-__device__ __forceinline__ R& word(C* Z, int w) {
-    return reinterpret_cast<R*>(Z)[2 * pad16(w >> 1) + (w & 1)];
-}
-
-__global__ void __launch_bounds__(512) k_fft(const Params p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const long long i = blockIdx.x;
-    const BlockGeom g = block_geom(p, i);
-    float xv[kVals];
-    load_window_regs(p, g.start, xv);
-
-    pdl_wait();  // spectra (and, through it, the selection) complete
-    const Sel s = p.sel[i];
-    if (s.ci <= -2) {
+    const float Ms = bad ? __int_as_float(0x7fc00000) : m;
+    if (!finite || ks.bad || m == 0.f || ks.Mk == 0.f) {
         Pro pr;
-        pr.kind = s.ci == -3 ? 3 : 2;
-        pr.Ms = s.Ms;
+        pr.kind = (!finite || ks.bad) ? 3 : 2;
+        pr.Ms = Ms;
         pr.sig2 = 0.0;
         handle_trivial(p, i, g, pr);
         return;
     }
 
-    if (s.ci < 0) {
+    // Section IV.D selection (first admissible candidate in the Table 1 order).
+    int ci = -1;
+    float cs = 0.f, ck = 0.f;
+    double ferr = 0.0;
+    for (int c = 0; c < p.ncand; ++c) {
+        const Cand& cd = p.cand[c];
+        if (threadIdx.x == 0) s_flag = !p.autosel || snr_feasible(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K, p.thr);
+        __syncthreads();
+        const int go = s_flag;
+        __syncthreads();
+        if (!go) continue;
+        const float cs_c = compand_factor(cd.S, m);
+        const float ck_c = compand_factor(cd.K, ks.Mk);
+        long long ss = 0;
+#pragma unroll
+        for (int v = 0; v < kVals; ++v) {
+            const long long q = compand(cs_c, xv[v]);
+            ss += q * q;
+        }
+        ss = block_reduce<long long, false>(ss, sh.redl);
+        const long long l1 = kbar_l1(p, cd, ck_c, sh);
+        if (threadIdx.x == 0) {
+            const double eps = ldexp(1.0, -cd.b);
+            const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
+            const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
+            sh.bcast[1] = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ll2double_rn(l1)), l2), cd.sc);
+        }
+        __syncthreads();
+        const double E = sh.bcast[1];
+        __syncthreads();
+        if (E < 0.25) {
+            ci = c; cs = cs_c; ck = ck_c; ferr = E;
+            break;
+        }
+    }
+
+    if (ci < 0) {
         // Full precision: real FFT of length W_block in FP32.
-        const int m = p.Wb / 2;
+        const int mm = p.Wb / 2;
         float2* Z = reinterpret_cast<float2*>(smem);
 #pragma unroll
         for (int v = 0; v < kVals / 2; ++v)
             if (pair_ok(p, v)) Z[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
         __syncthreads();
-        fft_smem<float2, false>(Z, m, p.tw32, p.Wb);
-        spectral_multiply(Z, m, p.Hfull, p.tw32, 1);
-        fft_smem<float2, true>(Z, m, p.tw32, p.Wb);
+        fft_smem<float2, false>(Z, mm, p.tw32, p.Wb);
+        pdl_wait();  // the FP32 kernel spectrum from k_spec
+        spectral_multiply(Z, mm, static_cast<const float2*>(p.Hfull), p.tw32, 1, false);
+        fft_smem<float2, true>(Z, mm, p.tw32, p.Wb);
         for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
             const long long o = g.start + j;
             if (o < 0 || o >= p.out_len) continue;
             p.r[o] = word<float>(Z, j);
             if (p.rq) p.rq[o] = 0;
         }
-        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, s.Ms, s.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, Ms, sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
         return;
     }
 
-    const Cand& c = p.cand[s.ci];
-    const float cs = s.cs;
+    const Cand& c = p.cand[ci];
     const double eps = ldexp(1.0, -c.b);
     double2* Z = reinterpret_cast<double2*>(smem);
-    int n, Ls = 0, nr = 0;
+    const int n = c.blk == APX_BLK_SYM ? p.Wb / 2 : p.Wb;
+    const int mm = n / 2;
+
+    // The packed kernel spectrum, built once per call by the first CTA to claim it.
+    if (threadIdx.x == 0) {
+        int st = 0;  // 0 ready, 1 build it here, 2 wait for another CTA
+        if (ld_acquire(&p.ready[ci]) != p.epoch) st = atomicExch(&p.claim[ci], p.epoch) != p.epoch ? 1 : 2;
+        s_flag = st;
+    }
+    __syncthreads();
+    const int role = s_flag;
+    __syncthreads();
+    if (role == 1) {
+        auto tap = [&](int t) -> double { return (double)kbar_int(p, c, ck, t); };  // Eq. (5) / k~
+        spectrum_of<double>(tap, p.Wb, n, p.tw64, c.H, Z);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(&p.ready[ci], p.epoch);
+    }
+
+    int Ls = 0, nr = 0;
     if (c.blk == APX_BLK_SYM) {
         // Eq. (4): word w = s~[2w] + eps s~[2w+1]; this thread holds pair w
-        n = p.Wb / 2;
 #pragma unroll
         for (int v = 0; v < kVals / 2; ++v)
             if (pair_ok(p, v)) {
@@ -198,7 +222,6 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
             }
     } else {
         // Eq. (7): word w = sum_q eps^q s~[w + q Ls], zero past Ls
-        n = p.Wb;
         Ls = (p.Wb + c.M - 1) / c.M;
         nr = Ls + p.Nodd - 1;
         int* sq = reinterpret_cast<int*>(smem + sizeof(double2) * padded_len(p.Wb / 2));
@@ -223,12 +246,30 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         }
     }
     __syncthreads();
-    const int m = n / 2;
-    fft_smem<double2, false>(Z, m, p.tw64, p.Wb);
-    spectral_multiply(Z, m, c.H, p.tw64, p.Wb / n);
-    fft_smem<double2, true>(Z, m, p.tw64, p.Wb);
+    fft_smem<double2, false>(Z, mm, p.tw64, p.Wb);
 
-    const float inv = s.inv;
+    if (role == 2) {
+        if (threadIdx.x == 0) {
+            int ok = 0;
+            for (int it = 0; it < kSpinLimit; ++it) {
+                if (ld_acquire(&p.ready[ci]) == p.epoch) { ok = 1; break; }
+                __nanosleep(256);
+            }
+            if (!ok) atomicOr(p.status, 2u);
+            s_flag = ok;
+        }
+        __syncthreads();
+        if (!s_flag) {
+            store_constant(p, g, __int_as_float(0x7fc00000));
+            return;
+        }
+    }
+    spectral_multiply(Z, mm, static_cast<const double2*>(c.H), p.tw64, p.Wb / n, true);
+    fft_smem<double2, true>(Z, mm, p.tw64, p.Wb);
+
+    if (threadIdx.x == 0) sh.bcast[2] = 1.0 / ((double)cs * (double)ck);
+    __syncthreads();
+    const float inv = (float)sh.bcast[2];
     auto Tat = [&](int idx) { return scaled(word<double>(Z, idx), c.sc); };
     for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
@@ -238,21 +279,19 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         if (p.rq) p.rq[o] = (int)rt;
     }
     if (threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, s.Ms, s.sig2, s.snr_db, s.ferr);
-}
-
-cudaError_t launch_select(const Params& p, cudaStream_t st) {
-    if (p.P <= 0) return cudaSuccess;
-    return launch_k(k_select, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), 0, st, false, p);
+        write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, ks.sig2k, ks.Mk, c.S, c.K), ferr);
 }
 
 size_t fft_smem_bytes(const Params& p) {
-    bool asym = false, packed = p.ncand > 0;
+    bool asym = false;
     for (int j = 0; j < p.ncand; ++j) asym |= p.cand[j].blk != APX_BLK_SYM;
-    size_t z32 = sizeof(float2) * padded_len(p.Wb / 2);
-    size_t z64 = packed ? sizeof(double2) * padded_len(asym ? p.Wb / 2 : p.Wb / 4) : 0;
-    size_t sq = asym ? sizeof(int) * (size_t)p.Wb : 0;
-    return (z32 > z64 + sq ? z32 : z64 + sq);
+    const size_t z32 = sizeof(float2) * padded_len(p.Wb / 2);
+    // a symmetric candidate transforms W_block/2 real words (W_block/4 complex),
+    // an asymmetric one W_block real words plus the companded block as int32
+    size_t z64 = 0;
+    if (p.ncand > 0) z64 = sizeof(double2) * padded_len(asym ? p.Wb / 2 : p.Wb / 4);
+    if (asym) z64 += sizeof(int) * (size_t)p.Wb;
+    return z32 > z64 ? z32 : z64;
 }
 
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {

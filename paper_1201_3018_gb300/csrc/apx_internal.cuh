@@ -27,15 +27,7 @@ struct Cand {
     int nk;           // packed taps: (N'+1)/2 (sym) or N' (asym)
     int log2n;        // FFT core: log2 of the real transform length
     double fftc;      // FFT core: (3 phi + 16 u) for log2n (error-bound constant)
-    const double2* H; // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries
-};
-
-// Kernel statistics; every CTA derives them from the raw taps (the same bits
-// everywhere), and the FFT core's first CTA also publishes them here.
-struct KInfo {
-    float Mk;         // ||k||_inf
-    int nonfinite;    // kernel has NaN/Inf
-    double sig2k;     // second moment of the kernel (24-bit fixed point)
+    double2* H;       // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries (built on demand)
 };
 
 // Shared-memory layout of the direct kernel (byte offsets; element pads).
@@ -48,17 +40,6 @@ struct DirectLayout {
     int offKb;        // packed taps: byte offset
 };
 
-// Per-block decision of the FFT core's selection pass.
-struct Sel {
-    int ci;           // candidate index, -1: full precision, -2 zero block, -3 non-finite
-    float cs;         // c_s of the chosen candidate
-    float Ms;         // ||s||_inf of the window
-    float inv;        // 1 / (c_s c_k) as FP32 (Eq. 16)
-    double sig2;      // second moment of the window
-    double ferr;      // FFT error bound in digits of the chosen candidate
-    double snr_db;    // model SNR of the chosen candidate
-};
-
 struct Params {
     const float* s;       // input, L samples
     long long L;
@@ -68,19 +49,18 @@ struct Params {
     float* r;             // output, out_len
     int* rq;              // integer-domain output or null
     apx_block_stats* st;  // per-block stats or null
-    const float2* Hfull;  // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
+    float2* Hfull;        // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
     const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
     const float2* tw32;
-    KInfo* ki;            // FFT core: kernel statistics published by CTA 0 of the selection pass
-    unsigned* status;     // bit 0: non-finite input seen
-    unsigned* used;       // FFT core: bit c set when candidate c is used, bit 3 for full precision
-    unsigned* used_next;  // the other slot, cleared for the next call
+    unsigned* status;     // bit 0: non-finite input seen; bit 1: a bounded wait gave up
+    unsigned* claim;      // FFT core, per candidate: last call that claimed building its spectrum
+    unsigned* ready;      // FFT core, per candidate: last call whose spectrum is complete
+    unsigned epoch;       // FFT core: this call's number (never 0)
     int autosel;          // 1: per-block selection under thr
     int ncand;
     double thr;           // 10^(target/10)
     Cand cand[kMaxCand];
     DirectLayout dl;      // direct core
-    Sel* sel;             // FFT core: per-block decisions (P entries)
 };
 
 // ------------------------------------------------------------------ reductions
@@ -390,14 +370,19 @@ __device__ __forceinline__ void real_pre(C yk, C ymk, C w, C& Zk, C& Zmk) {
 // entries, natural order).  The factor 2 of X2, the missing 1/2 of the inverse
 // step and the 1/m of the inverse FFT fold into that power-of-two scale.
 template <typename C>
-__device__ void spectral_multiply(C* Z, int m, const C* __restrict__ H, const C* __restrict__ tw, int twn) {
+__device__ __forceinline__ C load_h(const C* H, int k, bool coherent) {
+    return coherent ? __ldcg(&H[k]) : __ldg(&H[k]);
+}
+// `coherent`: H was written during this kernel (read around L1).
+template <typename C>
+__device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__ tw, int twn, bool coherent) {
     for (int k = threadIdx.x; k <= m / 2; k += blockDim.x) {
         if (k == 0) {
             C z0 = Z[0];
             C X0, Xm;
             X0.x = 2 * (z0.x + z0.y); X0.y = 0;
             Xm.x = 2 * (z0.x - z0.y); Xm.y = 0;
-            C Y0 = cmul(X0, __ldg(&H[0])), Ym = cmul(Xm, __ldg(&H[m]));
+            C Y0 = cmul(X0, load_h(H, 0, coherent)), Ym = cmul(Xm, load_h(H, m, coherent));
             C cym = cconj(Ym);
             Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
         } else {
@@ -406,8 +391,8 @@ __device__ void spectral_multiply(C* Z, int m, const C* __restrict__ H, const C*
             C w = __ldg(&tw[k * twn]);
             C Xk, Xmk;
             real_post(a, b, w, Xk, Xmk);
-            C Yk = cmul(Xk, __ldg(&H[k]));
-            C Ymk = cmul(Xmk, __ldg(&H[m - k]));
+            C Yk = cmul(Xk, load_h(H, k, coherent));
+            C Ymk = cmul(Xmk, load_h(H, m - k, coherent));
             C Zk, Zmk;
             real_pre(Yk, Ymk, w, Zk, Zmk);
             Z[pk] = Zk;
@@ -421,5 +406,14 @@ __device__ void spectral_multiply(C* Z, int m, const C* __restrict__ H, const C*
 // wait for the previous one's results.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* a, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
 
 }  // namespace apx

@@ -8,6 +8,7 @@
 namespace apx {
 
 constexpr int kDirectThreads = 256;
+constexpr int kSpecFreqs = 16;  // frequencies per CTA of the FP32 spectrum
 constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (static shared memory needs the rest)
 
 // FFT core: one thread per 16 complex points of the largest transform (W_block/2).
@@ -32,8 +33,7 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-cudaError_t launch_select(const Params& p, cudaStream_t st);
-cudaError_t launch_spectra(const Params& p, float2* Hfull, double2* Hc[kMaxCand], cudaStream_t st);
+cudaError_t launch_spec(const Params& p, cudaStream_t st);
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
 size_t fft_smem_bytes(const Params& p);

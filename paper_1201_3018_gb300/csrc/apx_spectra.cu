@@ -1,80 +1,70 @@
-// apx_spectra.cu -- kernel spectra of the FFT core (Section IV "Initialization":
-// the kernel is prepared once per request).
+// apx_spectra.cu -- the FP32 kernel spectrum of the FFT core (Section IV
+// "Initialization": the kernel is prepared once per request).
 //
-// CTA 0 transforms the FP32 taps (reversed for cross-correlation); it needs
-// nothing from the selection pass and runs while that pass is still working.
-// CTA 1 + c transforms the packed taps of candidate c (Eq. 5 with the pair
-// order k~[2n+1] + eps^-1 k~[2n], or k~ for asymmetric packing), and only if
-// some block selected candidate c.  Every CTA waits for the selection pass
-// before it exits, so this grid's completion implies that pass's.
+// H[k] = FFT_n(taps)[k] / (4m), k in [0, m], n = W_block = 2m real points, as a
+// direct DFT split over many CTAs: each CTA owns a few frequencies, each thread
+// a strided subset of the taps (twiddles advanced by a complex recurrence from
+// the table), partial sums combined by a tree reduction.  With N taps this is
+// N (m+1) complex multiply-adds spread over the whole GPU, which finishes well
+// before the block kernel (launched as its programmatic dependent) needs it.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
 namespace apx {
 
-// H = FFT_n(taps) / (4m), k in [0, m], natural order; tap(j) gives tap j.
-template <typename R, typename C, typename F>
-__device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H, C* Z) {
-    const int m = n / 2;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        C v;
-        v.x = tap(2 * j);
-        v.y = tap(2 * j + 1);
-        Z[pad16(j)] = v;
+constexpr int kSpecThreads = 256;
+
+__global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p) {
+    __shared__ float2 part[kSpecThreads / 32][kSpecFreqs];
+    pdl_trigger();
+    const int m = p.Wb / 2, n = p.Wb;
+    const int k0 = blockIdx.x * kSpecFreqs;
+    float2 acc[kSpecFreqs], w[kSpecFreqs], st[kSpecFreqs];
+    const int t0 = threadIdx.x;
+    const float h0 = ktap(p, t0);  // t0 < N handled by ktap (zero past N)
+#pragma unroll
+    for (int f = 0; f < kSpecFreqs; ++f) {
+        const int k = min(k0 + f, m);
+        w[f] = __ldg(&p.tw32[(int)(((long long)t0 * k) & (n - 1))]);               // W^(t0 k)
+        st[f] = __ldg(&p.tw32[(int)(((long long)kSpecThreads * k) & (n - 1))]);    // W^(NT k)
+        acc[f] = make_float2(0.f, 0.f);
+    }
+    float h = h0;
+    for (int t = t0; t < p.N; t += kSpecThreads) {
+        const float hn = ktap(p, t + kSpecThreads);
+#pragma unroll
+        for (int f = 0; f < kSpecFreqs; ++f) {
+            acc[f].x = fmaf(h, w[f].x, acc[f].x);
+            acc[f].y = fmaf(h, w[f].y, acc[f].y);
+            w[f] = cmul(w[f], st[f]);
+        }
+        h = hn;
+    }
+    // tree reduction over the CTA
+#pragma unroll
+    for (int f = 0; f < kSpecFreqs; ++f) {
+        float x = acc[f].x, y = acc[f].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5][f] = make_float2(x, y);
     }
     __syncthreads();
-    fft_smem<C, false>(Z, m, tw, Wb);
-    const R scale = (R)1 / (R)(8 * m);
-    for (int k = threadIdx.x; k <= m; k += blockDim.x) {
-        C X;
-        if (k == 0 || k == m) {
-            const C z0 = Z[0];
-            X.x = 2 * (k == 0 ? z0.x + z0.y : z0.x - z0.y);
-            X.y = 0;
-        } else {
-            C Xmk;
-            real_post(Z[pad16(fft_perm(k, m))], Z[pad16(fft_perm(m - k, m))], __ldg(&tw[k * (Wb / n)]), X, Xmk);
-        }
-        X.x *= scale; X.y *= scale;
-        H[k] = X;
+    if (threadIdx.x < kSpecFreqs && k0 + threadIdx.x <= m) {
+        float x = 0.f, y = 0.f;
+#pragma unroll
+        for (int wi = 0; wi < kSpecThreads / 32; ++wi) { x += part[wi][threadIdx.x].x; y += part[wi][threadIdx.x].y; }
+        const float scale = 1.f / (float)(4 * m);
+        p.Hfull[k0 + threadIdx.x] = make_float2(x * scale, y * scale);
     }
 }
 
-__global__ void __launch_bounds__(512) k_spectra(const Params p, float2* Hfull, double2* H0, double2* H1,
-                                                 double2* H2) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    pdl_trigger();
-    const int job = blockIdx.x;
-    if (job == 0) {
-        auto tap = [&](int n) -> float { return ktap(p, n); };
-        spectrum_of<float>(tap, p.Wb, p.Wb, p.tw32, Hfull, reinterpret_cast<float2*>(smem));
-        if (threadIdx.x == 0) *p.used_next = 0u;
-        pdl_wait();
-        return;
-    }
-    pdl_wait();  // selection complete: `used` and the published kernel statistics are final
-    const int c = job - 1;
-    if (c >= p.ncand || !(*p.used & (1u << c))) return;
-    const Cand& cd = p.cand[c];
-    const float ck = compand_factor(cd.K, p.ki->Mk);
-    auto tap = [&](int n) -> double { return (double)kbar_int(p, cd, ck, n); };
-    double2* Hc = c == 0 ? H0 : (c == 1 ? H1 : H2);
-    const int n = cd.blk == APX_BLK_SYM ? p.Wb / 2 : p.Wb;
-    spectrum_of<double>(tap, p.Wb, n, p.tw64, Hc, reinterpret_cast<double2*>(smem));
-}
-
-cudaError_t launch_spectra(const Params& p, float2* Hfull, double2* Hc[kMaxCand], cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev;
-    cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
-    const size_t smem = sizeof(double2) * padded_len(p.Wb / 2);
-    return launch_k(k_spectra, dim3(1 + p.ncand), dim3(fft_threads(p.Wb)), smem, st, true, p, Hfull, Hc[0], Hc[1],
-                    Hc[2]);
+cudaError_t launch_spec(const Params& p, cudaStream_t st) {
+    const int m = p.Wb / 2;
+    const int grid = (m + 1 + kSpecFreqs - 1) / kSpecFreqs;
+    return launch_k(k_spec, dim3(grid), dim3(kSpecThreads), 0, st, false, p);
 }
 
 }  // namespace apx
