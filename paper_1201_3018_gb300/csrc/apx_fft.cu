@@ -1,22 +1,22 @@
 // apx_fft.cu -- the frequency-domain (FFT) block kernel.
 //
 // One CTA per overlap-save block, launched as the programmatic dependent of
-// k_spec (the FP32 kernel spectrum).  Each CTA:
-//   1. fetches its W_block window into registers,
-//   2. derives the kernel statistics from the raw taps and the block
-//      statistics from the window (identical bits in every CTA),
+// k_spec (kernel statistics and the FP32 kernel spectrum).  Each CTA:
+//   1. fetches its W_block window into registers and computes the block
+//      statistics,
+//   2. starts the FP32 forward real FFT of the window (full precision is every
+//      block's fallback) before griddepcontrol.wait, overlapping k_spec,
 //   3. runs the Section IV.D selection; for a packing candidate it companded
 //      the block and checks the FFT error bound (reading c7) with the exact
 //      integer norms sum(s~^2) and ||kbar||_1, so rounding recovers the digits,
-//   4. companded and packs (Eqs. 2, 4, 7) into a complex buffer (two real words
-//      per complex entry) and runs the forward real FFT,
-//   5. waits for the kernel spectrum, multiplies, runs the inverse FFT,
-//   6. extracts the digits (Eqs. 11-15), inverse-companded (Eq. 16), stores
-//      (Eq. 17).
-// The FP32 spectrum comes from k_spec (griddepcontrol.wait).  A packed
-// candidate's FP64 spectrum is built on demand by the first CTA that selects
-// it; later CTAs wait for it with a bounded spin and report a timeout in the
-// status word instead of hanging.
+//   4. full precision: multiplies by the spectrum and inverts; packed:
+//      companded and packs (Eqs. 2, 4, 7) into an FP64 complex buffer (two
+//      real words per complex entry), forward FFT, product, inverse FFT, digit
+//      extraction (Eqs. 11-15), inverse companding (Eq. 16),
+//   5. stores its W outputs (Eq. 17).
+// A packed candidate's FP64 spectrum is built on demand by the first CTA that
+// selects it; later CTAs wait for it with a bounded spin and report a timeout
+// in the status word instead of hanging.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
@@ -117,12 +117,28 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         acc = block_reduce<long long, false>(acc, sh.redl);
         sig2 = fx_moment(acc, f, p.Wb, sh);
     }
-    // Kernel initialisation of Section IV, from the raw taps in every CTA.
-    const KStats ks = kernel_stats(p, sh);
+
+    // Full precision is every block's fallback: start its forward FFT (FP32)
+    // while the kernel preparation may still be running.
+    const int mf = p.Wb / 2;
+    float2* Zf = reinterpret_cast<float2*>(smem);
+    const bool live = finite && m > 0.f;
+    if (live) {
+#pragma unroll
+        for (int v = 0; v < kVals / 2; ++v)
+            if (pair_ok(p, v)) Zf[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
+        __syncthreads();
+        fft_smem<float2, false>(Zf, mf, p.tw32, p.Wb);
+    }
+
+    pdl_wait();  // kernel statistics and FP32 kernel spectrum from the preparation launch
+    const float Mk = __ldcg(&p.ki->Mk);
+    const int kbad = __ldcg(&p.ki->bad);
+    const double sig2k = __ldcg(&p.ki->sig2k);
     const float Ms = bad ? __int_as_float(0x7fc00000) : m;
-    if (!finite || ks.bad || m == 0.f || ks.Mk == 0.f) {
+    if (!finite || kbad || m == 0.f || Mk == 0.f) {
         Pro pr;
-        pr.kind = (!finite || ks.bad) ? 3 : 2;
+        pr.kind = (!finite || kbad) ? 3 : 2;
         pr.Ms = Ms;
         pr.sig2 = 0.0;
         handle_trivial(p, i, g, pr);
@@ -133,15 +149,17 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
     int ci = -1;
     float cs = 0.f, ck = 0.f;
     double ferr = 0.0;
+    bool have_window = false;
     for (int c = 0; c < p.ncand; ++c) {
         const Cand& cd = p.cand[c];
-        if (threadIdx.x == 0) s_flag = !p.autosel || snr_feasible(sig2, m, ks.sig2k, ks.Mk, cd.S, cd.K, p.thr);
+        if (threadIdx.x == 0) s_flag = !p.autosel || snr_feasible(sig2, m, sig2k, Mk, cd.S, cd.K, p.thr);
         __syncthreads();
         const int go = s_flag;
         __syncthreads();
         if (!go) continue;
+        if (!have_window) { load_window_regs(p, g.start, xv); have_window = true; }
         const float cs_c = compand_factor(cd.S, m);
-        const float ck_c = compand_factor(cd.K, ks.Mk);
+        const float ck_c = compand_factor(cd.K, Mk);
         long long ss = 0;
 #pragma unroll
         for (int v = 0; v < kVals; ++v) {
@@ -149,12 +167,11 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
             ss += q * q;
         }
         ss = block_reduce<long long, false>(ss, sh.redl);
-        const long long l1 = kbar_l1(p, cd, ck_c, sh);
         if (threadIdx.x == 0) {
             const double eps = ldexp(1.0, -cd.b);
             const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
             const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
-            sh.bcast[1] = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ll2double_rn(l1)), l2), cd.sc);
+            sh.bcast[1] = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ldcg(&p.ki->l1[c])), l2), cd.sc);
         }
         __syncthreads();
         const double E = sh.bcast[1];
@@ -166,21 +183,13 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
     }
 
     if (ci < 0) {
-        // Full precision: real FFT of length W_block in FP32.
-        const int mm = p.Wb / 2;
-        float2* Z = reinterpret_cast<float2*>(smem);
-#pragma unroll
-        for (int v = 0; v < kVals / 2; ++v)
-            if (pair_ok(p, v)) Z[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
-        __syncthreads();
-        fft_smem<float2, false>(Z, mm, p.tw32, p.Wb);
-        pdl_wait();  // the FP32 kernel spectrum from k_spec
-        spectral_multiply(Z, mm, static_cast<const float2*>(p.Hfull), p.tw32, 1, false);
-        fft_smem<float2, true>(Z, mm, p.tw32, p.Wb);
+        // Full precision: finish the FP32 real-FFT convolution.
+        spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, 1, true);
+        fft_smem<float2, true>(Zf, mf, p.tw32, p.Wb);
         for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
             const long long o = g.start + j;
             if (o < 0 || o >= p.out_len) continue;
-            p.r[o] = word<float>(Z, j);
+            p.r[o] = word<float>(Zf, j);
             if (p.rq) p.rq[o] = 0;
         }
         write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, Ms, sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
     }
     __syncthreads();
     const int role = s_flag;
-    __syncthreads();
+    __syncthreads();  // (also: every thread is done with the speculative FP32 buffer)
     if (role == 1) {
         auto tap = [&](int t) -> double { return (double)kbar_int(p, c, ck, t); };  // Eq. (5) / k~
         spectrum_of<double>(tap, p.Wb, n, p.tw64, c.H, Z);
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         if (p.rq) p.rq[o] = (int)rt;
     }
     if (threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, ks.sig2k, ks.Mk, c.S, c.K), ferr);
+        write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, sig2k, Mk, c.S, c.K), ferr);
 }
 
 size_t fft_smem_bytes(const Params& p) {

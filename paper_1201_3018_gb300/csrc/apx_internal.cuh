@@ -30,6 +30,14 @@ struct Cand {
     double2* H;       // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries (built on demand)
 };
 
+// Kernel statistics published by the FFT core's spectrum launch.
+struct KInfo {
+    float Mk;             // ||k||_inf
+    int bad;              // kernel has NaN/Inf
+    double sig2k;         // second moment of the kernel (24-bit fixed point)
+    double l1[kMaxCand];  // ||kbar||_1 of each candidate, exact integer
+};
+
 // Shared-memory layout of the direct kernel (byte offsets; element pads).
 struct DirectLayout {
     int padF;         // zero floats in front of the window
@@ -50,6 +58,7 @@ struct Params {
     int* rq;              // integer-domain output or null
     apx_block_stats* st;  // per-block stats or null
     float2* Hfull;        // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
+    KInfo* ki;            // FFT core: kernel statistics from the spectrum launch
     const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
     const float2* tw32;
     unsigned* status;     // bit 0: non-finite input seen; bit 1: a bounded wait gave up
