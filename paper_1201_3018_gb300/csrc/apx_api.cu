@@ -30,7 +30,7 @@ struct apx_ctx {
     size_t budget = 0;
     size_t in_use = 0;
     int64_t launches = 0;
-    DevBuf flags, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    DevBuf flags, ki, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     int tw_wb = 0;          // W_block the twiddle tables were built for
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     // tracing
@@ -289,6 +289,16 @@ struct DeviceGuard {
     }
 };
 
+// Every device pointer a launch dereferences must be set before it launches.
+bool device_pointers_set(const Params& p) {
+    if (!p.s || !p.k || !p.r || !p.status) return false;
+    if (!p.fft) return true;
+    if (!p.Hfull || !p.ki || !p.tw64 || !p.tw32 || !p.claim || !p.ready) return false;
+    for (int j = 0; j < p.ncand; ++j)
+        if (!p.cand[j].H) return false;
+    return true;
+}
+
 // Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
 int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
         int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
@@ -354,6 +364,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     if (!rc && pl.fft) {
         const size_t m1 = (size_t)Wb / 2 + 1;
         rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
+        if (!rc) rc = ensure(ctx, ctx->ki, sizeof(KInfo));
         for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->Hc[j], sizeof(double2) * m1);
         if (!rc) rc = ensure_twiddles(ctx, Wb, stream);
     }
@@ -366,8 +377,10 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     p.claim = (unsigned*)ctx->flags.p + 1;
     p.ready = (unsigned*)ctx->flags.p + 1 + kMaxCand;
     p.Hfull = (float2*)ctx->Hfull.p;
+    p.ki = (KInfo*)ctx->ki.p;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
+    if (!device_pointers_set(p)) return APX_ERR_CUDA;
 
     cudaError_t e;
     if (!pl.fft) {
@@ -418,8 +431,8 @@ void apx_destroy(apx_ctx* c) {
     {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
-        DevBuf* all[] = {&c->flags, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32, &c->hs,
-                         &c->hk, &c->hr};
+        DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32,
+                         &c->hs, &c->hk, &c->hr};
         for (DevBuf* b : all) release(c, *b);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }
