@@ -244,4 +244,40 @@ __device__ __forceinline__ long long unpack_asym(const Cand& c, int j, int Ls, i
     return acc;
 }
 
+// real word w of a padded complex buffer
+template <typename R, typename C>
+__device__ __forceinline__ R& word(C* Z, int w) {
+    return reinterpret_cast<R*>(Z)[2 * pad16(w >> 1) + (w & 1)];
+}
+
+// H = FFT_n(taps) / (4m), k in [0, m], natural order, through the block FFT;
+// tap(j) gives tap j.  Z is scratch of padded_len(n/2) entries.
+template <typename R, typename C, typename F>
+__device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H, C* Z) {
+    const int m = n / 2;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        C v;
+        v.x = tap(2 * j);
+        v.y = tap(2 * j + 1);
+        Z[pad16(j)] = v;
+    }
+    __syncthreads();
+    fft_smem<C, false>(Z, m, tw, Wb);
+    const R scale = (R)1 / (R)(8 * m);
+    for (int k = threadIdx.x; k <= m; k += blockDim.x) {
+        C X;
+        if (k == 0 || k == m) {
+            const C z0 = Z[0];
+            X.x = 2 * (k == 0 ? z0.x + z0.y : z0.x - z0.y);
+            X.y = 0;
+        } else {
+            C Xmk;
+            real_post(Z[pad16(fft_perm<C>(k, m))], Z[pad16(fft_perm<C>(m - k, m))], __ldg(&tw[k * (Wb / n)]), X, Xmk);
+        }
+        X.x *= scale; X.y *= scale;
+        H[k] = X;
+    }
+    __syncthreads();
+}
+
 }  // namespace apx

@@ -22,7 +22,6 @@
 
 namespace apx {
 
-constexpr int kVals = 32;  // window samples per thread (W_block / threads)
 constexpr int kSpinLimit = 1 << 22;
 
 // Thread t holds window samples 2(t + i NT) and 2(t + i NT) + 1 (pair t + i NT)
@@ -30,6 +29,7 @@ constexpr int kSpinLimit = 1 << 22;
 // the second moment and the companded norm unchanged.
 __device__ __forceinline__ bool pair_ok(const Params& p, int i) { return threadIdx.x + i * blockDim.x < p.Wb / 2; }
 
+template <int kVals>
 __device__ __forceinline__ void load_window_regs(const Params& p, long long start, float (&xv)[kVals]) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(p.s + start) & 7u) == 0);
 #pragma unroll
@@ -51,43 +51,9 @@ __device__ __forceinline__ void load_window_regs(const Params& p, long long star
     }
 }
 
-// real word w of a padded complex buffer
-template <typename R, typename C>
-__device__ __forceinline__ R& word(C* Z, int w) {
-    return reinterpret_cast<R*>(Z)[2 * pad16(w >> 1) + (w & 1)];
-}
-
-// H = FFT_n(taps) / (4m), k in [0, m], natural order, through the block FFT;
-// tap(j) gives tap j.  Z is scratch of padded_len(n/2) entries.
-template <typename R, typename C, typename F>
-__device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H, C* Z) {
-    const int m = n / 2;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        C v;
-        v.x = tap(2 * j);
-        v.y = tap(2 * j + 1);
-        Z[pad16(j)] = v;
-    }
-    __syncthreads();
-    fft_smem<C, false>(Z, m, tw, Wb);
-    const R scale = (R)1 / (R)(8 * m);
-    for (int k = threadIdx.x; k <= m; k += blockDim.x) {
-        C X;
-        if (k == 0 || k == m) {
-            const C z0 = Z[0];
-            X.x = 2 * (k == 0 ? z0.x + z0.y : z0.x - z0.y);
-            X.y = 0;
-        } else {
-            C Xmk;
-            real_post(Z[pad16(fft_perm(k, m))], Z[pad16(fft_perm(m - k, m))], __ldg(&tw[k * (Wb / n)]), X, Xmk);
-        }
-        X.x *= scale; X.y *= scale;
-        H[k] = X;
-    }
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(512) k_fft(const Params p) {
+// kVals: window samples per thread (W_block / threads: 16, or 32 at the largest W_block)
+template <int kVals>
+__global__ void __launch_bounds__(512, 2) k_fft(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int s_flag;
@@ -309,11 +275,15 @@ cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
     int dev;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_fft<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fft<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    return launch_k(k_fft, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
+    if (p.Wb / fft_threads(p.Wb) > 16)
+        return launch_k(k_fft<32>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
+    return launch_k(k_fft<16>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
 }
 
 }  // namespace apx

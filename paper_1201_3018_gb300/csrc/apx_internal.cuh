@@ -282,51 +282,56 @@ __device__ __forceinline__ void twiddles(C (&w)[RAD], const C* __restrict__ tw, 
     }
 }
 
+// Radix of the main passes of a length-m transform on nt threads: 8 when
+// every thread gets at least one radix-8 butterfly, else 4; FP64 transforms
+// always use radix 4 (their time is set by the FP64 rate, and the small
+// butterfly keeps the register count low).
+template <typename C>
+__host__ __device__ constexpr int fft_radix(int m, int nt) {
+    return sizeof(C) == 16 ? 4 : (m >= 8 * nt ? 8 : 4);
+}
+
 // One in-place pass over sub-transforms of length M with radix RAD (stride
 // S = M/RAD).  Forward (decimation in frequency): DFT then twiddle W_M^(r j).
 // Inverse (decimation in time, the exact reverse): conjugate twiddle then
-// inverse DFT.  Each thread reads and writes the same slots, so a pass needs
+// inverse DFT.  Each butterfly reads and writes the same slots, so a pass needs
 // no barrier inside; callers separate passes with __syncthreads().
 template <typename C, int RAD, bool INV>
 __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab) {
     const int S = M / RAD, nbf = m / RAD;
     const int tstep = ntab / M;
-    constexpr int BPT = 16 / RAD;
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+        const int g = b / S, j = b - g * S;
+        const int base = g * M + j;
+        C v[RAD], w[RAD];
 #pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * blockDim.x;
-        if (b < nbf) {
-            const int g = b / S, j = b - g * S;
-            const int base = g * M + j;
-            C v[RAD], w[RAD];
-#pragma unroll
-            for (int q = 0; q < RAD; ++q) v[q] = Z[pad16(base + q * S)];
-            twiddles<C, RAD, INV>(w, tw, j * tstep);
-            if (!INV) {
-                dft_small<RAD, C, false>(v);
+        for (int q = 0; q < RAD; ++q) v[q] = Z[pad16(base + q * S)];
+        if (S > 1) twiddles<C, RAD, INV>(w, tw, j * tstep);
+        if (!INV) {
+            dft_small<RAD, C, false>(v);
+            if (S > 1) {
 #pragma unroll
                 for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
-            } else {
-#pragma unroll
-                for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
-                dft_small<RAD, C, true>(v);
             }
+        } else {
+            if (S > 1) {
 #pragma unroll
-            for (int q = 0; q < RAD; ++q) Z[pad16(base + q * S)] = v[q];
+                for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], w[r]);
+            }
+            dft_small<RAD, C, true>(v);
         }
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) Z[pad16(base + q * S)] = v[q];
     }
 }
 
-// Length-m (power of two) complex FFT of the padded buffer Z.  Forward:
-// natural order in, digit-reversed order out (see fft_perm).  Inverse: that
-// order in, natural order out, unnormalised.  Needs blockDim.x >= m / 16.
-template <typename C, bool INV>
-__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw, int ntab) {
     int a = 0, t = m;
-    while (t >= 16) { t >>= 4; ++a; }   // m = 16^a * t, t in {1, 2, 4, 8}
+    while (t >= R) { t /= R; ++a; }   // m = R^a * t, t < R
     if (!INV) {
         int M = m;
-        for (int s = 0; s < a; ++s) { fft_pass<C, 16, false>(Z, m, M, tw, ntab); __syncthreads(); M >>= 4; }
+        for (int s = 0; s < a; ++s) { fft_pass<C, R, false>(Z, m, M, tw, ntab); __syncthreads(); M /= R; }
         if (t == 8) fft_pass<C, 8, false>(Z, m, 8, tw, ntab);
         else if (t == 4) fft_pass<C, 4, false>(Z, m, 4, tw, ntab);
         else if (t == 2) fft_pass<C, 2, false>(Z, m, 2, tw, ntab);
@@ -336,18 +341,29 @@ __device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
         else if (t == 4) fft_pass<C, 4, true>(Z, m, 4, tw, ntab);
         else if (t == 2) fft_pass<C, 2, true>(Z, m, 2, tw, ntab);
         if (t > 1) __syncthreads();
-        int M = t * 16;
-        for (int s = 0; s < a; ++s) { fft_pass<C, 16, true>(Z, m, M, tw, ntab); __syncthreads(); M <<= 4; }
+        int M = t * R;
+        for (int s = 0; s < a; ++s) { fft_pass<C, R, true>(Z, m, M, tw, ntab); __syncthreads(); M *= R; }
     }
+}
+
+// Length-m (power of two) complex FFT of the padded buffer Z by the whole
+// CTA.  Forward: natural order in, digit-reversed order out (see fft_perm).
+// Inverse: that order in, natural order out, unnormalised.
+template <typename C, bool INV>
+__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
+    if (sizeof(C) == 8 && fft_radix<C>(m, blockDim.x) == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab);
+    else fft_passes<C, 4, INV>(Z, m, tw, ntab);
 }
 
 // Slot of frequency k after the forward FFT: k = r1 + R1 r2 + R1 R2 r3 + ...
 // (r_s the output digit of pass s) sits at r1 S1 + r2 S2 + ..., S_s the
 // stride of pass s.
+template <typename C>
 __device__ __forceinline__ int fft_perm(int k, int m) {
+    const int R = fft_radix<C>(m, blockDim.x);
     int pos = 0, S = m;
-    while (S >= 16) { S >>= 4; pos += (k & 15) * S; k >>= 4; }
-    if (S > 1) pos += k & (S - 1);   // last pass: stride 1
+    while (S >= R) { S /= R; pos += (k % R) * S; k /= R; }
+    if (S > 1) pos += k % S;   // last pass: stride 1
     return pos;
 }
 
@@ -395,7 +411,7 @@ __device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__
             C cym = cconj(Ym);
             Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
         } else {
-            const int pk = pad16(fft_perm(k, m)), pmk = pad16(fft_perm(m - k, m));
+            const int pk = pad16(fft_perm<C>(k, m)), pmk = pad16(fft_perm<C>(m - k, m));
             C a = Z[pk], b = Z[pmk];
             C w = __ldg(&tw[k * twn]);
             C Xk, Xmk;

@@ -8,11 +8,13 @@
 namespace apx {
 
 constexpr int kDirectThreads = 256;
-constexpr int kSpecFreqs = 16;  // frequencies per CTA of the FP32 spectrum
 constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (static shared memory needs the rest)
 
-// FFT core: one thread per 16 complex points of the largest transform (W_block/2).
-__host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 32 > 32 ? Wb / 32 : 32; }
+// FFT core block kernel: one thread per 8 complex points of the largest
+// transform (W_block/2), between 32 and 512 threads.
+__host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 16 > 512 ? 512 : (Wb / 16 > 32 ? Wb / 16 : 32); }
+// FFT core kernel spectrum: one CTA of this many threads.
+constexpr int kSpecThreads = 1024;
 
 // Launch through cudaLaunchKernelEx; `pdl` marks the launch as a programmatic
 // dependent of the previous kernel in the stream (the kernel calls
