@@ -30,7 +30,7 @@ struct apx_ctx {
     size_t budget = 0;
     size_t in_use = 0;
     int64_t launches = 0;
-    DevBuf flags, ki, Hfull, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     int tw_wb = 0;          // W_block the twiddle tables were built for
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     // tracing
@@ -293,7 +293,7 @@ struct DeviceGuard {
 bool device_pointers_set(const Params& p) {
     if (!p.s || !p.k || !p.r || !p.status) return false;
     if (!p.fft) return true;
-    if (!p.Hfull || !p.ki || !p.tw64 || !p.tw32 || !p.claim || !p.ready) return false;
+    if (!p.Hfull || !p.Ysub || !p.ki || !p.tw64 || !p.tw32 || !p.claim || !p.ready) return false;
     for (int j = 0; j < p.ncand; ++j)
         if (!p.cand[j].H) return false;
     return true;
@@ -365,6 +365,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         const size_t m1 = (size_t)Wb / 2 + 1;
         rc = ensure(ctx, ctx->Hfull, sizeof(float2) * m1);
         if (!rc) rc = ensure(ctx, ctx->ki, sizeof(KInfo));
+        if (!rc) rc = ensure(ctx, ctx->Ysub, sizeof(float2) * (size_t)Wb);
         for (int j = 0; j < nc && !rc; ++j) rc = ensure(ctx, ctx->Hc[j], sizeof(double2) * m1);
         if (!rc) rc = ensure_twiddles(ctx, Wb, stream);
     }
@@ -378,6 +379,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     p.ready = (unsigned*)ctx->flags.p + 1 + kMaxCand;
     p.Hfull = (float2*)ctx->Hfull.p;
     p.ki = (KInfo*)ctx->ki.p;
+    p.Ysub = (float2*)ctx->Ysub.p;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
     if (!device_pointers_set(p)) return APX_ERR_CUDA;
@@ -393,7 +395,8 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         {
             Trace t(ctx, stream, APX_PHASE_SPECTRA);
             e = launch_spec(p, stream);
-            ctx->launches += 1;
+            if (e == cudaSuccess) e = launch_spec_combine(p, stream);
+            ctx->launches += 2;
         }
         if (e == cudaSuccess) {
             Trace t(ctx, stream, APX_PHASE_FFT);
@@ -431,8 +434,8 @@ void apx_destroy(apx_ctx* c) {
     {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
-        DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64, &c->tw32,
-                         &c->hs, &c->hk, &c->hr};
+        DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
+                         &c->tw32, &c->hs, &c->hk, &c->hr};
         for (DevBuf* b : all) release(c, *b);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }

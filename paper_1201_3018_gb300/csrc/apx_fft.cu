@@ -53,7 +53,7 @@ __device__ __forceinline__ void load_window_regs(const Params& p, long long star
 
 // kVals: window samples per thread (W_block / threads: 16, or 32 at the largest W_block)
 template <int kVals>
-__global__ void __launch_bounds__(512, 2) k_fft(const Params p) {
+__global__ void __launch_bounds__(512) k_fft(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int s_flag;

@@ -58,6 +58,7 @@ struct Params {
     int* rq;              // integer-domain output or null
     apx_block_stats* st;  // per-block stats or null
     float2* Hfull;        // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
+    float2* Ysub;         // FFT core: spectra of the R1 decimated tap sequences (n entries)
     KInfo* ki;            // FFT core: kernel statistics from the spectrum launch
     const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
     const float2* tw32;
@@ -282,13 +283,13 @@ __device__ __forceinline__ void twiddles(C (&w)[RAD], const C* __restrict__ tw, 
     }
 }
 
-// Radix of the main passes of a length-m transform on nt threads: 8 when
-// every thread gets at least one radix-8 butterfly, else 4; FP64 transforms
+// Radix of the main passes of a length-m transform on nt threads: the largest
+// of 16, 8, 4 that still gives every thread a butterfly; FP64 transforms
 // always use radix 4 (their time is set by the FP64 rate, and the small
 // butterfly keeps the register count low).
 template <typename C>
 __host__ __device__ constexpr int fft_radix(int m, int nt) {
-    return sizeof(C) == 16 ? 4 : (m >= 8 * nt ? 8 : 4);
+    return sizeof(C) == 16 ? 4 : (m >= 16 * nt ? 16 : (m >= 8 * nt ? 8 : 4));
 }
 
 // One in-place pass over sub-transforms of length M with radix RAD (stride
@@ -351,7 +352,9 @@ __device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw
 // Inverse: that order in, natural order out, unnormalised.
 template <typename C, bool INV>
 __device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
-    if (sizeof(C) == 8 && fft_radix<C>(m, blockDim.x) == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab);
+    const int R = fft_radix<C>(m, blockDim.x);
+    if (sizeof(C) == 8 && R == 16) fft_passes<C, 16, INV>(Z, m, tw, ntab);
+    else if (sizeof(C) == 8 && R == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab);
     else fft_passes<C, 4, INV>(Z, m, tw, ntab);
 }
 

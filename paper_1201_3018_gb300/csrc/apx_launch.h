@@ -10,11 +10,12 @@ namespace apx {
 constexpr int kDirectThreads = 256;
 constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (static shared memory needs the rest)
 
-// FFT core block kernel: one thread per 8 complex points of the largest
-// transform (W_block/2), between 32 and 512 threads.
-__host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 16 > 512 ? 512 : (Wb / 16 > 32 ? Wb / 16 : 32); }
-// FFT core kernel spectrum: one CTA of this many threads.
-constexpr int kSpecThreads = 1024;
+// FFT core block kernel: one thread per 16 complex points of the largest
+// transform (W_block/2), at least 32.
+__host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 32 > 32 ? Wb / 32 : 32; }
+// FFT core kernel spectrum: R1 decimated sub-transforms of n / R1 points.
+__host__ __device__ constexpr int spec_r1(int n) { return n / 2 < 16 ? n / 2 : 16; }
+constexpr int kSpecThreads = 64;
 
 // Launch through cudaLaunchKernelEx; `pdl` marks the launch as a programmatic
 // dependent of the previous kernel in the stream (the kernel calls
@@ -36,6 +37,7 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 }
 
 cudaError_t launch_spec(const Params& p, cudaStream_t st);
+cudaError_t launch_spec_combine(const Params& p, cudaStream_t st);
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
 size_t fft_smem_bytes(const Params& p);

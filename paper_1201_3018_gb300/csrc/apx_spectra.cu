@@ -1,13 +1,16 @@
 // apx_spectra.cu -- kernel preparation of the FFT core (Section IV
 // "Initialization": the kernel is prepared once per request).
 //
-// CTA 0: the FP32 spectrum H[k] = FFT_n(taps)[k] / (4m), k in [0, m],
-// n = W_block = 2m, through the shared-memory FFT on 1024 threads (radix-4 or
-// radix-8 passes, one butterfly per thread).
-// CTA 1: the kernel statistics (||k||_inf, second moment) and the exact
-// ||kbar||_1 of every packing candidate, for the selection in the block kernel.
-// Two SMs busy; the block kernel, launched as this launch's programmatic
-// dependent, fills the rest of the GPU meanwhile.
+// The FP32 spectrum H[k] = FFT_n(taps)[k] / (4m), k in [0, m], n = W_block = 2m,
+// in two small launches that run ahead of the block kernel:
+//   k_spec:   CTA r < R1 transforms the decimated taps h[r], h[r+R1], ... (n/R1
+//             points) in shared memory: Y_r = FFT_{n/R1}(h[r::R1]);
+//             CTA R1 publishes the kernel statistics (||k||_inf, second moment)
+//             and the exact ||kbar||_1 of every packing candidate.
+//   k_combine: H[k] = sum_{r < R1} W_n^(r k) Y_r[k mod n/R1]  (the last
+//             decimation-in-time stage), one thread per frequency.
+// Each launch is the programmatic dependent of the one before it; the block
+// kernel waits for k_combine only where it multiplies by H.
 #include "apx_block.cuh"
 #include "apx_launch.h"
 
@@ -17,7 +20,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     pdl_trigger();
-    if (blockIdx.x == 1) {
+    const int n = p.Wb, R1 = spec_r1(n), ns = n / R1;
+    if ((int)blockIdx.x == R1) {
         const KStats ks = kernel_stats(p, sh);
         double l1s[kMaxCand] = {0.0, 0.0, 0.0};
         const bool ok = !ks.bad && ks.Mk > 0.f;
@@ -33,21 +37,41 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p) {
         }
         return;
     }
-    auto tap = [&](int n) -> float { return ktap(p, n); };
-    spectrum_of<float>(tap, p.Wb, p.Wb, p.tw32, p.Hfull, reinterpret_cast<float2*>(smem));
+    const int r = blockIdx.x;
+    float2* Z = reinterpret_cast<float2*>(smem);
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) Z[pad16(j)] = make_float2(ktap(p, r + j * R1), 0.f);
+    __syncthreads();
+    fft_smem<float2, false>(Z, ns, p.tw32, n);
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) p.Ysub[r * ns + k] = Z[pad16(fft_perm<float2>(k, ns))];
+}
+
+__global__ void __launch_bounds__(256) k_combine(const Params p) {
+    pdl_trigger();
+    pdl_wait();  // the decimated sub-spectra
+    const int n = p.Wb, m = n / 2, R1 = spec_r1(n), ns = n / R1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > m) return;
+    float2 acc = make_float2(0.f, 0.f);
+    const int kk = k & (ns - 1);
+    for (int r = 0; r < R1; ++r) {
+        const float2 y = __ldcg(&p.Ysub[r * ns + kk]);
+        const float2 w = __ldg(&p.tw32[(r * k) & (n - 1)]);
+        acc.x = fmaf(y.x, w.x, fmaf(-y.y, w.y, acc.x));
+        acc.y = fmaf(y.x, w.y, fmaf(y.y, w.x, acc.y));
+    }
+    const float scale = 1.f / (float)(4 * m);
+    p.Hfull[k] = make_float2(acc.x * scale, acc.y * scale);
 }
 
 cudaError_t launch_spec(const Params& p, cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev;
-    cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
-    const size_t smem = sizeof(float2) * padded_len(p.Wb / 2);
-    return launch_k(k_spec, dim3(2), dim3(kSpecThreads), smem, st, false, p);
+    const int n = p.Wb, R1 = spec_r1(n);
+    const size_t smem = sizeof(float2) * padded_len(n / R1);
+    return launch_k(k_spec, dim3(R1 + 1), dim3(kSpecThreads), smem, st, false, p);
+}
+
+cudaError_t launch_spec_combine(const Params& p, cudaStream_t st) {
+    const int m = p.Wb / 2;
+    return launch_k(k_combine, dim3((m + 1 + 255) / 256), dim3(256), 0, st, true, p);
 }
 
 }  // namespace apx
