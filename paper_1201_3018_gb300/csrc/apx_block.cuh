@@ -100,14 +100,23 @@ struct KStats {
     double sig2k;
 };
 
-// ||k||_inf and the kernel's second moment over its N taps (block-wide).
+// ||k||_inf and the kernel's second moment over its N taps (block-wide); taps
+// are fetched 8 per thread at a time so the loads overlap.
+constexpr int kTapBatch = 8;
 __device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
     float m = 0.f;
     int bad = 0;
-    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
-        const float a = fabsf(ktap(p, n));
-        if (!(a <= 3.402823466e38f)) bad = 1;
-        m = fmaxf(m, a);
+    const int step = kTapBatch * blockDim.x;
+    for (int n0 = threadIdx.x; n0 < p.N; n0 += step) {
+        float v[kTapBatch];
+#pragma unroll
+        for (int u = 0; u < kTapBatch; ++u) v[u] = ktap(p, n0 + u * blockDim.x);
+#pragma unroll
+        for (int u = 0; u < kTapBatch; ++u) {
+            const float a = fabsf(v[u]);
+            if (!(a <= 3.402823466e38f)) bad = 1;
+            m = fmaxf(m, a);
+        }
     }
     KStats k;
     k.Mk = block_reduce<float, true>(m, sh.redf);
@@ -116,7 +125,13 @@ __device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
     if (!k.bad && k.Mk > 0.f) {
         const FxScale f = fx_scale(k.Mk);
         long long acc = 0;
-        for (int n = threadIdx.x; n < p.N; n += blockDim.x) acc += fx_sq(f, ktap(p, n));
+        for (int n0 = threadIdx.x; n0 < p.N; n0 += step) {
+            float v[kTapBatch];
+#pragma unroll
+            for (int u = 0; u < kTapBatch; ++u) v[u] = ktap(p, n0 + u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < kTapBatch; ++u) acc += fx_sq(f, v[u]);
+        }
         acc = block_reduce<long long, false>(acc, sh.redl);
         k.sig2k = fx_moment(acc, f, p.N, sh);
     }
@@ -134,12 +149,16 @@ __device__ __forceinline__ long long kbar_int(const Params& p, const Cand& c, fl
     if (c.blk == APX_BLK_SYM) return kq(p, ck, 2 * n + 1) + (kq(p, ck, 2 * n) << c.b);
     return kq(p, ck, n);
 }
-// ||kbar||_1, exact (block-wide).
+// ||kbar||_1, exact (block-wide), packed taps fetched in batches.
 __device__ inline long long kbar_l1(const Params& p, const Cand& c, float ck, Shared& sh) {
     long long l1 = 0;
-    for (int n = threadIdx.x; n < c.nk; n += blockDim.x) {
-        const long long v = kbar_int(p, c, ck, n);
-        l1 += v < 0 ? -v : v;
+    const int step = kTapBatch * blockDim.x;
+    for (int n0 = threadIdx.x; n0 < c.nk; n0 += step) {
+        long long v[kTapBatch];
+#pragma unroll
+        for (int u = 0; u < kTapBatch; ++u) v[u] = kbar_int(p, c, ck, n0 + u * blockDim.x);
+#pragma unroll
+        for (int u = 0; u < kTapBatch; ++u) l1 += v[u] < 0 ? -v[u] : v[u];
     }
     return block_reduce<long long, false>(l1, sh.redl);
 }

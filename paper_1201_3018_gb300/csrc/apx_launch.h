@@ -15,7 +15,7 @@ constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (stati
 __host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 32 > 32 ? Wb / 32 : 32; }
 // FFT core kernel spectrum: R1 decimated sub-transforms of n / R1 points.
 __host__ __device__ constexpr int spec_r1(int n) { return n / 2 < 16 ? n / 2 : 16; }
-constexpr int kSpecThreads = 64;
+constexpr int kSpecThreads = 256;
 
 // Launch through cudaLaunchKernelEx; `pdl` marks the launch as a programmatic
 // dependent of the previous kernel in the stream (the kernel calls

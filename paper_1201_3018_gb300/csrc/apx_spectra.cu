@@ -53,11 +53,20 @@ __global__ void __launch_bounds__(256) k_combine(const Params p) {
     if (k > m) return;
     float2 acc = make_float2(0.f, 0.f);
     const int kk = k & (ns - 1);
-    for (int r = 0; r < R1; ++r) {
-        const float2 y = __ldcg(&p.Ysub[r * ns + kk]);
-        const float2 w = __ldg(&p.tw32[(r * k) & (n - 1)]);
-        acc.x = fmaf(y.x, w.x, fmaf(-y.y, w.y, acc.x));
-        acc.y = fmaf(y.x, w.y, fmaf(y.y, w.x, acc.y));
+    float2 y[16], w[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        if (r < R1) {
+            y[r] = __ldcg(&p.Ysub[r * ns + kk]);
+            w[r] = __ldg(&p.tw32[(r * k) & (n - 1)]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        if (r < R1) {
+            acc.x = fmaf(y[r].x, w[r].x, fmaf(-y[r].y, w[r].y, acc.x));
+            acc.y = fmaf(y[r].x, w[r].y, fmaf(y[r].y, w[r].x, acc.y));
+        }
     }
     const float scale = 1.f / (float)(4 * m);
     p.Hfull[k] = make_float2(acc.x * scale, acc.y * scale);
