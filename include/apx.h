@@ -159,6 +159,32 @@ int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
 /* Static string naming a status code. */
 const char* apx_strerror(int status);
 
+/* ---- allocation-free FFT core ---------------------------------------------
+ * The paper has no counterpart: this is a deployment variant of apx_conv with
+ * the FFT core for callers that may not allocate device memory once they are
+ * running -- a real-time audio callback, a plug-in inside a host application
+ * whose allocator owns the GPU, code that runs while another library holds the
+ * device's memory pool.  It takes no context and calls no cudaMalloc, cudaFree
+ * or other allocating routine: all of its scratch (twiddle tables, kernel
+ * spectra, kernel statistics, claim words) lives in one fixed device array of
+ * about 490 KB that every GPU loading the library keeps until the process
+ * exits.
+ *   s_in, k, r_out : device pointers as for apx_conv (L, N and L+N-1 floats)
+ *   mode           : op | APX_CORE_FFT | pack bits (APX_PACK_AUTO uses
+ *                    snr_target_db); the direct core is rejected (APX_ERR_ARG)
+ *   W_block        : a power of two up to 8192; larger -> APX_ERR_WBLOCK
+ * Results equal apx_conv's for the same arguments (integer domain exactly,
+ * FP32 outputs within rounding).  Non-finite input yields NaN outputs for the
+ * affected blocks; there is no status word to read back.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and fills the twiddle tables; a call with a W_block
+ * different from the previous one on that device refills them on `stream`.
+ * Make the first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (different streams, or several host threads)
+ * race and must be serialised by the caller. */
+int apx_conv_fft_static(const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block, uint32_t mode,
+                        double snr_target_db, float* r_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,7 @@ SIGNATURES = {
     "apx_launch_count": (_i64, [_vp]),
     "apx_strerror": (C.c_char_p, [C.c_int]),
     "apx_profile": (C.c_int, [_vp, C.c_int]),
+    "apx_conv_fft_static": (C.c_int, [_vp, _i64, _vp, _i32, _i32, _u32, _d, _vp, _vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft")
@@ -103,6 +104,14 @@ def _dev_f32(t, name):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
     return t
+
+
+def apx_conv_fft_static(s, k, W_block, mode, snr_db, r, stream=None):
+    """Allocation-free FFT-core call (no context): s, k, r are CUDA float32
+    tensors on the current device."""
+    _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+    return _check("apx_conv_fft_static", lib().apx_conv_fft_static(_ptr(s), s.numel(), _ptr(k), k.numel(), W_block,
+                                                                   mode, float(snr_db), _ptr(r), _stream(stream)))
 
 
 class Context:

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "apx_launch.h"
@@ -555,3 +556,134 @@ const char* apx_strerror(int s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free FFT core.
+//
+// For callers that may not allocate device memory after start-up (a real-time
+// audio callback, a host application whose allocator owns the device, code
+// running while another library holds the memory pool): every scratch buffer
+// of the FFT core lives in one file-scope device array of fixed size, sized
+// for W_block up to kStaticWbMax.  The array belongs to every GPU that loads
+// the library until the process exits.
+namespace {
+
+constexpr int kStaticWbMax = 8192;
+constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kSOffFlags = 0;  // status, claim[3], ready[3]
+constexpr size_t kSOffKInfo = kSOffFlags + 256;
+constexpr size_t kSOffHfull = kSOffKInfo + al256(sizeof(KInfo));
+constexpr size_t kSOffYsub = kSOffHfull + al256(sizeof(float2) * (kStaticWbMax / 2 + 1));
+constexpr size_t kSOffTw32 = kSOffYsub + al256(sizeof(float2) * kStaticWbMax);
+constexpr size_t kSOffTw64 = kSOffTw32 + al256(sizeof(float2) * kStaticWbMax);
+constexpr size_t kSOffHc = kSOffTw64 + al256(sizeof(double2) * kStaticWbMax);
+constexpr size_t kSHcBytes = al256(sizeof(double2) * (kStaticWbMax / 2 + 1));
+constexpr size_t kStaticBytes = kSOffHc + kMaxCand * kSHcBytes;  // about 490 KB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_apx_scratch[kStaticBytes];
+
+namespace {
+
+struct StaticDevice {
+    unsigned char* base = nullptr;  // device address of g_apx_scratch on this device
+    int tw_wb = 0;                  // W_block the twiddle tables hold
+    unsigned epoch = 0;             // call number (claims of on-demand spectra)
+};
+std::mutex g_static_mu;
+StaticDevice g_static[64];
+
+// exp(-2 pi i t / Wb) from sincospi of the exact ratio 2t/Wb.
+__global__ void k_twiddles(double2* t64, float2* t32, int Wb) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Wb) return;
+    double sn, cs;
+    sincospi(2.0 * (double)t / (double)Wb, &sn, &cs);
+    t64[t] = make_double2(cs, -sn);
+    t32[t] = make_float2((float)cs, (float)-sn);
+}
+
+}  // namespace
+
+extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
+                                   uint32_t mode, double snr_target_db, float* r_out, void* stream) {
+    if (!s_in || !k || !r_out) return APX_ERR_ARG;
+    if ((mode & 0xF0u) != APX_CORE_FFT) return APX_ERR_ARG;
+    if (W_block > kStaticWbMax) return APX_ERR_WBLOCK;
+    Plan pl;
+    int rc = plan(L, N, W_block, mode, &pl);
+    if (rc) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APX_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    unsigned char* base;
+    unsigned epoch;
+    bool need_tw;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        StaticDevice& sd = g_static[dev];
+        if (!sd.base) {  // first call on this device: the array's device address
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_apx_scratch) != cudaSuccess || !ptr) return APX_ERR_CUDA;
+            sd.base = (unsigned char*)ptr;
+        }
+        if (++sd.epoch == 0) sd.epoch = 1;
+        need_tw = sd.tw_wb != W_block;
+        sd.tw_wb = W_block;
+        base = sd.base;
+        epoch = sd.epoch;
+    }
+
+    // Candidates as in apx_conv: per-block choice under the target, or a forced
+    // packing at the largest S_q = K_q its bound admits, or none.
+    Params p;
+    memset(&p, 0, sizeof p);
+    const uint32_t pack = mode & 0xF00u;
+    int nc = 0;
+    if (pack == APX_PACK_AUTO) {
+        const int order[3] = {APX_BLK_SYM, APX_BLK_ASYM3, APX_BLK_ASYM2};
+        for (int j = 0; j < 3; ++j) {
+            int Q = qmax_fft(order[j], pl.Nodd, W_block);
+            if (Q >= 1) p.cand[nc++] = make_cand(order[j], Q, Q, pl.Nodd, W_block);
+        }
+    } else if (pack != APX_PACK_NONE) {
+        int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
+        int Q = qmax_fft(blk, pl.Nodd, W_block);
+        if (Q < 1) return APX_ERR_RANGE;
+        p.cand[nc++] = make_cand(blk, Q, Q, pl.Nodd, W_block);
+    }
+    p.ncand = nc;
+    p.autosel = pack == APX_PACK_AUTO;
+    p.thr = pow(10.0, snr_target_db / 10.0);
+    p.s = s_in; p.L = L; p.k = k; p.N = N; p.Nodd = pl.Nodd; p.Wb = W_block; p.W = pl.W; p.head = pl.head;
+    p.fft = 1; p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
+    p.P = pl.P; p.out_len = L + N - 1;
+    p.r = r_out;
+    p.status = (unsigned*)(base + kSOffFlags);
+    p.claim = p.status + 1;
+    p.ready = p.status + 1 + kMaxCand;
+    p.epoch = epoch;
+    p.ki = (KInfo*)(base + kSOffKInfo);
+    p.Hfull = (float2*)(base + kSOffHfull);
+    p.Ysub = (float2*)(base + kSOffYsub);
+    p.tw32 = (const float2*)(base + kSOffTw32);
+    p.tw64 = (const double2*)(base + kSOffTw64);
+    for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)(base + kSOffHc + j * kSHcBytes);
+    const size_t smem = fft_smem_bytes(p);
+    if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
+
+    cudaError_t e = cudaSuccess;
+    if (need_tw) {
+        k_twiddles<<<(W_block + 255) / 256, 256, 0, st>>>((double2*)(base + kSOffTw64), (float2*)(base + kSOffTw32),
+                                                          W_block);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_spec(p, st);
+    if (e == cudaSuccess) e = launch_spec_combine(p, st);
+    if (e == cudaSuccess) e = launch_fft(p, smem, st);
+    return cuda_status(e);
+}
+
+
