@@ -53,6 +53,7 @@ extern "C" {
 #define APX_OP_XCORR     0x001u  /* x[l+N-1] = sum_n s[n+l] t[n], l in [-(N-1), L-1] */
 #define APX_CORE_DIRECT  0x000u  /* time-domain block convolution             */
 #define APX_CORE_FFT     0x010u  /* frequency-domain block convolution (W_block a power of two) */
+#define APX_CORE_AUTO    0x020u  /* batched calls only: the library picks the core */
 #define APX_PACK_AUTO    0x000u  /* per-block choice under snr_target_db (Section IV.D) */
 #define APX_PACK_NONE    0x100u  /* full precision, FP32                        */
 #define APX_PACK_SYM     0x200u  /* symmetric packing, Eqs. (4)-(5)            */
@@ -158,6 +159,43 @@ int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
 
 /* Static string naming a status code. */
 const char* apx_strerror(int status);
+
+/* ---- batched calls ---------------------------------------------------------
+ * Many independent signals in one call (Section II: overlap-save blocks are
+ * independent, so the blocks of all requests share each launch).  Requests are
+ * grouped by core and W_block; each group is one launch of the direct kernel
+ * or three of the FFT core (spectrum, combine, block kernel).  Each request's
+ * result equals that of the corresponding single call. */
+typedef struct {
+    const float* s_in;      /* device, L samples                                  */
+    int64_t L;
+    const float* k;         /* device, N taps (template for cross-correlation)    */
+    int32_t N;
+    float* r_out;           /* device, L+N-1 outputs                              */
+    int32_t W_block;        /* 0: the library's default for the core and N        */
+    uint32_t mode;          /* op | core (APX_CORE_AUTO allowed) | pack           */
+    double snr_target_db;   /* APX_PACK_AUTO: per-block target (Section IV.D)     */
+    int32_t S_q, K_q;       /* > 0 with SYM / ASYM2 / ASYM3: fixed quantiser      */
+} apx_request;
+
+/* Enqueue all requests on `stream`.  Errors: any single-call error of a request
+ * (the whole batch is rejected before anything is enqueued), APX_ERR_OOM,
+ * APX_ERR_BUDGET, APX_ERR_CUDA.  The context's batch workspace is reused by the
+ * next batched call: calls on different streams must not overlap. */
+int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream);
+
+/* A batch captured once into a CUDA graph and replayed: apx_graph_create plans
+ * the requests, gives the graph its own workspace (device memory allocated
+ * here, not from the context budget), and captures the launches; every
+ * apx_graph_launch recomputes everything from the current contents of the
+ * requests' inputs into their outputs (the pointers are fixed at creation).
+ * The context must outlive the graph (its status word reports non-finite
+ * input through apx_sync). */
+typedef struct apx_graph apx_graph;
+int apx_graph_create(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream, apx_graph** out);
+int apx_graph_launch(apx_graph* graph, void* stream);
+int64_t apx_graph_launch_count(const apx_graph* graph);  /* kernel launches per replay */
+void apx_graph_destroy(apx_graph* graph);
 
 /* ---- allocation-free FFT core ---------------------------------------------
  * The paper has no counterpart: this is a deployment variant of apx_conv with

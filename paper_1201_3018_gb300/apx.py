@@ -22,13 +22,22 @@ _lib = None
 APX_OK, APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE, APX_ERR_NONFINITE = 0, -1, -2, -3, -4
 APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA, APX_ERR_TIMEOUT = -5, -6, -7, -8
 OP_CONV, OP_XCORR = 0x000, 0x001
-CORE_DIRECT, CORE_FFT = 0x000, 0x010
+CORE_DIRECT, CORE_FFT, CORE_AUTO = 0x000, 0x010, 0x020
 PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
 BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
 
 STATS_DTYPE = np.dtype([("mode", "<i4"), ("Sq", "<i4"), ("Kq", "<i4"), ("b", "<i4"), ("cs", "<f4"),
                         ("maxabs", "<f4"), ("sigma2", "<f8"), ("snr_pred_db", "<f8"), ("fft_err", "<f8")])
 assert STATS_DTYPE.itemsize == 48
+
+class Request(C.Structure):
+    """apx_request of include/apx.h."""
+    _fields_ = [("s_in", C.c_void_p), ("L", C.c_int64), ("k", C.c_void_p), ("N", C.c_int32),
+                ("r_out", C.c_void_p), ("W_block", C.c_int32), ("mode", C.c_uint32), ("snr_target_db", C.c_double),
+                ("S_q", C.c_int32), ("K_q", C.c_int32)]
+
+
+assert C.sizeof(Request) == 64
 
 # (restype, argtypes) of every entry point in include/apx.h
 _vp, _i32, _i64, _u32, _d, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double, C.c_size_t
@@ -45,6 +54,11 @@ SIGNATURES = {
     "apx_strerror": (C.c_char_p, [C.c_int]),
     "apx_profile": (C.c_int, [_vp, C.c_int]),
     "apx_conv_fft_static": (C.c_int, [_vp, _i64, _vp, _i32, _i32, _u32, _d, _vp, _vp]),
+    "apx_conv_batch": (C.c_int, [_vp, _vp, _i32, _vp]),
+    "apx_graph_create": (C.c_int, [_vp, _vp, _i32, _vp, C.POINTER(C.c_void_p)]),
+    "apx_graph_launch": (C.c_int, [_vp, _vp]),
+    "apx_graph_launch_count": (_i64, [_vp]),
+    "apx_graph_destroy": (None, [_vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft")
@@ -104,6 +118,30 @@ def _dev_f32(t, name):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
     return t
+
+
+class Graph:
+    """A captured batch (apx_graph)."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def launch(self, stream=None):
+        return _check("apx_graph_launch", lib().apx_graph_launch(self._h, _stream(stream)))
+
+    def launch_count(self):
+        return lib().apx_graph_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apx_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apx_conv_fft_static(s, k, W_block, mode, snr_db, r, stream=None):
@@ -177,6 +215,31 @@ class Context:
 
     def apx_sync(self, stream=None):
         return _check("apx_sync", lib().apx_sync(self._h, _stream(stream)))
+
+    # ---------------------------------------------------------------- batches
+    @staticmethod
+    def make_requests(items):
+        """items: dicts with s, k, r (CUDA float32 tensors), mode, and optional
+        W_block, snr_db, Sq, Kq.  Returns a ctypes array of Request."""
+        arr = (Request * len(items))()
+        for q, it in zip(arr, items):
+            s, k, r = it["s"], it["k"], it["r"]
+            _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+            q.s_in, q.L, q.k, q.N, q.r_out = s.data_ptr(), s.numel(), k.data_ptr(), k.numel(), r.data_ptr()
+            q.W_block = int(it.get("W_block", 0))
+            q.mode = int(it.get("mode", 0))
+            q.snr_target_db = float(it.get("snr_db", 0.0))
+            q.S_q, q.K_q = int(it.get("Sq", 0)), int(it.get("Kq", 0))
+        return arr
+
+    def apx_conv_batch(self, reqs, stream=None):
+        return _check("apx_conv_batch", lib().apx_conv_batch(self._h, reqs, len(reqs), _stream(stream)))
+
+    def graph(self, reqs, stream=None):
+        """Capture the batch once; returns a Graph (launch() replays it)."""
+        h = C.c_void_p()
+        _check("apx_graph_create", lib().apx_graph_create(self._h, reqs, len(reqs), _stream(stream), C.byref(h)))
+        return Graph(h)
 
     # ---------------------------------------------------------------- convenience
     def conv(self, s, k, W_block, mode=0, snr_db=None, Sq=None, Kq=None, want_int=False, want_stats=False,

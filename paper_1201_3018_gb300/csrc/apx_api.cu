@@ -32,6 +32,10 @@ struct apx_ctx {
     size_t in_use = 0;
     int64_t launches = 0;
     DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
+    void* hstage = nullptr;             // pinned staging for batch parameters
+    size_t hstage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;     // last upload from hstage
     int tw_wb = 0;          // W_block the twiddle tables were built for
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     // tracing
@@ -229,9 +233,10 @@ size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl) 
     return (size_t)dl->offKb + (size_t)8 * nkb;
 }
 
-// exp(-2 pi i t / Wb), t in [0, Wb), from long double arithmetic.
+// exp(-2 pi i t / Wb), t in [0, Wb), from long double arithmetic.  One table
+// for the largest W_block seen; smaller transforms index it with a stride.
 int ensure_twiddles(apx_ctx* c, int Wb, cudaStream_t st) {
-    if (c->tw_wb == Wb) return APX_OK;
+    if (c->tw_wb >= Wb) return APX_OK;
     int rc = ensure(c, c->tw64, sizeof(double2) * Wb);
     if (!rc) rc = ensure(c, c->tw32, sizeof(float2) * Wb);
     if (rc) return rc;
@@ -300,11 +305,13 @@ bool device_pointers_set(const Params& p) {
     return true;
 }
 
-// Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
-int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
-        int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
-        apx_block_stats* st, cudaStream_t stream) {
-    if (!ctx || !s || !k || !r) return APX_ERR_ARG;
+// Host half of a call: validate, plan (Section III, Eq. 17), choose the
+// packing candidates and the block kernel's shared memory.  Pointers to the
+// workspace are filled in by the caller.
+int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
+                int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
+                apx_block_stats* st, Params* out, size_t* smem_out) {
+    if (!s || !k || !r) return APX_ERR_ARG;
     Plan pl;
     int rc = plan(L, N, Wb, mode, &pl);
     if (rc) return rc;
@@ -319,11 +326,10 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         S = K = Q;
         sel_kind = 1;
     }
-    DeviceGuard dg(ctx->device);
-
-    Params p;
+    Params& p = *out;
     memset(&p, 0, sizeof p);
-    p.s = s; p.L = L; p.N = N; p.Nodd = pl.Nodd; p.Wb = Wb; p.W = pl.W; p.head = pl.head; p.fft = pl.fft;
+    p.s = s; p.L = L; p.k = k; p.N = N; p.Nodd = pl.Nodd; p.Wb = Wb; p.W = pl.W; p.head = pl.head; p.fft = pl.fft;
+    p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
     p.P = pl.P; p.out_len = L + N - 1;
     p.r = r; p.rq = rq; p.st = st;
     p.autosel = sel_kind == 0;
@@ -343,7 +349,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     }
 
     // Shared memory of the block kernel for this candidate set.
-    size_t smem;
+    size_t smem = 0;
     if (!pl.fft) {
         smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
         while (smem > (size_t)kMaxSmem && nc > 0 && sel_kind == 0) {
@@ -359,6 +365,22 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     }
     p.ncand = nc;
     if (pl.fft) smem = fft_smem_bytes(p);
+    *smem_out = smem;
+    return APX_OK;
+}
+
+// Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
+int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
+        int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
+        apx_block_stats* st, cudaStream_t stream) {
+    if (!ctx) return APX_ERR_ARG;
+    Params p;
+    size_t smem = 0;
+    int rc = make_params(s, L, k, N, Wb, mode, sel_kind, snr_db, S, K, r, rq, st, &p, &smem);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    const int nc = p.ncand;
+    struct { int fft; } pl = {p.fft};
 
     // Workspace: status word, per-candidate claim and ready words, spectra, twiddles.
     rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
@@ -373,8 +395,6 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     if (rc) return rc;
 
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
-    p.k = k;
-    p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
     p.status = (unsigned*)ctx->flags.p;
     p.claim = (unsigned*)ctx->flags.p + 1;
     p.ready = (unsigned*)ctx->flags.p + 1 + kMaxCand;
@@ -383,6 +403,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     p.Ysub = (float2*)ctx->Ysub.p;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
+    p.ntab = ctx->tw_wb;
     if (!device_pointers_set(p)) return APX_ERR_CUDA;
 
     cudaError_t e;
@@ -405,6 +426,206 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
             ctx->launches += 1;
         }
     }
+    return cuda_status(e);
+}
+
+
+// ------------------------------------------------------------------ batched calls
+// Library defaults when a request leaves the core or W_block open (the
+// autotuner in tune.py measures and passes explicit choices): the FFT core
+// above 64 taps, W_block the power of two at or above 4 N' (at least 1024).
+int default_core_fft(int Nodd) { return Nodd > 64; }
+int default_wblock(int Nodd) {
+    int w = 1024;
+    while (w < 4 * Nodd && w < kMaxWblock) w <<= 1;
+    while (w - Nodd - 1 < 2 && w < kMaxWblock) w <<= 1;
+    return w;
+}
+
+struct BatchPlan {
+    std::vector<Params> prm;
+    std::vector<size_t> smem;
+    struct Group {
+        int fft, Wb;
+        std::vector<int> reqs;
+        size_t smem = 0;
+        std::vector<int> start_blk, start_spec, start_comb;  // CTA offsets, nreq + 1 each
+        int off_blk = 0, off_spec = 0, off_comb = 0;         // offsets of those tables in the int table
+    };
+    std::vector<Group> groups;
+    std::vector<size_t> arena_off;  // per request
+    size_t arena_bytes = 0;
+    size_t flags_bytes = 0;         // leading part of the arena: claim/ready words of every request
+    int max_wb = 0;
+    std::vector<int> table;         // all CTA tables
+};
+
+size_t al256b(size_t b) { return (b + 255) / 256 * 256; }
+
+// Per-request arena: claim[3], ready[3] | KInfo | Hfull | Ysub | Hc[ncand]
+size_t arena_need(const Params& p) {
+    if (!p.fft) return 0;
+    const size_t m1 = (size_t)p.Wb / 2 + 1;
+    return al256b(sizeof(KInfo)) + al256b(sizeof(float2) * m1) + al256b(sizeof(float2) * (size_t)p.Wb) +
+           (size_t)p.ncand * al256b(sizeof(double2) * m1);
+}
+
+int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
+    if (!reqs || n < 1) return APX_ERR_ARG;
+    bp->prm.resize(n);
+    bp->smem.resize(n);
+    for (int r = 0; r < n; ++r) {
+        const apx_request& q = reqs[r];
+        if (q.N < 1) return APX_ERR_ARG;
+        const int Nodd = (q.N % 2) ? q.N : q.N + 1;
+        uint32_t mode = q.mode;
+        uint32_t core = mode & 0xF0u;
+        if (core == APX_CORE_AUTO) core = default_core_fft(Nodd) ? APX_CORE_FFT : APX_CORE_DIRECT;
+        mode = (mode & ~0xF0u) | core;
+        const int Wb = q.W_block > 0 ? q.W_block : default_wblock(Nodd);
+        const uint32_t pack = mode & 0xF00u;
+        int sel = 0;
+        if (pack == APX_PACK_NONE) sel = 2;
+        else if (pack != APX_PACK_AUTO && q.S_q > 0 && q.K_q > 0) sel = 1;
+        int rc = make_params(q.s_in, q.L, q.k, q.N, Wb, mode, sel, q.snr_target_db, q.S_q, q.K_q, q.r_out, nullptr,
+                             nullptr, &bp->prm[r], &bp->smem[r]);
+        if (rc) return rc;
+    }
+    // group by core and W_block
+    for (int r = 0; r < n; ++r) {
+        const Params& p = bp->prm[r];
+        int g = -1;
+        for (size_t j = 0; j < bp->groups.size(); ++j)
+            if (bp->groups[j].fft == p.fft && bp->groups[j].Wb == p.Wb) g = (int)j;
+        if (g < 0) {
+            bp->groups.emplace_back();
+            bp->groups.back().fft = p.fft;
+            bp->groups.back().Wb = p.Wb;
+            g = (int)bp->groups.size() - 1;
+        }
+        bp->groups[g].reqs.push_back(r);
+        if (bp->smem[r] > bp->groups[g].smem) bp->groups[g].smem = bp->smem[r];
+        if (p.fft && p.Wb > bp->max_wb) bp->max_wb = p.Wb;
+    }
+    // arena: flags for every request first, then each FFT request's buffers
+    bp->flags_bytes = al256b(sizeof(unsigned) * 2 * kMaxCand * (size_t)n);
+    size_t off = bp->flags_bytes;
+    bp->arena_off.resize(n);
+    for (int r = 0; r < n; ++r) {
+        bp->arena_off[r] = off;
+        off += arena_need(bp->prm[r]);
+    }
+    bp->arena_bytes = off;
+    // CTA tables
+    for (auto& G : bp->groups) {
+        int a = 0, b = 0, c = 0;
+        G.start_blk.push_back(0);
+        G.start_spec.push_back(0);
+        G.start_comb.push_back(0);
+        for (int r : G.reqs) {
+            const Params& p = bp->prm[r];
+            a += (int)p.P;
+            G.start_blk.push_back(a);
+            if (G.fft) {
+                b += spec_ctas(p.Wb);
+                c += combine_ctas(p.Wb);
+            }
+            G.start_spec.push_back(b);
+            G.start_comb.push_back(c);
+        }
+        G.off_blk = (int)bp->table.size();
+        bp->table.insert(bp->table.end(), G.start_blk.begin(), G.start_blk.end());
+        G.off_spec = (int)bp->table.size();
+        bp->table.insert(bp->table.end(), G.start_spec.begin(), G.start_spec.end());
+        G.off_comb = (int)bp->table.size();
+        bp->table.insert(bp->table.end(), G.start_comb.begin(), G.start_comb.end());
+    }
+    return APX_OK;
+}
+
+// Point every request at its workspace (arena base, twiddles, status word).
+void bind_batch(BatchPlan* bp, unsigned char* arena, const double2* tw64, const float2* tw32, int ntab,
+                unsigned* status, unsigned epoch) {
+    const int n = (int)bp->prm.size();
+    for (int r = 0; r < n; ++r) {
+        Params& p = bp->prm[r];
+        p.status = status;
+        p.claim = reinterpret_cast<unsigned*>(arena) + 2 * kMaxCand * r;
+        p.ready = p.claim + kMaxCand;
+        p.epoch = epoch;
+        p.tw64 = tw64;
+        p.tw32 = tw32;
+        p.ntab = ntab;
+        if (!p.fft) continue;
+        unsigned char* b = arena + bp->arena_off[r];
+        const size_t m1 = (size_t)p.Wb / 2 + 1;
+        p.ki = (KInfo*)b;
+        b += al256b(sizeof(KInfo));
+        p.Hfull = (float2*)b;
+        b += al256b(sizeof(float2) * m1);
+        p.Ysub = (float2*)b;
+        b += al256b(sizeof(float2) * (size_t)p.Wb);
+        for (int j = 0; j < p.ncand; ++j) {
+            p.cand[j].H = (double2*)b;
+            b += al256b(sizeof(double2) * m1);
+        }
+    }
+}
+
+// The launches of a planned batch, groups one after another on `st`.
+cudaError_t launch_batch(const BatchPlan& bp, const Params* dprm, const int* dtab, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    size_t base = 0;  // the device parameter array holds the requests group by group
+    for (const auto& G : bp.groups) {
+        const int nr = (int)G.reqs.size();
+        const Params* gp = dprm + base;
+        const Params& any = bp.prm[G.reqs[0]];
+        BatchTab tb = {gp, dtab + G.off_blk, nr};
+        if (!G.fft) {
+            e = launch_direct_batch(any, tb, G.start_blk[nr], G.smem, st);
+        } else {
+            BatchTab ts = {gp, dtab + G.off_spec, nr};
+            BatchTab tc = {gp, dtab + G.off_comb, nr};
+            e = launch_spec_batch(any, ts, G.start_spec[nr], st, false);
+            if (e == cudaSuccess) e = launch_combine_batch(any, tc, G.start_comb[nr], st);
+            if (e == cudaSuccess) e = launch_fft_batch(any, tb, G.start_blk[nr], G.smem, st);
+        }
+        if (e != cudaSuccess) return e;
+        base += nr;
+    }
+    return e;
+}
+
+// Parameters in group order (the device array is indexed per group).
+std::vector<Params> grouped_params(const BatchPlan& bp) {
+    std::vector<Params> v;
+    v.reserve(bp.prm.size());
+    for (const auto& G : bp.groups)
+        for (int r : G.reqs) v.push_back(bp.prm[r]);
+    return v;
+}
+
+int stage_upload(apx_ctx* c, const void* src1, size_t n1, void* dst1, const void* src2, size_t n2, void* dst2,
+                 cudaStream_t st) {
+    const size_t need = n1 + n2;
+    if (c->stage_ev) {
+        cudaError_t e = cudaEventSynchronize(c->stage_ev);
+        if (e != cudaSuccess) return cuda_status(e);
+    } else if (cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        return APX_ERR_CUDA;
+    }
+    if (c->hstage_bytes < need) {
+        if (c->hstage) cudaFreeHost(c->hstage);
+        c->hstage = nullptr;
+        c->hstage_bytes = 0;
+        if (cudaMallocHost(&c->hstage, need) != cudaSuccess) { c->hstage = nullptr; return APX_ERR_OOM; }
+        c->hstage_bytes = need;
+    }
+    memcpy(c->hstage, src1, n1);
+    memcpy((char*)c->hstage + n1, src2, n2);
+    cudaError_t e = cudaMemcpyAsync(dst1, c->hstage, n1, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst2, (char*)c->hstage + n1, n2, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, st);
     return cuda_status(e);
 }
 
@@ -436,8 +657,10 @@ void apx_destroy(apx_ctx* c) {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
         DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
-                         &c->tw32, &c->hs, &c->hk, &c->hr};
+                         &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab};
         for (DevBuf* b : all) release(c, *b);
+        if (c->hstage) cudaFreeHost(c->hstage);
+        if (c->stage_ev) cudaEventDestroy(c->stage_ev);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     }
     delete c;
@@ -558,6 +781,109 @@ const char* apx_strerror(int s) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Batched calls and captured graphs.
+struct apx_graph {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* bufs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // arena, params, table, tw64, tw32
+    int64_t launches = 0;
+};
+
+extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
+    if (!ctx) return APX_ERR_ARG;
+    BatchPlan bp;
+    int rc = plan_batch(reqs, n, &bp);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+    if (!rc && bp.max_wb > 0) rc = ensure_twiddles(ctx, bp.max_wb, st);
+    if (!rc) rc = ensure(ctx, ctx->barena, bp.arena_bytes);
+    if (!rc) rc = ensure(ctx, ctx->bparams, sizeof(Params) * (size_t)n);
+    if (!rc) rc = ensure(ctx, ctx->btab, sizeof(int) * bp.table.size());
+    if (rc) return rc;
+    bind_batch(&bp, (unsigned char*)ctx->barena.p, (const double2*)ctx->tw64.p, (const float2*)ctx->tw32.p,
+               ctx->tw_wb, (unsigned*)ctx->flags.p, 1u);
+    const std::vector<Params> gp = grouped_params(bp);
+    rc = stage_upload(ctx, gp.data(), sizeof(Params) * gp.size(), ctx->bparams.p, bp.table.data(),
+                      sizeof(int) * bp.table.size(), ctx->btab.p, st);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(ctx->barena.p, 0, bp.flags_bytes, st);  // claim/ready words
+    if (e == cudaSuccess) e = launch_batch(bp, (const Params*)ctx->bparams.p, (const int*)ctx->btab.p, st);
+    for (const auto& G : bp.groups) ctx->launches += G.fft ? 3 : 1;
+    return cuda_status(e);
+}
+
+extern "C" int apx_graph_create(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream, apx_graph** out) {
+    if (!ctx || !out) return APX_ERR_ARG;
+    *out = nullptr;
+    BatchPlan bp;
+    int rc = plan_batch(reqs, n, &bp);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+    if (!rc && bp.max_wb > 0) rc = ensure_twiddles(ctx, bp.max_wb, (cudaStream_t)stream);
+    if (rc) return rc;
+    apx_graph* g = new apx_graph();
+    g->device = ctx->device;
+    const size_t ntw = (size_t)(bp.max_wb > 0 ? ctx->tw_wb : 0);
+    const size_t sizes[5] = {bp.arena_bytes > 0 ? bp.arena_bytes : 256, sizeof(Params) * (size_t)n,
+                             sizeof(int) * bp.table.size(), sizeof(double2) * (ntw ? ntw : 1),
+                             sizeof(float2) * (ntw ? ntw : 1)};
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 5 && e == cudaSuccess; ++b) e = cudaMalloc(&g->bufs[b], sizes[b]);
+    if (e == cudaSuccess && ntw) e = cudaMemcpy(g->bufs[3], ctx->tw64.p, sizes[3], cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && ntw) e = cudaMemcpy(g->bufs[4], ctx->tw32.p, sizes[4], cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) {
+        bind_batch(&bp, (unsigned char*)g->bufs[0], (const double2*)g->bufs[3], (const float2*)g->bufs[4], (int)ntw,
+                   (unsigned*)ctx->flags.p, 1u);
+        const std::vector<Params> gp = grouped_params(bp);
+        e = cudaMemcpy(g->bufs[1], gp.data(), sizes[1], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->bufs[2], bp.table.data(), sizes[2], cudaMemcpyHostToDevice);
+    }
+    cudaStream_t cap = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaMemsetAsync(g->bufs[0], 0, bp.flags_bytes, cap);
+        if (le == cudaSuccess) le = launch_batch(bp, (const Params*)g->bufs[1], (const int*)g->bufs[2], cap);
+        e = cudaStreamEndCapture(cap, &g->graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    for (const auto& G : bp.groups) g->launches += G.fft ? 3 : 1;
+    if (e != cudaSuccess) {
+        apx_graph_destroy(g);
+        return cuda_status(e);
+    }
+    *out = g;
+    return APX_OK;
+}
+
+extern "C" int apx_graph_launch(apx_graph* g, void* stream) {
+    if (!g || !g->exec) return APX_ERR_ARG;
+    DeviceGuard dg(g->device);
+    return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+}
+
+extern "C" int64_t apx_graph_launch_count(const apx_graph* g) { return g ? g->launches : 0; }
+
+extern "C" void apx_graph_destroy(apx_graph* g) {
+    if (!g) return;
+    {
+        DeviceGuard dg(g->device);
+        cudaDeviceSynchronize();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        for (void* b : g->bufs)
+            if (b) cudaFree(b);
+    }
+    delete g;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free FFT core.
 //
 // For callers that may not allocate device memory after start-up (a real-time
@@ -670,6 +996,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     p.Ysub = (float2*)(base + kSOffYsub);
     p.tw32 = (const float2*)(base + kSOffTw32);
     p.tw64 = (const double2*)(base + kSOffTw64);
+    p.ntab = W_block;
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)(base + kSOffHc + j * kSHcBytes);
     const size_t smem = fft_smem_bytes(p);
     if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;

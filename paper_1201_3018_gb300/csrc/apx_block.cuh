@@ -270,9 +270,10 @@ __device__ __forceinline__ R& word(C* Z, int w) {
 }
 
 // H = FFT_n(taps) / (4m), k in [0, m], natural order, through the block FFT;
-// tap(j) gives tap j.  Z is scratch of padded_len(n/2) entries.
+// tap(j) gives tap j; tw holds exp(-2 pi i t / ntab).  Z is scratch of
+// padded_len(n/2) entries.
 template <typename R, typename C, typename F>
-__device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H, C* Z) {
+__device__ void spectrum_of(F tap, int ntab, int n, const C* __restrict__ tw, C* H, C* Z) {
     const int m = n / 2;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         C v;
@@ -281,7 +282,7 @@ __device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H
         Z[pad16(j)] = v;
     }
     __syncthreads();
-    fft_smem<C, false>(Z, m, tw, Wb);
+    fft_smem<C, false>(Z, m, tw, ntab);
     const R scale = (R)1 / (R)(8 * m);
     for (int k = threadIdx.x; k <= m; k += blockDim.x) {
         C X;
@@ -291,7 +292,7 @@ __device__ void spectrum_of(F tap, int Wb, int n, const C* __restrict__ tw, C* H
             X.y = 0;
         } else {
             C Xmk;
-            real_post(Z[pad16(fft_perm<C>(k, m))], Z[pad16(fft_perm<C>(m - k, m))], __ldg(&tw[k * (Wb / n)]), X, Xmk);
+            real_post(Z[pad16(fft_perm<C>(k, m))], Z[pad16(fft_perm<C>(m - k, m))], __ldg(&tw[k * (ntab / n)]), X, Xmk);
         }
         X.x *= scale; X.y *= scale;
         H[k] = X;

@@ -62,11 +62,14 @@ __device__ __forceinline__ void conv_f64(const double* sig, const double* taps, 
 
 __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
-__global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
+template <bool BATCH>
+__global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int s_ci;
-    const long long i = blockIdx.x;
+    __shared__ Params sp;
+    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
+    const Params& p = BATCH ? sp : p0;
     const BlockGeom g = block_geom(p, i);
     const DirectLayout& dl = p.dl;
 
@@ -188,17 +191,30 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p) {
         write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
-cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
+template <bool BATCH>
+static cudaError_t direct_attrs() {
     static int attr_dev = -1;
     int dev;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    if (attr_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_direct<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess) attr_dev = dev;
+    return e;
+}
+
+cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
+    cudaError_t e = direct_attrs<false>();
+    if (e != cudaSuccess) return e;
     if (p.P <= 0) return cudaSuccess;
-    return launch_k(k_direct, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p);
+    const BatchTab none = {nullptr, nullptr, 0};
+    return launch_k(k_direct<false>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
+}
+
+cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {
+    cudaError_t e = direct_attrs<true>();
+    if (e != cudaSuccess) return e;
+    if (ctas <= 0) return cudaSuccess;
+    return launch_k(k_direct<true>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
 }
 
 }  // namespace apx

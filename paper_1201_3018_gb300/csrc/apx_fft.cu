@@ -52,12 +52,14 @@ __device__ __forceinline__ void load_window_regs(const Params& p, long long star
 }
 
 // kVals: window samples per thread (W_block / threads: 16, or 32 at the largest W_block)
-template <int kVals>
-__global__ void __launch_bounds__(512) k_fft(const Params p) {
+template <int kVals, bool BATCH>
+__global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int s_flag;
-    const long long i = blockIdx.x;
+    __shared__ Params sp;
+    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
+    const Params& p = BATCH ? sp : p0;
     const BlockGeom g = block_geom(p, i);
     float xv[kVals];
     load_window_regs(p, g.start, xv);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         for (int v = 0; v < kVals / 2; ++v)
             if (pair_ok(p, v)) Zf[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
         __syncthreads();
-        fft_smem<float2, false>(Zf, mf, p.tw32, p.Wb);
+        fft_smem<float2, false>(Zf, mf, p.tw32, p.ntab);
     }
 
     pdl_wait();  // kernel statistics and FP32 kernel spectrum from the preparation launch
@@ -150,8 +152,8 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
 
     if (ci < 0) {
         // Full precision: finish the FP32 real-FFT convolution.
-        spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, 1, true);
-        fft_smem<float2, true>(Zf, mf, p.tw32, p.Wb);
+        spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, p.ntab / p.Wb, true);
+        fft_smem<float2, true>(Zf, mf, p.tw32, p.ntab);
         for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
             const long long o = g.start + j;
             if (o < 0 || o >= p.out_len) continue;
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
     __syncthreads();  // (also: every thread is done with the speculative FP32 buffer)
     if (role == 1) {
         auto tap = [&](int t) -> double { return (double)kbar_int(p, c, ck, t); };  // Eq. (5) / k~
-        spectrum_of<double>(tap, p.Wb, n, p.tw64, c.H, Z);
+        spectrum_of<double>(tap, p.ntab, n, p.tw64, c.H, Z);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) st_release(&p.ready[ci], p.epoch);
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
         }
     }
     __syncthreads();
-    fft_smem<double2, false>(Z, mm, p.tw64, p.Wb);
+    fft_smem<double2, false>(Z, mm, p.tw64, p.ntab);
 
     if (role == 2) {
         if (threadIdx.x == 0) {
@@ -239,8 +241,8 @@ __global__ void __launch_bounds__(512) k_fft(const Params p) {
             return;
         }
     }
-    spectral_multiply(Z, mm, static_cast<const double2*>(c.H), p.tw64, p.Wb / n, true);
-    fft_smem<double2, true>(Z, mm, p.tw64, p.Wb);
+    spectral_multiply(Z, mm, static_cast<const double2*>(c.H), p.tw64, p.ntab / n, true);
+    fft_smem<double2, true>(Z, mm, p.tw64, p.ntab);
 
     if (threadIdx.x == 0) sh.bcast[2] = 1.0 / ((double)cs * (double)ck);
     __syncthreads();
@@ -269,21 +271,36 @@ size_t fft_smem_bytes(const Params& p) {
     return z32 > z64 ? z32 : z64;
 }
 
-cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
-    if (p.P <= 0) return cudaSuccess;
+template <bool BATCH>
+static cudaError_t fft_attrs() {
     static int attr_dev = -1;
     int dev;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_fft<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fft<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    if (attr_dev == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fft<16, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft<32, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess) attr_dev = dev;
+    return e;
+}
+
+cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
+    if (p.P <= 0) return cudaSuccess;
+    cudaError_t e = fft_attrs<false>();
+    if (e != cudaSuccess) return e;
+    const BatchTab none = {nullptr, nullptr, 0};
     if (p.Wb / fft_threads(p.Wb) > 16)
-        return launch_k(k_fft<32>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
-    return launch_k(k_fft<16>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p);
+        return launch_k(k_fft<32, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
+    return launch_k(k_fft<16, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
+}
+
+cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {
+    if (ctas <= 0) return cudaSuccess;
+    cudaError_t e = fft_attrs<true>();
+    if (e != cudaSuccess) return e;
+    if (any.Wb / fft_threads(any.Wb) > 16)
+        return launch_k(k_fft<32, true>, dim3((unsigned)ctas), dim3(fft_threads(any.Wb)), smem, st, true, any, bt);
+    return launch_k(k_fft<16, true>, dim3((unsigned)ctas), dim3(fft_threads(any.Wb)), smem, st, true, any, bt);
 }
 
 }  // namespace apx

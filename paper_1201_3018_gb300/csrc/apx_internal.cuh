@@ -60,8 +60,9 @@ struct Params {
     float2* Hfull;        // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
     float2* Ysub;         // FFT core: spectra of the R1 decimated tap sequences (n entries)
     KInfo* ki;            // FFT core: kernel statistics from the spectrum launch
-    const double2* tw64;  // twiddles exp(-2 pi i t / W_block), t in [0, W_block)
+    const double2* tw64;  // twiddles exp(-2 pi i t / ntab), t in [0, ntab)
     const float2* tw32;
+    int ntab;             // twiddle table length: a power of two >= W_block
     unsigned* status;     // bit 0: non-finite input seen; bit 1: a bounded wait gave up
     unsigned* claim;      // FFT core, per candidate: last call that claimed building its spectrum
     unsigned* ready;      // FFT core, per candidate: last call whose spectrum is complete
@@ -72,6 +73,28 @@ struct Params {
     Cand cand[kMaxCand];
     DirectLayout dl;      // direct core
 };
+
+// Several requests in one launch: request r owns CTAs [cta_start[r], cta_start[r+1]).
+struct BatchTab {
+    const Params* reqs;
+    const int* cta_start;
+    int nreq;
+};
+
+// The request of this CTA (binary search) and the CTA's index within it; the
+// request's parameters are copied into shared memory `sp`.
+__device__ __forceinline__ long long batch_enter(const BatchTab& t, Params& sp) {
+    int lo = 0, hi = t.nreq;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&t.cta_start[mid]) <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const int* src = reinterpret_cast<const int*>(&t.reqs[lo]);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int w = threadIdx.x; w < (int)(sizeof(Params) / sizeof(int)); w += blockDim.x) dst[w] = __ldg(&src[w]);
+    __syncthreads();
+    return (long long)blockIdx.x - __ldg(&t.cta_start[lo]);
+}
 
 // ------------------------------------------------------------------ reductions
 template <typename T>

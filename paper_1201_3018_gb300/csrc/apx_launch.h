@@ -42,4 +42,14 @@ cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
 size_t fft_smem_bytes(const Params& p);
 
+// Batched launches: `any` is one request's parameters (for the launch shape and
+// as the unused parameter-space copy); the kernels read every request's own
+// parameters through the table.
+int spec_ctas(int Wb);
+int combine_ctas(int Wb);
+cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st);
+cudaError_t launch_spec_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st, bool pdl);
+cudaError_t launch_combine_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st);
+cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st);
+
 }  // namespace apx

@@ -16,12 +16,16 @@
 
 namespace apx {
 
-__global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p) {
+template <bool BATCH>
+__global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
+    __shared__ Params sp;
     pdl_trigger();
+    const int cta = BATCH ? (int)batch_enter(bt, sp) : (int)blockIdx.x;
+    const Params& p = BATCH ? sp : p0;
     const int n = p.Wb, R1 = spec_r1(n), ns = n / R1;
-    if ((int)blockIdx.x == R1) {
+    if (cta == R1) {
         const KStats ks = kernel_stats(p, sh);
         double l1s[kMaxCand] = {0.0, 0.0, 0.0};
         const bool ok = !ks.bad && ks.Mk > 0.f;
@@ -37,19 +41,23 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p) {
         }
         return;
     }
-    const int r = blockIdx.x;
+    const int r = cta;
     float2* Z = reinterpret_cast<float2*>(smem);
     for (int j = threadIdx.x; j < ns; j += blockDim.x) Z[pad16(j)] = make_float2(ktap(p, r + j * R1), 0.f);
     __syncthreads();
-    fft_smem<float2, false>(Z, ns, p.tw32, n);
+    fft_smem<float2, false>(Z, ns, p.tw32, p.ntab);
     for (int k = threadIdx.x; k < ns; k += blockDim.x) p.Ysub[r * ns + k] = Z[pad16(fft_perm<float2>(k, ns))];
 }
 
-__global__ void __launch_bounds__(256) k_combine(const Params p) {
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_combine(const Params p0, const BatchTab bt) {
+    __shared__ Params sp;
     pdl_trigger();
+    const int cta = BATCH ? (int)batch_enter(bt, sp) : (int)blockIdx.x;
+    const Params& p = BATCH ? sp : p0;
     pdl_wait();  // the decimated sub-spectra
     const int n = p.Wb, m = n / 2, R1 = spec_r1(n), ns = n / R1;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = cta * blockDim.x + threadIdx.x;
     if (k > m) return;
     float2 acc = make_float2(0.f, 0.f);
     const int kk = k & (ns - 1);
@@ -58,7 +66,7 @@ __global__ void __launch_bounds__(256) k_combine(const Params p) {
     for (int r = 0; r < 16; ++r) {
         if (r < R1) {
             y[r] = __ldcg(&p.Ysub[r * ns + kk]);
-            w[r] = __ldg(&p.tw32[(r * k) & (n - 1)]);
+            w[r] = __ldg(&p.tw32[(r * k * (p.ntab / n)) & (p.ntab - 1)]);
         }
     }
 #pragma unroll
@@ -75,12 +83,27 @@ __global__ void __launch_bounds__(256) k_combine(const Params p) {
 cudaError_t launch_spec(const Params& p, cudaStream_t st) {
     const int n = p.Wb, R1 = spec_r1(n);
     const size_t smem = sizeof(float2) * padded_len(n / R1);
-    return launch_k(k_spec, dim3(R1 + 1), dim3(kSpecThreads), smem, st, false, p);
+    const BatchTab none = {nullptr, nullptr, 0};
+    return launch_k(k_spec<false>, dim3(R1 + 1), dim3(kSpecThreads), smem, st, false, p, none);
 }
 
 cudaError_t launch_spec_combine(const Params& p, cudaStream_t st) {
     const int m = p.Wb / 2;
-    return launch_k(k_combine, dim3((m + 1 + 255) / 256), dim3(256), 0, st, true, p);
+    const BatchTab none = {nullptr, nullptr, 0};
+    return launch_k(k_combine<false>, dim3((m + 1 + 255) / 256), dim3(256), 0, st, true, p, none);
+}
+
+int spec_ctas(int Wb) { return spec_r1(Wb) + 1; }
+int combine_ctas(int Wb) { return (Wb / 2 + 1 + 255) / 256; }
+
+cudaError_t launch_spec_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st, bool pdl) {
+    const int n = any.Wb, R1 = spec_r1(n);
+    const size_t smem = sizeof(float2) * padded_len(n / R1);
+    return launch_k(k_spec<true>, dim3(ctas), dim3(kSpecThreads), smem, st, pdl, any, bt);
+}
+
+cudaError_t launch_combine_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st) {
+    return launch_k(k_combine<true>, dim3(ctas), dim3(256), 0, st, true, any, bt);
 }
 
 }  // namespace apx
