@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -234,6 +236,72 @@ def cpu_baseline(case, mode_bits):
                       "%d runs, %.1f s wall on %d threads" % (Ls, out, runs, total, cores)}
 
 
+# ---------------------------------------------------------------------------- batched and serving
+def bench_batched(ctx, tuner, dev, steps, flush, stream):
+    """256 signals of log-uniform length in [2^14, 2^20], N in {256, 1024},
+    targets {30, 45, 60} dB: one captured-graph launch per step with the
+    autotuned core and W_block; the full-precision twin as a second graph."""
+    import torch
+    from paper_1201_3018_gb300 import apx, tune
+    case = wl.batched_uneven()
+    tens = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in zip(case.signals, case.kernels)]
+    items = tune.batch_items(case, tuner, dev, tensors=tens)
+    full = tune.batch_items(case, tuner, dev, pack=apx.PACK_NONE, tensors=tens)
+    g = ctx.graph(ctx.make_requests(items), stream=stream)
+    gf = ctx.graph(ctx.make_requests(full), stream=stream)
+    for _ in range(3):
+        g.launch(stream)
+        gf.launch(stream)
+    torch.cuda.synchronize()
+    t = time_steps(lambda: g.launch(stream), steps, flush, stream) / steps
+    tf = time_steps(lambda: gf.launch(stream), steps, flush, stream) / steps
+    outs = sum(len(a) + len(b) - 1 for a, b in zip(case.signals, case.kernels))
+    geo = sorted({(int(len(k)), t_, it["W_block"], "fft" if (it["mode"] & 0xF0) == apx.CORE_FFT else "direct")
+                  for k, t_, it in zip(case.kernels, case.targets, items)})
+    res = {"workload": "batched_uneven: 256 Laplacian(0,0.1) signals, L log-uniform in [2^14,2^20], N in "
+                       "{256,1024} U[-1,1], targets {30,45,60} dB, conv, one captured-graph launch",
+           "outputs_per_step": outs, "value": outs / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
+           "full_precision": {"value": outs / (tf * 1e-3) / 1e9, "ms_per_step": tf},
+           "speedup_vs_full_precision": tf / t, "graph_kernel_launches": g.launch_count(),
+           "tuned": [{"N": a, "target_db": b, "W_block": c, "core": d} for a, b, c, d in geo],
+           "l2": "inputs (190 MB) larger than L2, also flushed between steps"}
+    g.close()
+    gf.close()
+    return res
+
+
+def bench_serving(tuner, dev, seconds):
+    """Poisson arrivals at 2000 req/s, L log-uniform in [2^12, 2^22], N in
+    [64, 8192], targets {30, 45, 60} dB, 40 GB admission budget, 4 streams."""
+    from paper_1201_3018_gb300 import serve
+    seed = wl.SEED_BASE + 5
+    s_host, k_host = serve.host_pools(seed)
+    srv = serve.Server(dev.index or 0, budget_bytes=40 << 30, streams=4, tuner=tuner)
+    try:
+        warm = serve.make_trace(seed + 100, duration_s=0.25)
+        srv.run(warm, s_host, k_host, realtime=False)       # tuner entries, workspaces, pinned pools
+        for op in (0, 1):
+            for t in (30.0, 45.0, 60.0):
+                b = 64
+                while b <= 8192:
+                    srv.choice(b, op, t)
+                    b *= 2
+        trace = serve.make_trace(seed, duration_s=seconds)
+        srv.peak_in_flight = srv.batches = srv.max_overlap = 0
+        done = srv.run(trace, s_host, k_host, realtime=True)
+        p50, p99 = serve.latency_ms(done)
+        span = max(q.done for q in done) - min(q.arrival for q in done)
+        outs = sum(q.L + q.N - 1 for q in done)
+        return {"workload": "serving: Poisson 2000 req/s for %.1f s, conv/xcorr, L log-uniform [2^12,2^22], "
+                            "N log-uniform [64,8192], targets {30,45,60} dB, 40 GB budget" % seconds,
+                "requests": len(done), "p50_ms": p50, "p99_ms": p99, "value": outs / span / 1e9, "unit": UNIT,
+                "batches": srv.batches, "max_batches_in_flight": srv.max_overlap,
+                "peak_in_flight_bytes": srv.peak_in_flight,
+                "latency": "arrival to result in pinned host memory (H2D, kernels, D2H included)"}
+    finally:
+        srv.close()
+
+
 # ---------------------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -343,6 +411,13 @@ def main():
     full_value = whole_job_gsamples(out_len, world, t_full_ms / args.steps)
     e2e_value = whole_job_gsamples(out_len, world, t_e2e_ms / args.steps)
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        from paper_1201_3018_gb300 import tune
+        tuner = tune.Tuner(ctx)
+        extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
+        extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
+
     if rank != 0:
         ctx.close()
         if dist:
@@ -392,7 +467,8 @@ def main():
         "block_modes": {"full": hist[0], "sym": hist[1], "asym2": hist[2], "asym3": hist[3], "zero": hist[4],
                         "nonfinite": hist[5]},
         "snr_vs_full_db": snr_vs_full,
-        "serving": {"p50_ms": None, "p99_ms": None},
+        "serving": extras.get("serving", {"p50_ms": None, "p99_ms": None}),
+        "batched": extras.get("batched"),
         "kernel_ms_per_step": {ph: prof[ph][0] / args.steps for ph in prof},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (L + N),

@@ -1,0 +1,200 @@
+"""Serving loop with continuous batching.
+
+Requests (convolution or cross-correlation of a signal with a kernel under an
+SNR target, Section IV.D) arrive over time.  The scheduler admits, in arrival
+order, every waiting request whose device buffers fit the memory budget next to
+the work already on the GPU, groups the admitted ones into one batched call
+(apx_conv_batch: one launch per core and W_block group), and issues it on the
+next free stream.  Requests that arrive while earlier batches are on the GPU
+are admitted into later batches as streams and memory free up, so their work
+overlaps on the device.  Every request copies its input from pinned host
+memory and reads its result back into pinned host memory; its latency is
+completion (the batch's event observed done) minus arrival.
+
+Each stream has its own library context, so the workspaces of batches in
+flight never alias; a request's result does not depend on what else shares
+its batch (the batched kernels take each request's parameters from its own
+table entry).  Core and W_block per kernel length come from the autotuner
+(tune.Tuner, one measurement per power-of-two bucket of N) or the library
+default.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    t: float              # arrival time, seconds from the start of the trace
+    L: int
+    N: int
+    xcorr: bool
+    target: float
+    s_off: int            # offset of the signal in the host pool
+    k_id: int             # template index
+    arrival: float = 0.0  # wall clock of arrival
+    done: float = 0.0     # wall clock of completion
+    W_block: int = 0      # what was launched (0: library default)
+    mode: int = 0
+    out: object = None    # pinned host result
+
+
+def device_bytes(q) -> int:
+    """Device memory a request holds while in flight: signal, kernel, result."""
+    return 4 * (q.L + q.N + q.L + q.N - 1)
+
+
+def admit(waiting_bytes, in_flight: int, budget: int, max_batch: int) -> int:
+    """How many of the waiting requests (arrival order) the next batch takes.
+
+    A request is admitted while the bytes in flight plus the batch so far plus
+    its own stay within the budget.  A request larger than the whole budget is
+    admitted alone once nothing else is in flight, so it cannot starve."""
+    n, used = 0, 0
+    for b in waiting_bytes:
+        if n >= max_batch:
+            break
+        if in_flight + used + b > budget and (n > 0 or in_flight > 0):
+            break
+        used += b
+        n += 1
+    return n
+
+
+def n_bucket(N: int) -> int:
+    """Power of two at or above N: the autotuner's key for kernel length N."""
+    b = 1
+    while b < N:
+        b *= 2
+    return b
+
+
+class Server:
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, streams: int = 4, tuner=None,
+                 max_batch: int = 64):
+        import torch
+        from . import apx
+        self.apx = apx
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.budget = budget_bytes
+        self.ctxs = [apx.Context(device) for _ in range(streams)]
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(streams)]
+        self.busy = [None] * streams   # (event, requests, bytes, device buffers, request table)
+        self.tuner = tuner
+        self.max_batch = max_batch
+        self.in_flight = 0
+        self.peak_in_flight = 0
+        self.batches = 0
+        self.max_overlap = 0           # most batches on the GPU at once
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+    def choice(self, N, op, target):
+        apx = self.apx
+        if self.tuner is None:
+            return 0, apx.CORE_AUTO
+        ch = self.tuner.choose(n_bucket(N), op, apx.PACK_AUTO, target)
+        return ch["W_block"], apx.CORE_FFT if ch["core"] == "fft" else apx.CORE_DIRECT
+
+    def _launch(self, si, batch, s_host, k_host):
+        torch, apx = self.torch, self.apx
+        st = self.streams[si]
+        bufs, items = [], []
+        with torch.cuda.stream(st):
+            for q in batch:
+                s = torch.empty(q.L, dtype=torch.float32, device=self.dev)
+                k = torch.empty(q.N, dtype=torch.float32, device=self.dev)
+                r = torch.empty(q.L + q.N - 1, dtype=torch.float32, device=self.dev)
+                s.copy_(s_host[q.s_off:q.s_off + q.L], non_blocking=True)
+                k.copy_(k_host[q.k_id, :q.N], non_blocking=True)
+                op = apx.OP_XCORR if q.xcorr else apx.OP_CONV
+                Wb, core = self.choice(q.N, op, q.target)
+                q.W_block, q.mode = Wb, op | core | apx.PACK_AUTO
+                items.append(dict(s=s, k=k, r=r, mode=q.mode, W_block=Wb, snr_db=q.target))
+                bufs.append((s, k, r))
+            reqs = self.ctxs[si].make_requests(items)
+            self.ctxs[si].apx_conv_batch(reqs, stream=st)
+            for q, (_, _, r) in zip(batch, bufs):
+                q.out = torch.empty(r.numel(), dtype=torch.float32, pin_memory=True)
+                q.out.copy_(r, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        nbytes = sum(device_bytes(q) for q in batch)
+        self.busy[si] = (ev, batch, nbytes, bufs, reqs)
+        self.in_flight += nbytes
+        self.peak_in_flight = max(self.peak_in_flight, self.in_flight)
+        self.batches += 1
+        self.max_overlap = max(self.max_overlap, sum(b is not None for b in self.busy))
+
+    def _poll(self):
+        done = []
+        for si, b in enumerate(self.busy):
+            if b is not None and b[0].query():
+                now = time.perf_counter()
+                for q in b[1]:
+                    q.done = now
+                self.in_flight -= b[2]
+                done.extend(b[1])
+                self.busy[si] = None
+        return done
+
+    def run(self, trace, s_host, k_host, realtime: bool = True):
+        """Serve `trace` (Requests sorted by arrival time t).  With realtime
+        False every request arrives at once.  Returns the completed requests."""
+        pending = collections.deque(trace)
+        waiting = collections.deque()
+        finished = []
+        t0 = time.perf_counter()
+        while pending or waiting or any(b is not None for b in self.busy):
+            now = time.perf_counter()
+            while pending and (not realtime or pending[0].t <= now - t0):
+                q = pending.popleft()
+                q.arrival = t0 + q.t if realtime else now
+                waiting.append(q)
+            finished.extend(self._poll())
+            free = [i for i, b in enumerate(self.busy) if b is None]
+            if waiting and free:
+                n = admit((device_bytes(q) for q in waiting), self.in_flight, self.budget, self.max_batch)
+                if n:
+                    batch = [waiting.popleft() for _ in range(n)]
+                    self._launch(free[0], batch, s_host, k_host)
+                    continue
+            if realtime and pending and not waiting:
+                time.sleep(max(0.0, min(1e-4, pending[0].t - (time.perf_counter() - t0))))
+        return finished
+
+
+def make_trace(seed, rate_hz=2000.0, duration_s=1.0, pool=1 << 23, ntemplates=32, lmax_log2=22.0, nmax=8192):
+    """Poisson trace of requests over a pinned signal pool and a set of
+    templates (matching/filtering requests reuse templates)."""
+    from . import workloads
+    reqs = []
+    for i, d in enumerate(workloads.serving_trace(seed, rate_hz, duration_s, lmax_log2=lmax_log2, nmax=nmax)):
+        g = np.random.default_rng(d["seed"])
+        L = min(d["L"], pool)
+        reqs.append(Request(rid=i, t=d["t"], L=L, N=min(d["N"], nmax, L), xcorr=d["xcorr"], target=d["target"],
+                            s_off=int(g.integers(0, pool - L + 1)), k_id=int(g.integers(0, ntemplates))))
+    return reqs
+
+
+def host_pools(seed, pool=1 << 23, ntemplates=32, nmax=8192):
+    """Pinned host signal pool (Laplacian(0, 0.1)) and templates (U[-1, 1])."""
+    import torch
+    from . import workloads
+    s = torch.from_numpy(workloads.random_signal(seed, pool, "laplace", 0.1)).pin_memory()
+    k = torch.from_numpy(np.stack([workloads.random_signal(seed + 1 + j, nmax, "uniform")
+                                   for j in range(ntemplates)])).pin_memory()
+    return s, k
+
+
+def latency_ms(done):
+    lat = np.array([(q.done - q.arrival) * 1e3 for q in done])
+    return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))

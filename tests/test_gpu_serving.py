@@ -1,0 +1,49 @@
+"""Serving loop on the GPU: every request of a Poisson trace completes, the
+admission budget holds, batches overlap on the device, and each result is the
+same bit for bit as the same request run alone (a batch of one on a fresh
+context), whatever shared its batch and whatever ran beside it."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1201_3018_gb300 import apx, serve
+from paper_1201_3018_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(ctx, q, s_host, k_host):
+    s = s_host[q.s_off:q.s_off + q.L].cuda()
+    k = k_host[q.k_id, :q.N].cuda()
+    r = torch.full((q.L + q.N - 1,), float("nan"), device="cuda")
+    ctx.apx_conv_batch(ctx.make_requests([dict(s=s, k=k, r=r, mode=q.mode, W_block=q.W_block, snr_db=q.target)]))
+    torch.cuda.synchronize()
+    return r.cpu()
+
+
+@pytest.mark.parametrize("budget_mb,streams", [(48, 4), (40 << 10, 3)])
+def test_serving_same_alone_and_in_mix(budget_mb, streams):
+    seed = wl.SEED_BASE + 41
+    pool = 1 << 20
+    s_host, k_host = serve.host_pools(seed, pool=pool, ntemplates=8)
+    trace = serve.make_trace(seed, rate_hz=2000.0, duration_s=0.12, pool=pool, ntemplates=8, lmax_log2=20.0)
+    budget = budget_mb << 20
+    srv = serve.Server(0, budget_bytes=budget, streams=streams, max_batch=16)
+    try:
+        done = srv.run(trace, s_host, k_host, realtime=True)
+    finally:
+        srv.close()
+    assert sorted(q.rid for q in done) == list(range(len(trace)))
+    biggest = max(serve.device_bytes(q) for q in trace)
+    assert srv.peak_in_flight <= max(budget, biggest)
+    assert srv.batches >= 2
+    p50, p99 = serve.latency_ms(done)
+    assert 0 < p50 <= p99
+    ctx = apx.Context(0)
+    try:
+        for q in done:
+            ref = _alone(ctx, q, s_host, k_host)
+            assert torch.isfinite(q.out).all()
+            assert torch.equal(q.out, ref), "request %d differs from its run alone" % q.rid
+    finally:
+        ctx.close()
