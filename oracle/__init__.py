@@ -101,6 +101,7 @@ def _declare(L):
         "or_unpack_sym_fp64": (None, [vp, i32, i32, d, d, d, vp]),
         "or_unpack_asym": (C.c_int, [vp, i32, i32, i32, i64, i32, i32, vp]),
         "or_apx_conv": (C.c_int, [vp, i64, vp, i32, i32, u32, d, i32, i32, vp, vp, vp, C.c_int, vp]),
+        "or_filterbank": (C.c_int, [vp, i64, vp, i32, i32, i32, i32, i32, i64, i64, vp, i64, vp, vp, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -331,6 +332,27 @@ def apx_conv(s, k, Wblock, mode, snr_db=0.0, Sq=0, Kq=0, nthreads=1, want_int=Tr
     rc = lib().or_apx_conv(_p(s), L, _p(k), N, Wblock, mode, float(snr_db), Sq, Kq, _p(r),
                            _p(rq) if want_int else None, st, nthreads, None if wm is None else _p(wm))
     return r, rq, list(st), rc
+
+
+def filterbank(s, kbank, T, Sq, Kq, blocks=None, nthreads=0):
+    """Exact-integer filterbank (Eqs. (1), (2), (16) per block of T outputs).
+    kbank: (F, N).  Returns (y float32 (F, L+N-1), yq int64 (F, L+N-1),
+    block_cs float32 (nb,)); only `blocks` = (b0, b1) are computed when given
+    (the other entries stay zero)."""
+    s, kb = _f32(s), _f32(np.atleast_2d(kbank))
+    L = len(s)
+    F, N = kb.shape
+    out_len = L + N - 1
+    nb = (out_len + T - 1) // T
+    b0, b1 = (0, nb) if blocks is None else blocks
+    y = np.zeros((F, out_len), np.float32)
+    yq = np.zeros((F, out_len), np.int64)
+    cs = np.zeros(nb, np.float32)
+    rc = lib().or_filterbank(_p(s), L, _p(kb), F, N, T, Sq, Kq, b0, b1, _p(y), out_len, _p(yq), _p(cs),
+                             nthreads)
+    if rc:
+        raise ArithmeticError("or_filterbank rc=%d" % rc)
+    return y, yq, cs
 
 
 def stats_arrays(stats):

@@ -764,3 +764,79 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     free(kr);
     return err;
 }
+
+/* ---- filterbank on exact small integers ------------------------------------
+ * The same three steps as the packed path, Eq. (2) companding per block,
+ * an exact integer convolution (here plain int64 sums, Eq. (1) on the
+ * quantized values), Eq. (16) inverse companding, for F kernels sharing one
+ * input.  The block is the set of T consecutive outputs, and its window is
+ * every input sample those outputs touch. */
+int or_filterbank(const float* s, int64_t L, const float* kbank, int32_t F, int32_t N, int32_t T,
+                  int32_t Sq, int32_t Kq, int64_t b0, int64_t b1, float* y, int64_t ldy, int64_t* yq,
+                  float* block_cs, int nthreads) {
+    if (!s || !kbank || !y || L < 1 || F < 1 || N < 1 || T < 1 || Sq < 1 || Kq < 1) return OR_ERR_ARG;
+    const int64_t out_len = L + N - 1;
+    const int64_t nb = (out_len + T - 1) / T;
+    if (ldy < out_len || b0 < 0 || b1 > nb || b0 > b1) return OR_ERR_ARG;
+    for (int64_t i = 0; i < L; ++i) if (!isfinite(s[i])) return OR_ERR_RANGE;
+    for (int64_t i = 0; i < (int64_t)F * N; ++i) if (!isfinite(kbank[i])) return OR_ERR_RANGE;
+
+    /* Eq. (2) on each filter, once */
+    int32_t* kq = malloc(sizeof(int32_t) * (size_t)F * (size_t)N);
+    float* ck = malloc(sizeof(float) * (size_t)F);
+    if (!kq || !ck) { free(kq); free(ck); return OR_ERR_ARG; }
+    for (int32_t f = 0; f < F; ++f) {
+        const float* kf = kbank + (int64_t)f * N;
+        float Mk = or_maxabs(kf, N);
+        ck[f] = Mk > 0.0f ? or_compand_factor(Kq, Mk) : 0.0f;
+        if (Mk > 0.0f) or_compand(kf, N, ck[f], kq + (int64_t)f * N);
+        else for (int32_t n = 0; n < N; ++n) kq[(int64_t)f * N + n] = 0;
+    }
+    const int64_t nw = (int64_t)T + N - 1;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    (void)nthreads;
+    int err = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        float* w = malloc(sizeof(float) * (size_t)nw);
+        int32_t* q = malloc(sizeof(int32_t) * (size_t)nw);
+        if (!w || !q) {
+#pragma omp atomic write
+            err = OR_ERR_ARG;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = b0; i < b1; ++i) {
+            if (err) continue;
+            const int64_t t0 = i * T;
+            for (int64_t u = 0; u < nw; ++u) {
+                int64_t g = t0 - N + 1 + u;
+                w[u] = (g >= 0 && g < L) ? s[g] : 0.0f;
+            }
+            const float Ms = or_maxabs(w, nw);
+            const float cs = Ms > 0.0f ? or_compand_factor(Sq, Ms) : 0.0f;   /* Eq. (2) */
+            if (block_cs) block_cs[i] = cs;
+            if (Ms > 0.0f) or_compand(w, nw, cs, q);
+            const int64_t t1 = t0 + T < out_len ? t0 + T : out_len;
+            for (int32_t f = 0; f < F; ++f) {
+                const int32_t* kf = kq + (int64_t)f * N;
+                for (int64_t t = t0; t < t1; ++t) {
+                    int64_t acc = 0;
+                    if (Ms > 0.0f && ck[f] > 0.0f)
+                        for (int32_t n = 0; n < N; ++n)                          /* Eq. (1) */
+                            acc += (int64_t)q[t - t0 + N - 1 - n] * (int64_t)kf[n];
+                    double sc = (double)cs * (double)ck[f];
+                    y[(int64_t)f * ldy + t] = acc == 0 ? 0.0f : (float)((double)acc / sc);  /* Eq. (16) */
+                    if (yq) yq[(int64_t)f * ldy + t] = acc;
+                }
+            }
+        }
+        free(w);
+        free(q);
+    }
+    free(kq);
+    free(ck);
+    return err;
+}

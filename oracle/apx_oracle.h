@@ -126,6 +126,20 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
                 float* r_out, int64_t* rq_out, or_block_stats_t* stats, int nthreads,
                 const uint8_t* want);
 
+/* ---- filterbank on exact small integers (time-domain Toeplitz reading) ---
+ * Eq. (1) for F kernels at once with the companding of Eq. (2) applied per
+ * block of T consecutive outputs and the inverse companding of Eq. (16).
+ * Block i quantizes the input window its outputs depend on,
+ * s[iT-N+1 .. iT+T-1] (zero outside [0, L)), with c_s = S_q / ||window||_inf;
+ * filter f is quantized once with c_k = K_q / ||k_f||_inf.  The integer
+ * convolution is exact (int64) and y = r~ / (c_s c_k) (Eq. 16) rounded once
+ * to FP32.  An all-zero window or an all-zero filter gives exact zeros.
+ * Only blocks [b0, b1) are written (y, yq: F rows of ldy entries; yq and
+ * block_cs may be NULL).  Returns OR_ERR_RANGE for a non-finite sample. */
+int or_filterbank(const float* s, int64_t L, const float* kbank, int32_t F, int32_t N, int32_t T,
+                  int32_t Sq, int32_t Kq, int64_t b0, int64_t b1, float* y, int64_t ldy, int64_t* yq,
+                  float* block_cs, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
