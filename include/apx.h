@@ -197,6 +197,35 @@ int apx_graph_launch(apx_graph* graph, void* stream);
 int64_t apx_graph_launch_count(const apx_graph* graph);  /* kernel launches per replay */
 void apx_graph_destroy(apx_graph* graph);
 
+/* ---- filterbank on the tensor cores ---------------------------------------
+ * F kernels applied to one input, y_f = s * k_f (Eq. 1), through the paper's
+ * companding layer: every block of T consecutive outputs quantizes the input
+ * window those outputs depend on, s[bT-N+1 .. bT+T-1], with its own factor
+ * c_s = S_q / ||window||_inf; kernel f is quantized once with
+ * c_k = K_q / ||k_f||_inf (Eq. 2, round half to even on the FP32 product); the
+ * integer convolution is exact; y = r~ / (c_s c_k) (Eq. 16).  The exact
+ * integer arithmetic runs on the tensor cores (FP16 integers, FP32
+ * accumulation), which is exact because N * S_q * K_q <= 2^24; it replaces the
+ * FP64 packing of Section III, whose gain does not carry over to a GPU whose
+ * FP64 rate is a small fraction of its FP32 and tensor rates.
+ *   s_in     : device, L samples (FP32)
+ *   k_bank   : device, F x N taps, row-major (FP32)
+ *   S_q, K_q : 1 .. 2048 with N * S_q * K_q <= 2^24, else APX_ERR_RANGE
+ *   y_out    : device, F rows of ldy floats, y_f[t] at y_out[f * ldy + t] for
+ *              t < L+N-1; ldy >= L+N-1, a multiple of 4, y_out 16-byte aligned
+ *   yq_out   : NULL or device int32 like y_out: the integer outputs r~
+ *   block_cs : NULL or device, one float per block: c_s (0 for an all-zero window)
+ * T = 128 * P outputs per block with P = 256 (F = 1), 128 (F = 2) or 64 (F >= 3);
+ * the number of blocks is ceil((L+N-1) / T).  Limits: F <= 1024, N <= 16384
+ * (APX_ERR_ARG beyond).  A window holding a non-finite sample gives zero
+ * outputs for its block and APX_ERR_NONFINITE from the next apx_sync.  The
+ * context's filterbank workspace (about 2.3 bytes per output of one kernel
+ * plus the FP16 Toeplitz columns) is reused by the next call on any stream.
+ * Errors: APX_ERR_ARG, APX_ERR_RANGE, APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA. */
+int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_bank, int32_t F, int32_t N,
+                   int32_t S_q, int32_t K_q, float* y_out, int64_t ldy, int32_t* yq_out, float* block_cs,
+                   void* stream);
+
 /* ---- allocation-free FFT core ---------------------------------------------
  * The paper has no counterpart: this is a deployment variant of apx_conv with
  * the FFT core for callers that may not allocate device memory once they are

@@ -60,8 +60,16 @@ SIGNATURES = {
     "apx_graph_launch_count": (_i64, [_vp]),
     "apx_graph_destroy": (None, [_vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
+    "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft")
+
+
+def filterbank_blocks(L, F, N):
+    """(outputs per block T, number of blocks) of apx_filterbank."""
+    P = 256 if F == 1 else (128 if F == 2 else 64)
+    T = 128 * P
+    return T, (L + N - 1 + T - 1) // T
 
 
 class ApxError(RuntimeError):
@@ -205,6 +213,24 @@ class Context:
         _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
         return _check("apx_conv_full", lib().apx_conv_full(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(),
                                                            W_block, mode, _ptr(r), _stream(stream)))
+
+    def apx_filterbank(self, s, k_bank, Sq, Kq, y, yq=None, block_cs=None, stream=None):
+        """s: (L,) float32; k_bank: (F, N) float32; y: (F, ldy) float32 with
+        ldy >= L+N-1 (rows may be padded); yq: None or int32 like y; block_cs:
+        None or float32 (blocks,).  All CUDA tensors."""
+        import torch
+        _dev_f32(s, "s_in"); _dev_f32(k_bank, "k_bank")
+        F, N = k_bank.shape
+        if not (y.is_cuda and y.dtype == torch.float32 and y.dim() == 2 and y.shape[0] == F and y.stride(1) == 1):
+            raise TypeError("y must be a (F, ldy) float32 CUDA tensor with unit inner stride")
+        if yq is not None and not (yq.is_cuda and yq.dtype == torch.int32 and yq.shape == y.shape
+                                   and yq.stride() == y.stride()):
+            raise TypeError("yq must be an int32 CUDA tensor shaped and strided like y")
+        if block_cs is not None:
+            _dev_f32(block_cs, "block_cs")
+        return _check("apx_filterbank", lib().apx_filterbank(self._h, _ptr(s), s.numel(), _ptr(k_bank), F, N, Sq, Kq,
+                                                             _ptr(y), y.stride(0), _ptr(yq), _ptr(block_cs),
+                                                             _stream(stream)))
 
     def apx_conv_host(self, s_host, k_host, W_block, mode, snr_db=0.0, Sq=0, Kq=0, r_host=None, stream=None):
         """s_host, k_host, r_host: contiguous float32 CPU tensors (pinned for speed)."""

@@ -33,6 +33,7 @@ struct apx_ctx {
     int64_t launches = 0;
     DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
+    DevBuf tc_seg, tc_b, tc_cs, tc_ck;  // filterbank: FP16 block segments, Toeplitz B, c_s per block, c_k per kernel
     void* hstage = nullptr;             // pinned staging for batch parameters
     size_t hstage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
@@ -657,7 +658,8 @@ void apx_destroy(apx_ctx* c) {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
         DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
-                         &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab};
+                         &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab,
+                         &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_ck};
         for (DevBuf* b : all) release(c, *b);
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -812,6 +814,33 @@ extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, 
     cudaError_t e = cudaMemsetAsync(ctx->barena.p, 0, bp.flags_bytes, st);  // claim/ready words
     if (e == cudaSuccess) e = launch_batch(bp, (const Params*)ctx->bparams.p, (const int*)ctx->btab.p, st);
     for (const auto& G : bp.groups) ctx->launches += G.fft ? 3 : 1;
+    return cuda_status(e);
+}
+
+extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_bank, int32_t F,
+                              int32_t N, int32_t S_q, int32_t K_q, float* y_out, int64_t ldy, int32_t* yq_out,
+                              float* block_cs, void* stream) {
+    if (!ctx || !s_in || !k_bank || !y_out) return APX_ERR_ARG;
+    if (L < 1 || F < 1 || N < 1 || F > kTcMaxF || N > kTcMaxN) return APX_ERR_ARG;
+    if (S_q < 1 || K_q < 1 || S_q > kTcMaxQ || K_q > kTcMaxQ) return APX_ERR_RANGE;
+    if ((long long)N * S_q * K_q > kTcExactSum) return APX_ERR_RANGE;
+    TcGeom g;
+    if (!tc_geometry(L, F, N, &g)) return APX_ERR_ARG;
+    if (ldy < g.out_len || (ldy & 3) || ((uintptr_t)y_out & 15) || ((uintptr_t)yq_out & 15)) return APX_ERR_ARG;
+    g.ldy = ldy;
+    DeviceGuard dg(ctx->device);
+    int rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+    if (!rc) rc = ensure(ctx, ctx->tc_seg, tc_seg_bytes(g));
+    if (!rc) rc = ensure(ctx, ctx->tc_b, tc_b_bytes(g));
+    if (!rc) rc = ensure(ctx, ctx->tc_cs, sizeof(float) * (size_t)g.nb);
+    if (!rc) rc = ensure(ctx, ctx->tc_ck, sizeof(float) * (size_t)g.ngroups * g.G);
+    if (rc) return rc;
+    bool enc_failed = false;
+    cudaError_t e = launch_tc(g, s_in, L, k_bank, S_q, K_q, ctx->tc_seg.p, ctx->tc_b.p, (float*)ctx->tc_cs.p,
+                              (float*)ctx->tc_ck.p, y_out, yq_out, block_cs, (unsigned*)ctx->flags.p,
+                              (cudaStream_t)stream, &enc_failed);
+    if (enc_failed) return APX_ERR_CUDA;
+    if (e == cudaSuccess) ctx->launches += 3;
     return cuda_status(e);
 }
 

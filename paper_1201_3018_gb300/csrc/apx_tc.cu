@@ -1,0 +1,473 @@
+// apx_tc.cu -- time-domain convolution core on the tensor cores, for a bank of
+// kernels sharing one input (the filterbank).
+//
+// The paper's layer around the core is kept: each block of outputs quantizes
+// the input window it depends on with its own companding factor (Eq. 2), the
+// kernels are companded once, the convolution of the small integers is exact,
+// and the result is scaled back (Eq. 16).  What replaces the FP64 packing is
+// the arithmetic: the integers (|q| <= 2048) are exact in FP16, their products
+// exact in FP32, and FP32 accumulation stays exact while every partial sum is
+// at most 2^24 in magnitude, which N * S_q * K_q <= 2^24 guarantees.
+//
+// Eq. (1) as a matrix product.  With P output phases per row,
+//   y_f[t0 + q P + p] = sum_j A[q][j] B[j][(f, p)],
+//   A[q][j]      = s~[t0 - N + 1 + q P + j]          (Toeplitz in q, j)
+//   B[j][(f, p)] = k~_f[p + N - 1 - j]  (zero outside [0, N)),
+// j in [0, K), K = N + P - 1.  Rows q are time (M = 128 per tile), columns are
+// G = 256 / P kernels times P phases (N_gemm = 256).
+//
+// The Toeplitz operand without expansion: the quantized window of each block
+// is stored as a matrix with rows of P samples, S[r][c] = seg[r P + c]; then
+// A[q][j] = S[q + j / P][j % P], so the 64-wide K slice j0..j0+63 (P a
+// multiple of 64) is the plain 128 x 64 box of S at (row j0 / P, column j0 % P),
+// one TMA load.
+//
+// Kernels:
+//   k_tc_quant  one CTA per block: ||window||_inf, c_s, companding into the
+//               block's FP16 segment (Eq. 2), c_s to the block table.
+//   k_tc_kern   one CTA per kernel: c_k, companding, the Toeplitz columns of B
+//               (K-major, FP16).
+//   k_tc_mma    one CTA per (block, kernel group): warp 0 streams A and B
+//               slices with TMA into a 4-stage shared-memory ring, warp 1
+//               issues tcgen05.mma (M 128, N 256, K 16, FP32 accumulators in
+//               tensor memory), warps 2-5 read the accumulators back with
+//               tcgen05.ld, scale by (c_s c_k)^-1 (Eq. 16) and store.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "apx_launch.h"
+
+namespace apx {
+
+namespace {
+
+constexpr int kTcThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
+constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
+constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr uint32_t kTcTmemCols = kTcN;
+constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+// kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B FP16
+// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after about two
+// seconds (the caller records the timeout and winds down).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, bool sleep) {
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (clock64() - t0 > kTcWaitCycles) return false;
+        if (sleep) __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major with the 128-byte swizzle that the
+// TMA loads write: start address >> 4 (bits 0-13), leading byte offset 16
+// (unused for this layout), stride byte offset 1024 between 8-row groups
+// (bits 32-45), descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits
+// 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64_t hi, int64_t L, bool* bad,
+                                               float* red) {
+    float m = 0.f;
+    bool nf = false;
+    for (int64_t g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+        if (g < 0 || g >= L) continue;
+        const float v = fabsf(x[g]);
+        if (!(v <= 3.402823466e38f)) nf = true;  // NaN or Inf
+        else m = fmaxf(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        nf |= __shfl_xor_sync(0xffffffffu, (int)nf, o) != 0;
+    }
+    __shared__ int nfs;
+    if (threadIdx.x == 0) nfs = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = m;
+        if (nf) nfs = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        red[0] = t;
+    }
+    __syncthreads();
+    const float r = red[0];
+    *bad = nfs != 0;
+    __syncthreads();
+    return r;
+}
+
+// Eq. (2) on the block's window, written as the block's FP16 segment
+// seg[u] = s~[t0 - N + 1 + u]; entries past the window (u >= T + N - 1) are 0.
+__global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, int64_t L, TcGeom g, int Sq,
+                                                  __half* __restrict__ seg, float* __restrict__ cs_tab,
+                                                  float* __restrict__ cs_out, unsigned* __restrict__ status) {
+    __shared__ float red[8];
+    const int64_t b = blockIdx.x;
+    const int64_t t0 = b * g.T;
+    const int64_t lo = t0 - g.N + 1, nwin = (int64_t)g.T + g.N - 1;
+    bool bad = false;
+    const float M = block_max_abs(s, lo, lo + nwin, L, &bad, red);
+    float c = 0.f;
+    if (bad) {
+        c = __int_as_float(0x7fc00000);
+        if (threadIdx.x == 0) atomicOr(status, 1u);
+    } else if (M > 0.f) {
+        c = __fdiv_rn((float)Sq, M);
+    }
+    __half* out = seg + b * g.seg_rows * g.P;
+    const int64_t nseg = g.seg_rows * g.P;
+    const bool live = !bad && M > 0.f;
+    for (int64_t u = 2 * (int64_t)threadIdx.x; u < nseg; u += 2 * blockDim.x) {
+        float q0 = 0.f, q1 = 0.f;
+        const int64_t g0 = lo + u;
+        if (live && u < nwin && g0 >= 0 && g0 < L) q0 = rintf(__fmul_rn(c, s[g0]));
+        if (live && u + 1 < nwin && g0 + 1 >= 0 && g0 + 1 < L) q1 = rintf(__fmul_rn(c, s[g0 + 1]));
+        *reinterpret_cast<__half2*>(out + u) = __halves2half2(__float2half_rn(q0), __float2half_rn(q1));
+    }
+    if (threadIdx.x == 0) {
+        cs_tab[b] = c;
+        if (cs_out) cs_out[b] = c;
+    }
+}
+
+// Eq. (2) on kernel f and its Toeplitz columns: row n = group * 256 + fl * P + p
+// of the K-major B operand holds k~_f[p + N - 1 - j] at column j.
+__global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, TcGeom g, int Kq,
+                                                 __half* __restrict__ bt, float* __restrict__ ck_tab,
+                                                 unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char tc_kern_smem[];
+    __half* kq = reinterpret_cast<__half*>(tc_kern_smem);
+    __shared__ float red[8];
+    const int f = blockIdx.x;  // 0 .. ngroups * G - 1 (past F: zero columns)
+    float c = 0.f;
+    bool bad = false;
+    if (f < g.F) {
+        const float* k = kb + (int64_t)f * g.N;
+        const float M = block_max_abs(k, 0, g.N, g.N, &bad, red);
+        if (bad) {
+            if (threadIdx.x == 0) atomicOr(status, 1u);
+        } else if (M > 0.f) {
+            c = __fdiv_rn((float)Kq, M);
+        }
+        for (int n = threadIdx.x; n < g.N; n += blockDim.x)
+            kq[n] = __float2half_rn(c > 0.f ? rintf(__fmul_rn(c, k[n])) : 0.f);
+        if (threadIdx.x == 0) ck_tab[f] = bad ? __int_as_float(0x7fc00000) : c;
+    } else {
+        for (int n = threadIdx.x; n < g.N; n += blockDim.x) kq[n] = __float2half_rn(0.f);
+    }
+    __syncthreads();
+    const int grp = f / g.G, fl = f % g.G;
+    __half* rows = bt + ((int64_t)grp * kTcN + (int64_t)fl * g.P) * g.Kpad;
+    for (int p = 0; p < g.P; ++p) {
+        __half* row = rows + (int64_t)p * g.Kpad;
+        for (int j = threadIdx.x; j < g.Kpad; j += blockDim.x) {
+            const int n = p + g.N - 1 - j;
+            row[j] = (n >= 0 && n < g.N) ? kq[n] : __float2half_rn(0.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGeom g,
+             const float* __restrict__ cs_tab, const float* __restrict__ ck_tab, float* __restrict__ y,
+             int32_t* __restrict__ yq, unsigned* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], acc_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh, issued_sh;
+    const uint32_t base = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t blk = blockIdx.x;
+    const int grp = blockIdx.y;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_bar), 1);
+        abort_sh = 0;
+        issued_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            const int arow0 = (int)(blk * g.seg_rows);
+            int kt = 0;
+            for (; kt < g.ktiles; ++kt) {
+                const int s = kt % kTcStages;
+                const uint32_t ph = (uint32_t)(kt / kTcStages) & 1u;
+                if (kt >= kTcStages && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, false)) {
+                    atomicOr(status, 2u);
+                    abort_sh = 1;
+                    break;
+                }
+                if (*(volatile int*)&abort_sh) break;
+                const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                const int j0 = kt * kTcK;
+                mbar_expect_tx(fb, kTcStageBytes);
+                tma_load_2d(sa, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
+                tma_load_2d(sb, &tmB, j0, grp * kTcN, fb);
+            }
+            issued_sh = kt;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            for (int kt = 0; kt < g.ktiles; ++kt) {
+                const int s = kt % kTcStages;
+                const uint32_t ph = (uint32_t)(kt / kTcStages) & 1u;
+                if (!mbar_wait(smem_u32(&full_bar[s]), ph, false) || *(volatile int*)&abort_sh) {
+                    atomicOr(status, 2u);
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+#pragma unroll
+                for (int k = 0; k < kTcK / 16; ++k)
+                    umma_f16(tmem, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
+                umma_commit(smem_u32(&empty_bar[s]));
+            }
+            umma_commit(smem_u32(&acc_bar));  // all issued MMAs done
+        }
+    } else {  // epilogue: warps 2..5, TMEM lane quarter warp % 4
+        const bool ok = mbar_wait(smem_u32(&acc_bar), 0u, true);
+        tc_fence_after();
+        __syncwarp();
+        if (!ok) {
+            if (lane == 0) atomicOr(status, 2u);
+        } else if (!*(volatile int*)&abort_sh) {
+            const int lq = warp & 3;
+            const int row = lq * 32 + lane;
+            const int64_t trow = blk * (int64_t)g.T + (int64_t)row * g.P;
+            const float cs = cs_tab[blk];
+            for (int fl = 0; fl < g.G; ++fl) {
+                const int f = grp * g.G + fl;
+                if (f >= g.F) break;
+                const float ck = ck_tab[f];
+                float inv = 0.f;
+                if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
+                else if (!(cs >= 0.f) || !(ck >= 0.f)) inv = __int_as_float(0x7fc00000);
+                float* yf = y + (int64_t)f * g.ldy;
+                int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
+                for (int c = 0; c < g.P; c += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(fl * g.P + c), r);
+                    const int64_t t = trow + c;
+                    if (t >= g.out_len) continue;
+                    float v[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float a = __uint_as_float(r[i]);
+                        v[i] = a == 0.f ? 0.f : __fmul_rn(a, inv);
+                    }
+                    if (t + 32 <= g.out_len) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4*>(yf + t + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        if (qf) {
+#pragma unroll
+                            for (int i = 0; i < 32; i += 4)
+                                *reinterpret_cast<int4*>(qf + t + i) = make_int4(
+                                    __float2int_rn(__uint_as_float(r[i])), __float2int_rn(__uint_as_float(r[i + 1])),
+                                    __float2int_rn(__uint_as_float(r[i + 2])),
+                                    __float2int_rn(__uint_as_float(r[i + 3])));
+                        }
+                    } else {
+                        for (int i = 0; i < 32 && t + i < g.out_len; ++i) {
+                            yf[t + i] = v[i];
+                            if (qf) qf[t + i] = __float2int_rn(__uint_as_float(r[i]));
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && lane == 0 && abort_sh) {
+        // TMA loads issued but never consumed: let them land before the CTA exits
+        for (int kt = issued_sh - kTcStages; kt < issued_sh; ++kt)
+            if (kt >= 0) (void)mbar_wait(smem_u32(&full_bar[kt % kTcStages]), (uint32_t)(kt / kTcStages) & 1u, true);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols)
+                     : "memory");
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D FP16 map: inner extent `inner` (contiguous), `rows` rows `pitch` bytes
+// apart, box 64 x box_rows, 128-byte swizzle.
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch, uint32_t box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_geometry(int64_t L, int F, int N, TcGeom* g) {
+    if (L < 1 || F < 1 || N < 1 || N > kTcMaxN || F > kTcMaxF) return false;
+    g->P = F == 1 ? 256 : (F == 2 ? 128 : 64);
+    g->G = kTcN / g->P;
+    g->F = F;
+    g->N = N;
+    g->ngroups = (F + g->G - 1) / g->G;
+    g->Kpad = ((N + g->P - 1) + kTcK - 1) / kTcK * kTcK;
+    g->ktiles = g->Kpad / kTcK;
+    g->T = kTcM * g->P;
+    g->out_len = L + N - 1;
+    g->nb = (g->out_len + g->T - 1) / g->T;
+    g->seg_rows = ((int64_t)g->T + g->Kpad + g->P - 1) / g->P;
+    g->ldy = g->out_len;
+    return true;
+}
+
+size_t tc_seg_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)(g.nb * g.seg_rows * g.P); }
+size_t tc_b_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)g.ngroups * kTcN * (size_t)g.Kpad; }
+size_t tc_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + 1024; }
+
+cudaError_t launch_tc(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
+                      void* bt, float* cs_tab, float* ck_tab, float* y, int32_t* yq, float* cs_out, unsigned* status,
+                      cudaStream_t st, bool* encode_failed) {
+    *encode_failed = false;
+    CUtensorMap ma, mb;
+    if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * 2, kTcM) ||
+        !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * 2, kTcN)) {
+        *encode_failed = true;
+        return cudaErrorInvalidValue;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_tc_quant<<<(unsigned)g.nb, 256, 0, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
+    k_tc_kern<<<(unsigned)(g.ngroups * g.G), 256, sizeof(__half) * (size_t)g.N, st>>>(kb, g, Kq, (__half*)bt,
+                                                                                    ck_tab, status);
+    k_tc_mma<<<dim3((unsigned)g.nb, (unsigned)g.ngroups), kTcThreads, tc_smem_bytes(), st>>>(ma, mb, g, cs_tab,
+                                                                                         ck_tab, y, yq, status);
+    return cudaGetLastError();
+}
+
+}  // namespace apx
