@@ -173,94 +173,147 @@ __device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64
 
 // Eq. (2) on the block's window, written as the block's FP16 segment
 // seg[u] = s~[t0 - N + 1 + u]; entries past the window (u >= T + N - 1) are 0.
+// Each thread handles runs of kRun consecutive samples with independent loads.
+constexpr int kRun = 8;
 __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, int64_t L, TcGeom g, int Sq,
                                                   __half* __restrict__ seg, float* __restrict__ cs_tab,
                                                   float* __restrict__ cs_out, unsigned* __restrict__ status) {
     __shared__ float red[8];
+    __shared__ int nfs;
     const int64_t b = blockIdx.x;
-    const int64_t t0 = b * g.T;
-    const int64_t lo = t0 - g.N + 1, nwin = (int64_t)g.T + g.N - 1;
-    bool bad = false;
-    const float M = block_max_abs(s, lo, lo + nwin, L, &bad, red);
-    float c = 0.f;
-    if (bad) {
-        c = __int_as_float(0x7fc00000);
-        if (threadIdx.x == 0) atomicOr(status, 1u);
-    } else if (M > 0.f) {
-        c = __fdiv_rn((float)Sq, M);
-    }
-    __half* out = seg + b * g.seg_rows * g.P;
+    const int64_t lo = b * g.T - g.N + 1, nwin = (int64_t)g.T + g.N - 1;
     const int64_t nseg = g.seg_rows * g.P;
+    if (threadIdx.x == 0) nfs = 0;
+    float m = 0.f;
+    bool nf = false;
+    for (int64_t u0 = (int64_t)threadIdx.x * kRun; u0 < nwin; u0 += (int64_t)blockDim.x * kRun) {
+        float v[kRun];
+#pragma unroll
+        for (int i = 0; i < kRun; ++i) {
+            const int64_t gi = lo + u0 + i;
+            v[i] = (u0 + i < nwin && gi >= 0 && gi < L) ? __ldg(s + gi) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < kRun; ++i) {
+            const float a = fabsf(v[i]);
+            if (!(a <= 3.402823466e38f)) nf = true;
+            else m = fmaxf(m, a);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        nf |= __shfl_xor_sync(0xffffffffu, (int)nf, o) != 0;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = m;
+        if (nf) nfs = 1;
+    }
+    __syncthreads();
+    float M = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, red[w]);
+    const bool bad = nfs != 0;
+    float c = 0.f;
+    if (bad) c = __int_as_float(0x7fc00000);
+    else if (M > 0.f) c = __fdiv_rn((float)Sq, M);
     const bool live = !bad && M > 0.f;
-    for (int64_t u = 2 * (int64_t)threadIdx.x; u < nseg; u += 2 * blockDim.x) {
-        float q0 = 0.f, q1 = 0.f;
-        const int64_t g0 = lo + u;
-        if (live && u < nwin && g0 >= 0 && g0 < L) q0 = rintf(__fmul_rn(c, s[g0]));
-        if (live && u + 1 < nwin && g0 + 1 >= 0 && g0 + 1 < L) q1 = rintf(__fmul_rn(c, s[g0 + 1]));
-        *reinterpret_cast<__half2*>(out + u) = __halves2half2(__float2half_rn(q0), __float2half_rn(q1));
+    __half* out = seg + b * nseg;
+    for (int64_t u0 = (int64_t)threadIdx.x * kRun; u0 < nseg; u0 += (int64_t)blockDim.x * kRun) {
+        float v[kRun];
+#pragma unroll
+        for (int i = 0; i < kRun; ++i) {
+            const int64_t gi = lo + u0 + i;
+            v[i] = (live && u0 + i < nwin && gi >= 0 && gi < L) ? __ldg(s + gi) : 0.f;
+        }
+        __align__(16) __half2 h[kRun / 2];
+#pragma unroll
+        for (int i = 0; i < kRun; i += 2)
+            h[i / 2] = __halves2half2(__float2half_rn(rintf(__fmul_rn(c, v[i]))),
+                                      __float2half_rn(rintf(__fmul_rn(c, v[i + 1]))));
+        if (!live) {
+#pragma unroll
+            for (int i = 0; i < kRun / 2; ++i) h[i] = __float2half2_rn(0.f);
+        }
+        *reinterpret_cast<uint4*>(out + u0) = *reinterpret_cast<const uint4*>(h);  // nseg % 8 == 0
     }
     if (threadIdx.x == 0) {
+        if (bad) atomicOr(status, 1u);
         cs_tab[b] = c;
         if (cs_out) cs_out[b] = c;
     }
 }
 
 // Eq. (2) on kernel f and its Toeplitz columns: row n = group * 256 + fl * P + p
-// of the K-major B operand holds k~_f[p + N - 1 - j] at column j.
+// of the K-major B operand holds k~_f[p + N - 1 - j] at column j.  CTA
+// (f, y) writes the rows of phases p = y, y + gridDim.y, ...
 __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, TcGeom g, int Kq,
                                                  __half* __restrict__ bt, float* __restrict__ ck_tab,
                                                  unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char tc_kern_smem[];
-    __half* kq = reinterpret_cast<__half*>(tc_kern_smem);
+    __half* kq = reinterpret_cast<__half*>(tc_kern_smem);  // kq[n + 64] = k~[n], zero outside [0, N)
     __shared__ float red[8];
     const int f = blockIdx.x;  // 0 .. ngroups * G - 1 (past F: zero columns)
+    const int kpadded = g.N + 128;
     float c = 0.f;
     bool bad = false;
     if (f < g.F) {
         const float* k = kb + (int64_t)f * g.N;
         const float M = block_max_abs(k, 0, g.N, g.N, &bad, red);
-        if (bad) {
-            if (threadIdx.x == 0) atomicOr(status, 1u);
-        } else if (M > 0.f) {
-            c = __fdiv_rn((float)Kq, M);
+        if (!bad && M > 0.f) c = __fdiv_rn((float)Kq, M);
+        for (int n = threadIdx.x; n < kpadded; n += blockDim.x) {
+            const int t = n - 64;
+            kq[n] = __float2half_rn((c > 0.f && t >= 0 && t < g.N) ? rintf(__fmul_rn(c, k[t])) : 0.f);
         }
-        for (int n = threadIdx.x; n < g.N; n += blockDim.x)
-            kq[n] = __float2half_rn(c > 0.f ? rintf(__fmul_rn(c, k[n])) : 0.f);
-        if (threadIdx.x == 0) ck_tab[f] = bad ? __int_as_float(0x7fc00000) : c;
+        if (threadIdx.x == 0 && blockIdx.y == 0) {
+            ck_tab[f] = bad ? __int_as_float(0x7fc00000) : c;
+            if (bad) atomicOr(status, 1u);
+        }
     } else {
-        for (int n = threadIdx.x; n < g.N; n += blockDim.x) kq[n] = __float2half_rn(0.f);
+        for (int n = threadIdx.x; n < kpadded; n += blockDim.x) kq[n] = __float2half_rn(0.f);
     }
     __syncthreads();
     const int grp = f / g.G, fl = f % g.G;
     __half* rows = bt + ((int64_t)grp * kTcN + (int64_t)fl * g.P) * g.Kpad;
-    for (int p = 0; p < g.P; ++p) {
-        __half* row = rows + (int64_t)p * g.Kpad;
-        for (int j = threadIdx.x; j < g.Kpad; j += blockDim.x) {
-            const int n = p + g.N - 1 - j;
-            row[j] = (n >= 0 && n < g.N) ? kq[n] : __float2half_rn(0.f);
+    const int half_row = g.Kpad / 2;
+    for (int p = blockIdx.y; p < g.P; p += gridDim.y) {
+        __half2* row = reinterpret_cast<__half2*>(rows + (int64_t)p * g.Kpad);
+        for (int jj = threadIdx.x; jj < half_row; jj += blockDim.x) {
+            const int j = 2 * jj;
+            // taps n = p + N - 1 - j and n - 1; past the band they read the zero pad
+            int n0 = p + g.N - 1 - j;
+            n0 = n0 < -64 ? -64 : (n0 > g.N + 63 ? g.N + 63 : n0);
+            const int n1 = n0 - 1 < -64 ? -64 : n0 - 1;
+            row[jj] = __halves2half2(kq[n0 + 64], kq[n1 + 64]);
         }
     }
 }
 
+// Persistent: CTA i takes tiles i, i + gridDim.x, ...; tile t is block t / ngroups,
+// kernel group t % ngroups (the groups of one block run side by side, so a
+// block's segment comes from DRAM once).  The shared-memory ring runs across
+// tiles; the accumulator is double-buffered in tensor memory (2 x 256
+// columns) so that the epilogue of one tile overlaps the MMAs of the next.
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGeom g,
              const float* __restrict__ cs_tab, const float* __restrict__ ck_tab, float* __restrict__ y,
              int32_t* __restrict__ yq, unsigned* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, issued_sh;
     const uint32_t base = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t blk = blockIdx.x;
-    const int grp = blockIdx.y;
+    const int64_t ntiles = g.nb * g.ngroups;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&accf_bar[a]), 1);
+            mbar_init(smem_u32(&acce_bar[a]), 4);  // one arrival per epilogue warp
+        }
         abort_sh = 0;
         issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -268,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(kTcTmemCols)
+                     "r"(2 * kTcTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -279,96 +332,127 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            const int arow0 = (int)(blk * g.seg_rows);
-            int kt = 0;
-            for (; kt < g.ktiles; ++kt) {
-                const int s = kt % kTcStages;
-                const uint32_t ph = (uint32_t)(kt / kTcStages) & 1u;
-                if (kt >= kTcStages && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, false)) {
-                    atomicOr(status, 2u);
-                    abort_sh = 1;
-                    break;
+            int it = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !abort_sh; t += gridDim.x) {
+                const int64_t blk = t / g.ngroups;
+                const int grp = (int)(t % g.ngroups);
+                const int arow0 = (int)(blk * g.seg_rows);
+                for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
+                    const int s = it % kTcStages;
+                    const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
+                    if (it >= kTcStages && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, false)) {
+                        atomicOr(status, 2u);
+                        abort_sh = 1;
+                        break;
+                    }
+                    if (*(volatile int*)&abort_sh) break;
+                    const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    const int j0 = kt * kTcK;
+                    mbar_expect_tx(fb, kTcStageBytes);
+                    tma_load_2d(sa, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
+                    tma_load_2d(sb, &tmB, j0, grp * kTcN, fb);
+                    issued_sh = it + 1;
                 }
-                if (*(volatile int*)&abort_sh) break;
-                const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                const int j0 = kt * kTcK;
-                mbar_expect_tx(fb, kTcStageBytes);
-                tma_load_2d(sa, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
-                tma_load_2d(sb, &tmB, j0, grp * kTcN, fb);
             }
-            issued_sh = kt;
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            for (int kt = 0; kt < g.ktiles; ++kt) {
-                const int s = kt % kTcStages;
-                const uint32_t ph = (uint32_t)(kt / kTcStages) & 1u;
-                if (!mbar_wait(smem_u32(&full_bar[s]), ph, false) || *(volatile int*)&abort_sh) {
+            int it = 0, local = 0;
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+                const int a = local & 1;
+                const uint32_t acc = tmem + (uint32_t)(a * kTcTmemCols);
+                if (local >= 2 &&
+                    (!mbar_wait(smem_u32(&acce_bar[a]), (uint32_t)((local >> 1) - 1) & 1u, false) ||
+                     *(volatile int*)&abort_sh)) {
                     atomicOr(status, 2u);
                     abort_sh = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+                bool ok = true;
+                for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
+                    const int s = it % kTcStages;
+                    const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), ph, false) || *(volatile int*)&abort_sh) {
+                        atomicOr(status, 2u);
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
 #pragma unroll
-                for (int k = 0; k < kTcK / 16; ++k)
-                    umma_f16(tmem, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
-                umma_commit(smem_u32(&empty_bar[s]));
+                    for (int k = 0; k < kTcK / 16; ++k)
+                        umma_f16(acc, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
+                    umma_commit(smem_u32(&empty_bar[s]));
+                }
+                umma_commit(smem_u32(&accf_bar[a]));  // this tile's MMAs done
+                if (!ok) break;
             }
-            umma_commit(smem_u32(&acc_bar));  // all issued MMAs done
         }
     } else {  // epilogue: warps 2..5, TMEM lane quarter warp % 4
-        const bool ok = mbar_wait(smem_u32(&acc_bar), 0u, true);
-        tc_fence_after();
-        __syncwarp();
-        if (!ok) {
-            if (lane == 0) atomicOr(status, 2u);
-        } else if (!*(volatile int*)&abort_sh) {
-            const int lq = warp & 3;
-            const int row = lq * 32 + lane;
+        const int lq = warp & 3;
+        const int row = lq * 32 + lane;
+        int local = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            const int a = local & 1;
+            const bool ok = mbar_wait(smem_u32(&accf_bar[a]), (uint32_t)(local >> 1) & 1u, true);
+            tc_fence_after();
+            __syncwarp();
+            if (!ok || *(volatile int*)&abort_sh) {
+                if (lane == 0) atomicOr(status, ok ? 0u : 2u);
+                break;
+            }
+            const int64_t blk = t / g.ngroups;
+            const int grp = (int)(t % g.ngroups);
             const int64_t trow = blk * (int64_t)g.T + (int64_t)row * g.P;
             const float cs = cs_tab[blk];
+            const uint32_t acc = tmem + (uint32_t)(a * kTcTmemCols) + ((uint32_t)(lq * 32) << 16);
             for (int fl = 0; fl < g.G; ++fl) {
                 const int f = grp * g.G + fl;
                 if (f >= g.F) break;
                 const float ck = ck_tab[f];
                 float inv = 0.f;
                 if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
-                else if (!(cs >= 0.f) || !(ck >= 0.f)) inv = __int_as_float(0x7fc00000);
                 float* yf = y + (int64_t)f * g.ldy;
                 int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
                 for (int c = 0; c < g.P; c += 32) {
                     uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(fl * g.P + c), r);
-                    const int64_t t = trow + c;
-                    if (t >= g.out_len) continue;
+                    tmem_ld32(acc + (uint32_t)(fl * g.P + c), r);
+                    const int64_t tt = trow + c;
+                    if (tt >= g.out_len) continue;
                     float v[32];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const float a = __uint_as_float(r[i]);
-                        v[i] = a == 0.f ? 0.f : __fmul_rn(a, inv);
+                        const float x = __uint_as_float(r[i]);
+                        v[i] = x == 0.f ? 0.f : __fmul_rn(x, inv);
                     }
-                    if (t + 32 <= g.out_len) {
+                    if (tt + 32 <= g.out_len) {
 #pragma unroll
                         for (int i = 0; i < 32; i += 4)
-                            *reinterpret_cast<float4*>(yf + t + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                            __stcs(reinterpret_cast<float4*>(yf + tt + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
                         if (qf) {
 #pragma unroll
                             for (int i = 0; i < 32; i += 4)
-                                *reinterpret_cast<int4*>(qf + t + i) = make_int4(
+                                *reinterpret_cast<int4*>(qf + tt + i) = make_int4(
                                     __float2int_rn(__uint_as_float(r[i])), __float2int_rn(__uint_as_float(r[i + 1])),
                                     __float2int_rn(__uint_as_float(r[i + 2])),
                                     __float2int_rn(__uint_as_float(r[i + 3])));
                         }
                     } else {
-                        for (int i = 0; i < 32 && t + i < g.out_len; ++i) {
-                            yf[t + i] = v[i];
-                            if (qf) qf[t + i] = __float2int_rn(__uint_as_float(r[i]));
+                        for (int i = 0; i < 32 && tt + i < g.out_len; ++i) {
+                            yf[tt + i] = v[i];
+                            if (qf) qf[tt + i] = __float2int_rn(__uint_as_float(r[i]));
                         }
                     }
                 }
             }
+            // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[a]))
+                                        : "memory");
         }
     }
 
@@ -376,13 +460,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     if (warp == 0 && lane == 0 && abort_sh) {
         // TMA loads issued but never consumed: let them land before the CTA exits
-        for (int kt = issued_sh - kTcStages; kt < issued_sh; ++kt)
-            if (kt >= 0) (void)mbar_wait(smem_u32(&full_bar[kt % kTcStages]), (uint32_t)(kt / kTcStages) & 1u, true);
+        for (int i = issued_sh - kTcStages; i < issued_sh; ++i)
+            if (i >= 0) (void)mbar_wait(smem_u32(&full_bar[i % kTcStages]), (uint32_t)(i / kTcStages) & 1u, true);
     }
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcTmemCols)
                      : "memory");
     }
 }
@@ -462,11 +546,18 @@ cudaError_t launch_tc(const TcGeom& g, const float* s, int64_t L, const float* k
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    }
+    const int64_t ntiles = g.nb * g.ngroups;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
     k_tc_quant<<<(unsigned)g.nb, 256, 0, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
-    k_tc_kern<<<(unsigned)(g.ngroups * g.G), 256, sizeof(__half) * (size_t)g.N, st>>>(kb, g, Kq, (__half*)bt,
-                                                                                    ck_tab, status);
-    k_tc_mma<<<dim3((unsigned)g.nb, (unsigned)g.ngroups), kTcThreads, tc_smem_bytes(), st>>>(ma, mb, g, cs_tab,
-                                                                                         ck_tab, y, yq, status);
+    k_tc_kern<<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(__half) * (size_t)(g.N + 128),
+                st>>>(kb, g, Kq, (__half*)bt, ck_tab, status);
+    k_tc_mma<<<grid, kTcThreads, tc_smem_bytes(), st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ def test_filterbank_matches_oracle(ctx, L, F, N, Sq, Kq):
 def test_padded_rows_and_zero_kernel_and_silence(ctx):
     L, F, N = 30000, 6, 200
     s = wl.random_signal(5, L, "laplace", 0.1)
-    s[8000:20000] = 0.0          # a block whose window is silent
+    s[8000:] = 0.0               # blocks whose windows are silent
     kb = np.stack([wl.random_signal(50 + f, N, "uniform") for f in range(F)])
     kb[2] = 0.0
     y, yq, cs, T, nb = run_gpu(ctx, s, kb, 127, 127, pad=36)
