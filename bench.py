@@ -270,6 +270,71 @@ def bench_batched(ctx, tuner, dev, steps, flush, stream):
     return res
 
 
+def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
+    """2^22 N(0,1) samples through 32 Hann-windowed-sinc band-pass kernels of
+    1024 taps on the tensor cores (S_q = K_q = 127, exact integer arithmetic),
+    against the same bank through the FP32 full-precision path (32 calls of
+    apx_conv_full with the tuned core and W_block)."""
+    import torch
+    from paper_1201_3018_gb300 import apx
+    s, kb = wl.filterbank()
+    F, N = kb.shape
+    L = len(s)
+    out_len = L + N - 1
+    ldy = (out_len + 3) // 4 * 4
+    sd = torch.from_numpy(s).to(dev)
+    kd = torch.from_numpy(kb).to(dev)
+    y = torch.empty(F, ldy, device=dev)
+    Q = 127
+
+    def step():
+        ctx.apx_filterbank(sd, kd, Q, Q, y, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    t = time_steps(step, steps, flush, stream) / steps
+    ctx.profile(True)
+    time_steps(step, min(steps, 20), flush, stream)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    mma_ms = prof["tc_mma"][0] / max(prof["tc_mma"][1], 1)
+    prep_ms = prof["tc_prep"][0] / max(prof["tc_prep"][1], 1)
+    ch = tuner.choose(N, apx.OP_CONV, apx.PACK_NONE, 0.0)
+    core = apx.CORE_FFT if ch["core"] == "fft" else apx.CORE_DIRECT
+    yfull = torch.empty(F, out_len, device=dev)
+
+    def full():
+        for f in range(F):
+            ctx.apx_conv_full(sd, kd[f], ch["W_block"], core | apx.PACK_NONE, yfull[f], stream=stream)
+
+    full()
+    nfull = max(3, steps // 20)
+    tf = time_steps(full, nfull, flush, stream) / nfull
+    step()
+    assert ctx.apx_sync(stream) == 0
+    d = (y[:, :out_len].double() - yfull.double())
+    snr = (10 * torch.log10((yfull.double() ** 2).sum(1) / (d * d).sum(1))).cpu().numpy()
+    T, nb = apx.filterbank_blocks(L, F, N)
+    kpad = -(-(N + 63) // 64) * 64
+    useful = 2.0 * F * out_len * N
+    peak = float(pk.get("bf16_tflops", 1899.0))
+    return {"workload": "filterbank: 2^22 N(0,1) samples, 32 Hann-windowed-sinc band-pass kernels of 1024 taps "
+                        "(log-spaced 50 Hz - 20 kHz at 44.1 kHz), S_q = K_q = 127, FP16 integers on the tensor cores",
+            "outputs_per_step": F * out_len, "value": F * out_len / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
+            "tflops_useful": useful / (t * 1e-3) / 1e12,
+            "full_precision": {"value": F * out_len / (tf * 1e-3) / 1e9, "ms_per_step": tf,
+                               "core": ch["core"], "W_block": ch["W_block"]},
+            "speedup_vs_full_precision": tf / t,
+            "snr_vs_full_db": {"min": float(snr.min()), "median": float(np.median(snr)), "max": float(snr.max())},
+            "kernel_ms": {"tc_prep": prep_ms, "tc_mma": mma_ms},
+            "roofline_tc_mma": {"bound": "tensor", "achieved": useful / (mma_ms * 1e-3) / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "frac": useful / (mma_ms * 1e-3) / 1e12 / peak,
+                                "peak_source": "measured cuBLAS bf16 (FP16 runs at the same tensor rate)",
+                                "executed_over_useful": kpad / N},
+            "blocks": nb, "outputs_per_block": T}
+
+
 def bench_serving(tuner, dev, seconds):
     """Poisson arrivals at 2000 req/s, L log-uniform in [2^12, 2^22], N in
     [64, 8192], targets {30, 45, 60} dB, 40 GB admission budget, 4 streams."""
@@ -416,6 +481,7 @@ def main():
         from paper_1201_3018_gb300 import tune
         tuner = tune.Tuner(ctx)
         extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
+        extras["filterbank"] = bench_filterbank(ctx, tuner, dev, args.steps, flush, stream, peaks())
         extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
 
     if rank != 0:
@@ -469,6 +535,7 @@ def main():
         "snr_vs_full_db": snr_vs_full,
         "serving": extras.get("serving", {"p50_ms": None, "p99_ms": None}),
         "batched": extras.get("batched"),
+        "filterbank": extras.get("filterbank"),
         "kernel_ms_per_step": {ph: prof[ph][0] / args.steps for ph in prof},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (L + N),

@@ -153,7 +153,9 @@ int64_t apx_launch_count(const apx_ctx* ctx);
 #define APX_PHASE_DIRECT  0   /* direct core: the single fused block kernel        */
 #define APX_PHASE_SPECTRA 1   /* FFT core: FP32 kernel spectrum (direct DFT)       */
 #define APX_PHASE_FFT     2   /* FFT core: block kernel (packed spectra on demand) */
-#define APX_NPHASES       3
+#define APX_PHASE_TC_PREP 3   /* filterbank: block companding and Toeplitz columns */
+#define APX_PHASE_TC_MMA  4   /* filterbank: tensor-core GEMM and inverse companding */
+#define APX_NPHASES       5
 int apx_profile(apx_ctx* ctx, int enable);
 int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
 

@@ -62,7 +62,7 @@ SIGNATURES = {
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
 }
-PHASES = ("direct", "spectra", "fft")
+PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
 
 
 def filterbank_blocks(L, F, N):

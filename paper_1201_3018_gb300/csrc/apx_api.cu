@@ -835,10 +835,20 @@ extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const 
     if (!rc) rc = ensure(ctx, ctx->tc_cs, sizeof(float) * (size_t)g.nb);
     if (!rc) rc = ensure(ctx, ctx->tc_ck, sizeof(float) * (size_t)g.ngroups * g.G);
     if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    {
+        Trace t(ctx, st, APX_PHASE_TC_PREP);
+        e = launch_tc_prep(g, s_in, L, k_bank, S_q, K_q, ctx->tc_seg.p, ctx->tc_b.p, (float*)ctx->tc_cs.p,
+                           (float*)ctx->tc_ck.p, block_cs, (unsigned*)ctx->flags.p, st);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
     bool enc_failed = false;
-    cudaError_t e = launch_tc(g, s_in, L, k_bank, S_q, K_q, ctx->tc_seg.p, ctx->tc_b.p, (float*)ctx->tc_cs.p,
-                              (float*)ctx->tc_ck.p, y_out, yq_out, block_cs, (unsigned*)ctx->flags.p,
-                              (cudaStream_t)stream, &enc_failed);
+    {
+        Trace t(ctx, st, APX_PHASE_TC_MMA);
+        e = launch_tc_mma(g, ctx->tc_seg.p, ctx->tc_b.p, (const float*)ctx->tc_cs.p, (const float*)ctx->tc_ck.p, y_out,
+                          yq_out, (unsigned*)ctx->flags.p, st, &enc_failed);
+    }
     if (enc_failed) return APX_ERR_CUDA;
     if (e == cudaSuccess) ctx->launches += 3;
     return cuda_status(e);

@@ -27,11 +27,19 @@
 //               block's FP16 segment (Eq. 2), c_s to the block table.
 //   k_tc_kern   one CTA per kernel: c_k, companding, the Toeplitz columns of B
 //               (K-major, FP16).
-//   k_tc_mma    one CTA per (block, kernel group): warp 0 streams A and B
-//               slices with TMA into a 4-stage shared-memory ring, warp 1
-//               issues tcgen05.mma (M 128, N 256, K 16, FP32 accumulators in
-//               tensor memory), warps 2-5 read the accumulators back with
-//               tcgen05.ld, scale by (c_s c_k)^-1 (Eq. 16) and store.
+//   k_tc_mma    persistent, one CTA per SM over the (block, kernel group)
+//               tiles: warp 0 streams operands with TMA into a shared-memory
+//               ring, warp 1 issues tcgen05.mma (M 128, N 256, K 16, FP32
+//               accumulators in tensor memory, double-buffered), warps 2-5
+//               read the accumulators back with tcgen05.ld, scale by
+//               (c_s c_k)^-1 (Eq. 16) and store.
+//
+// With P = 64 a row of S is exactly one 128-byte swizzle row, and the A slice
+// of K step kt is rows kt .. kt+127 of S: the whole A operand of a tile (its
+// 128 + ktiles - 1 rows) is loaded once, and each K step's descriptor starts
+// kt rows further in (the swizzle phase goes in the descriptor's base-offset
+// field).  Only B streams through the ring.  For P = 128 or 256 both operands
+// stream, one 128 x 64 A box per K step.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -43,11 +51,14 @@ namespace apx {
 
 namespace {
 
-constexpr int kTcThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kTcEpiWarps = 4;   // one per tensor-memory lane quarter
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
 constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
-constexpr uint32_t kTcStageBytes = kTcABytes + kTcBBytes;
 constexpr uint32_t kTcTmemCols = kTcN;
+constexpr uint32_t kTcStageOut = kTcEpiWarps * 4096;  // output staging, 4 KB per epilogue warp
+constexpr int kTcABoxRows = 64;                     // resident A: TMA box rows
+constexpr uint32_t kTcABoxBytes = kTcABoxRows * 128;
 constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
 // kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B FP16
 // (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -103,8 +114,11 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // Shared-memory matrix descriptor, K-major with the 128-byte swizzle that the
 // TMA loads write: start address >> 4 (bits 0-13), leading byte offset 16
 // (unused for this layout), stride byte offset 1024 between 8-row groups
-// (bits 32-45), descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits
-// 61-63).
+// (bits 32-45), descriptor version 1 (bit 46), base offset 0 (bits 49-51),
+// swizzle mode 2 = 128 B (bits 61-63).  The swizzle phase of a row follows its
+// address bits 7-9 (the buffers are 1024-byte aligned, as the TMA writes
+// them), so a start address 32 k bytes into a row (K step k) or kt rows into
+// a buffer (the resident Toeplitz operand) selects that sub-matrix.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
@@ -124,7 +138,7 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -134,8 +148,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64_t hi, int64_t L, bool* bad,
                                                float* red) {
@@ -288,31 +303,42 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
     }
 }
 
-// Persistent: CTA i takes tiles i, i + gridDim.x, ...; tile t is block t / ngroups,
-// kernel group t % ngroups (the groups of one block run side by side, so a
-// block's segment comes from DRAM once).  The shared-memory ring runs across
-// tiles; the accumulator is double-buffered in tensor memory (2 x 256
-// columns) so that the epilogue of one tile overlaps the MMAs of the next.
+// Persistent: CTA c takes tiles u = c, c + gridDim.x, ...; tile u is block
+// u / ngroups, kernel group u % ngroups (the groups of one block run side by
+// side, so a block's segment comes from DRAM once).  The shared-memory ring
+// runs across tiles; the accumulator is double-buffered in tensor memory
+// (2 x 256 columns) so that the epilogue of one tile overlaps the MMAs of the
+// next.
+template <bool RESIDENT_A>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGeom g,
              const float* __restrict__ cs_tab, const float* __restrict__ ck_tab, float* __restrict__ y,
              int32_t* __restrict__ yq, unsigned* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], accf_bar[2], acce_bar[2];
+    __shared__ __align__(8) uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], accf_bar[2], acce_bar[2],
+        afull_bar[2], aempty_bar[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, issued_sh;
     const uint32_t base = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;
+    // [output staging, 4 KB per epilogue warp][A buffer 0][A buffer 1][B stages] (RESIDENT_A)
+    // [output staging][B stage, A stage] x stages (otherwise)
+    const uint32_t abuf0 = base + kTcStageOut;
+    const uint32_t ring = RESIDENT_A ? abuf0 + 2u * (uint32_t)g.abuf_bytes : abuf0;
+    const uint32_t stage_bytes = RESIDENT_A ? kTcBBytes : kTcABytes + kTcBBytes;
+    const int S = g.stages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = g.nb * g.ngroups;
+    const int64_t nsets = g.nb * g.ngroups;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&accf_bar[a]), 1);
-            mbar_init(smem_u32(&acce_bar[a]), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&acce_bar[a]), kTcEpiWarps);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&afull_bar[a]), 1);
+            mbar_init(smem_u32(&aempty_bar[a]), 1);
         }
         abort_sh = 0;
         issued_sh = 0;
@@ -332,26 +358,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            int it = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && !abort_sh; t += gridDim.x) {
-                const int64_t blk = t / g.ngroups;
-                const int grp = (int)(t % g.ngroups);
+            int it = 0, local = 0;
+            for (int64_t u = blockIdx.x; u < nsets && !*(volatile int*)&abort_sh; u += gridDim.x, ++local) {
+                const int64_t blk = u / g.ngroups;
+                const int grp = (int)(u % g.ngroups);
                 const int arow0 = (int)(blk * g.seg_rows);
+                if (RESIDENT_A) {
+                    const int ab = local & 1;
+                    if (local >= 2 &&
+                        !mbar_wait(smem_u32(&aempty_bar[ab]), (uint32_t)((local >> 1) - 1) & 1u, false)) {
+                        atomicOr(status, 2u);
+                        abort_sh = 1;
+                        break;
+                    }
+                    const uint32_t afb = smem_u32(&afull_bar[ab]);
+                    const uint32_t abase = abuf0 + (uint32_t)ab * (uint32_t)g.abuf_bytes;
+                    mbar_expect_tx(afb, (uint32_t)g.abuf_bytes);
+                    for (int r = 0; r < g.a_loads; ++r)
+                        tma_load_2d(abase + (uint32_t)r * kTcABoxBytes, &tmA, 0, arow0 + r * kTcABoxRows, afb);
+                }
                 for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
-                    const int s = it % kTcStages;
-                    const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
-                    if (it >= kTcStages && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, false)) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, false)) {
                         atomicOr(status, 2u);
                         abort_sh = 1;
                         break;
                     }
                     if (*(volatile int*)&abort_sh) break;
-                    const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+                    const uint32_t st = ring + (uint32_t)s * stage_bytes;
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     const int j0 = kt * kTcK;
-                    mbar_expect_tx(fb, kTcStageBytes);
-                    tma_load_2d(sa, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
-                    tma_load_2d(sb, &tmB, j0, grp * kTcN, fb);
+                    mbar_expect_tx(fb, stage_bytes);
+                    if (!RESIDENT_A) tma_load_2d(st + kTcBBytes, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
+                    tma_load_2d(st, &tmB, j0, grp * kTcN, fb);
                     issued_sh = it + 1;
                 }
             }
@@ -359,7 +399,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             int it = 0, local = 0;
-            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            for (int64_t u = blockIdx.x; u < nsets; u += gridDim.x, ++local) {
                 const int a = local & 1;
                 const uint32_t acc = tmem + (uint32_t)(a * kTcTmemCols);
                 if (local >= 2 &&
@@ -369,11 +409,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     abort_sh = 1;
                     break;
                 }
+                if (RESIDENT_A && !mbar_wait(smem_u32(&afull_bar[a]), (uint32_t)(local >> 1) & 1u, false)) {
+                    atomicOr(status, 2u);
+                    abort_sh = 1;
+                    break;
+                }
                 tc_fence_after();
+                const uint32_t abase = abuf0 + (uint32_t)a * (uint32_t)g.abuf_bytes;
                 bool ok = true;
                 for (int kt = 0; kt < g.ktiles; ++kt, ++it) {
-                    const int s = it % kTcStages;
-                    const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
                     if (!mbar_wait(smem_u32(&full_bar[s]), ph, false) || *(volatile int*)&abort_sh) {
                         atomicOr(status, 2u);
                         abort_sh = 1;
@@ -381,21 +427,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = base + (uint32_t)s * kTcStageBytes, sb = sa + kTcABytes;
+                    const uint32_t sb = ring + (uint32_t)s * stage_bytes;
+                    const uint32_t sa = RESIDENT_A ? abase + (uint32_t)kt * 128u : sb + kTcBBytes;
 #pragma unroll
                     for (int k = 0; k < kTcK / 16; ++k)
                         umma_f16(acc, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
                     umma_commit(smem_u32(&empty_bar[s]));
                 }
                 umma_commit(smem_u32(&accf_bar[a]));  // this tile's MMAs done
+                if (RESIDENT_A) umma_commit(smem_u32(&aempty_bar[a]));
                 if (!ok) break;
             }
         }
-    } else {  // epilogue: warps 2..5, TMEM lane quarter warp % 4
+    } else {  // epilogue: warps 2..9, TMEM lane quarter warp % 4; the two warps of a
+              // quarter take alternate 32-column chunks
         const int lq = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = lq * 32 + lane;
         int local = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+        for (int64_t u = blockIdx.x; u < nsets; u += gridDim.x, ++local) {
             const int a = local & 1;
             const bool ok = mbar_wait(smem_u32(&accf_bar[a]), (uint32_t)(local >> 1) & 1u, true);
             tc_fence_after();
@@ -404,48 +454,65 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (lane == 0) atomicOr(status, ok ? 0u : 2u);
                 break;
             }
-            const int64_t blk = t / g.ngroups;
-            const int grp = (int)(t % g.ngroups);
-            const int64_t trow = blk * (int64_t)g.T + (int64_t)row * g.P;
+            const int64_t blk = u / g.ngroups;
+            const int grp = (int)(u % g.ngroups);
             const float cs = cs_tab[blk];
             const uint32_t acc = tmem + (uint32_t)(a * kTcTmemCols) + ((uint32_t)(lq * 32) << 16);
+            // this warp's 4 KB staging buffer: 32 rows x 32 floats, 16-byte slot i of
+            // row r at r * 128 + ((i ^ (r & 7)) * 16) (conflict-free both ways)
+            const uint32_t stg = base + (uint32_t)(warp - 2) * 4096u;
+            const int rr = lane >> 3, ii = lane & 7;
             for (int fl = 0; fl < g.G; ++fl) {
                 const int f = grp * g.G + fl;
                 if (f >= g.F) break;
-                const float ck = ck_tab[f];
+                // (c_s c_k)^-1 once per warp (FP64 is a small fraction of the FP32 rate)
                 float inv = 0.f;
-                if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
+                if (lane == 0) {
+                    const float ck = ck_tab[f];
+                    if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
+                }
+                inv = __shfl_sync(0xffffffffu, inv, 0);
                 float* yf = y + (int64_t)f * g.ldy;
                 int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
-                for (int c = 0; c < g.P; c += 32) {
+                for (int c = 32 * half; c < g.P; c += 32 * (kTcEpiWarps / 4)) {
                     uint32_t r[32];
-                    tmem_ld32(acc + (uint32_t)(fl * g.P + c), r);
-                    const int64_t tt = trow + c;
-                    if (tt >= g.out_len) continue;
-                    float v[32];
+                    tmem_ld32_nowait(acc + (uint32_t)(fl * g.P + c), r);
+                    tmem_wait_ld();
+                    // scale (Eq. 16) and stage this lane's row
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float x = __uint_as_float(r[i]);
-                        v[i] = x == 0.f ? 0.f : __fmul_rn(x, inv);
+                    for (int i = 0; i < 8; ++i) {
+                        float v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
+                        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                         stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
+                                     "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                                     : "memory");
                     }
-                    if (tt + 32 <= g.out_len) {
+                    if (qf) {  // integer outputs (a test aid): straight from the row
+                        const int64_t t0 = blk * (int64_t)g.T + (int64_t)row * g.P + c;
+                        for (int i = 0; i < 32 && t0 + i < g.out_len; ++i)
+                            qf[t0 + i] = __float2int_rn(__uint_as_float(r[i]));
+                    }
+                    __syncwarp();
+                    // four whole rows (4 x 128 contiguous bytes) per store instruction
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
-                            __stcs(reinterpret_cast<float4*>(yf + tt + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
-                        if (qf) {
-#pragma unroll
-                            for (int i = 0; i < 32; i += 4)
-                                *reinterpret_cast<int4*>(qf + tt + i) = make_int4(
-                                    __float2int_rn(__uint_as_float(r[i])), __float2int_rn(__uint_as_float(r[i + 1])),
-                                    __float2int_rn(__uint_as_float(r[i + 2])),
-                                    __float2int_rn(__uint_as_float(r[i + 3])));
-                        }
-                    } else {
-                        for (int i = 0; i < 32 && tt + i < g.out_len; ++i) {
-                            yf[tt + i] = v[i];
-                            if (qf) qf[tt + i] = __float2int_rn(__uint_as_float(r[i]));
+                    for (int j = 0; j < 8; ++j) {
+                        const int srow = 4 * j + rr;
+                        float4 v;
+                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                                     : "r"(stg + (uint32_t)srow * 128u + (uint32_t)((ii ^ (srow & 7)) * 16))
+                                     : "memory");
+                        const int64_t t = blk * (int64_t)g.T + (int64_t)(lq * 32 + srow) * g.P + c + 4 * ii;
+                        if (t + 4 <= g.out_len) {
+                            __stcs(reinterpret_cast<float4*>(yf + t), v);
+                        } else {
+                            const float w[4] = {v.x, v.y, v.z, v.w};
+                            for (int e = 0; e < 4 && t + e < g.out_len; ++e) yf[t + e] = w[e];
                         }
                     }
+                    __syncwarp();
                 }
             }
             // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
@@ -460,8 +527,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     if (warp == 0 && lane == 0 && abort_sh) {
         // TMA loads issued but never consumed: let them land before the CTA exits
-        for (int i = issued_sh - kTcStages; i < issued_sh; ++i)
-            if (i >= 0) (void)mbar_wait(smem_u32(&full_bar[i % kTcStages]), (uint32_t)(i / kTcStages) & 1u, true);
+        for (int i = issued_sh - S; i < issued_sh; ++i)
+            if (i >= 0) (void)mbar_wait(smem_u32(&full_bar[i % S]), (uint32_t)(i / S) & 1u, true);
     }
     __syncthreads();
     if (warp == 1) {
@@ -522,27 +589,50 @@ bool tc_geometry(int64_t L, int F, int N, TcGeom* g) {
     g->nb = (g->out_len + g->T - 1) / g->T;
     g->seg_rows = ((int64_t)g->T + g->Kpad + g->P - 1) / g->P;
     g->ldy = g->out_len;
+    const int budget = kMaxSmem - 1024;  // data bytes after the 1024-byte alignment slack
+    if (g->P == 64) {
+        g->a_loads = (kTcM - 1 + g->ktiles + kTcABoxRows - 1) / kTcABoxRows;
+        g->abuf_bytes = g->a_loads * (int)kTcABoxBytes;
+        g->stages = (budget - (int)kTcStageOut - 2 * g->abuf_bytes) / (int)kTcBBytes;
+    } else {
+        g->a_loads = 0;
+        g->abuf_bytes = 0;
+        g->stages = (budget - (int)kTcStageOut) / (int)(kTcABytes + kTcBBytes);
+    }
+    if (g->stages > kTcMaxStages) g->stages = kTcMaxStages;
+    if (g->stages < 2) return false;
+    g->smem_bytes = (int)kTcStageOut +
+                    (g->P == 64 ? 2 * g->abuf_bytes + g->stages * (int)kTcBBytes
+                                : g->stages * (int)(kTcABytes + kTcBBytes)) + 1024;
     return true;
 }
 
 size_t tc_seg_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)(g.nb * g.seg_rows * g.P); }
 size_t tc_b_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)g.ngroups * kTcN * (size_t)g.Kpad; }
-size_t tc_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + 1024; }
 
-cudaError_t launch_tc(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
-                      void* bt, float* cs_tab, float* ck_tab, float* y, int32_t* yq, float* cs_out, unsigned* status,
-                      cudaStream_t st, bool* encode_failed) {
+cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
+                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st) {
+    k_tc_quant<<<(unsigned)g.nb, 256, 0, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
+    k_tc_kern<<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(__half) * (size_t)(g.N + 128),
+                st>>>(kb, g, Kq, (__half*)bt, ck_tab, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* cs_tab, const float* ck_tab,
+                          float* y, int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed) {
     *encode_failed = false;
     CUtensorMap ma, mb;
-    if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * 2, kTcM) ||
+    if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * 2,
+                   g.P == 64 ? kTcABoxRows : kTcM) ||
         !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * 2, kTcN)) {
         *encode_failed = true;
         return cudaErrorInvalidValue;
     }
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc_smem_bytes());
+        cudaError_t e = cudaFuncSetAttribute(k_tc_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -552,12 +642,12 @@ cudaError_t launch_tc(const TcGeom& g, const float* s, int64_t L, const float* k
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     }
-    const int64_t ntiles = g.nb * g.ngroups;
-    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-    k_tc_quant<<<(unsigned)g.nb, 256, 0, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
-    k_tc_kern<<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(__half) * (size_t)(g.N + 128),
-                st>>>(kb, g, Kq, (__half*)bt, ck_tab, status);
-    k_tc_mma<<<grid, kTcThreads, tc_smem_bytes(), st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
+    const int64_t nsets = g.nb * g.ngroups;
+    const unsigned grid = (unsigned)(nsets < sms ? nsets : sms);
+    if (g.P == 64)
+        k_tc_mma<true><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
+    else
+        k_tc_mma<false><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
     return cudaGetLastError();
 }
 
