@@ -335,6 +335,86 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
             "blocks": nb, "outputs_per_block": T}
 
 
+def bench_paper_comparison(ctx, dev, flush, stream):
+    """The paper's own comparison on this GPU: packed FP64 against full
+    precision in FP64 (the paper's baseline is an FP64 convolution), next to
+    the FP32 full-precision denominator.
+      single_conv: L = 65536 N(0,1), N = 64 U[-1,1], W_block = 1024, direct
+        core, as R = 1024 independent copies in one captured graph (a single
+        copy is launch-latency bound): per-block selection at 45 dB, FP64
+        full, FP32 full.
+      e1: the Section IV.A throughput-test shape, L = 8192 * 2^10 U[-128,128],
+        N = 800, direct core, fixed S_q = K_q = 16 (symmetric, asymmetric M=3)
+        and 256 (asymmetric M=2) where the exactness bound admits them, per
+        W_block; SNR against the FP64 full-precision output."""
+    import torch
+    from paper_1201_3018_gb300 import apx
+    out = {}
+    case = wl.single_conv()
+    R = 1024
+    s = torch.from_numpy(case.s).to(dev)
+    k = torch.from_numpy(case.k).to(dev)
+    n_out = len(case.s) + len(case.k) - 1
+    rbuf = torch.empty(R, n_out, device=dev)
+    res = {}
+    for name, mode in (("auto_45db", apx.CORE_DIRECT | apx.PACK_AUTO),
+                       ("full_fp64", apx.CORE_DIRECT | apx.PACK_NONE | apx.FULL_FP64),
+                       ("full_fp32", apx.CORE_DIRECT | apx.PACK_NONE)):
+        items = [dict(s=s, k=k, r=rbuf[j], mode=mode, W_block=case.Wblock, snr_db=45.0) for j in range(R)]
+        g = ctx.graph(ctx.make_requests(items), stream=stream)
+        for _ in range(3):
+            g.launch(stream)
+        nrep = 10
+        t = time_steps(lambda: g.launch(stream), nrep, flush, stream) / nrep
+        g.close()
+        res[name] = {"value": R * n_out / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t}
+    P, _ = apx.plan_blocks(len(case.s), len(case.k), case.Wblock, apx.CORE_DIRECT)
+    st = torch.empty(P * apx.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    ctx.apx_conv(s, k, case.Wblock, apx.CORE_DIRECT | apx.PACK_AUTO, 45.0, rbuf[0], None, st, stream=stream)
+    ctx.apx_sync(stream)
+    modes = np.bincount(np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)["mode"], minlength=6)
+    res["block_modes_45db"] = {"full": int(modes[0]), "sym": int(modes[1]), "asym2": int(modes[2]),
+                               "asym3": int(modes[3])}
+    res["speedup_packed_vs_full_fp64"] = res["full_fp64"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
+    res["speedup_packed_vs_full_fp32"] = res["full_fp32"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
+    res["copies"] = R
+    out["single_conv"] = res
+
+    e1 = wl.uniform_e1()
+    s = torch.from_numpy(e1.s).to(dev)
+    k = torch.from_numpy(e1.k).to(dev)
+    n_out = len(e1.s) + len(e1.k) - 1
+    r = torch.empty(n_out, device=dev)
+    ref = torch.empty(n_out, device=dev)
+    rows = []
+
+    def timed(fn, nrep=3):
+        fn()
+        return time_steps(fn, nrep, flush, stream) / nrep
+
+    for Wb in (2048, 4096, 8192):
+        t64 = timed(lambda: ctx.apx_conv_full(s, k, Wb, apx.CORE_DIRECT | apx.PACK_NONE | apx.FULL_FP64, ref,
+                                              stream=stream))
+        t32 = timed(lambda: ctx.apx_conv_full(s, k, Wb, apx.CORE_DIRECT | apx.PACK_NONE, r, stream=stream))
+        rows.append({"W_block": Wb, "method": "full_fp32", "ms": t32, "value": n_out / (t32 * 1e-3) / 1e9})
+        rows.append({"W_block": Wb, "method": "full_fp64", "ms": t64, "value": n_out / (t64 * 1e-3) / 1e9})
+        for method, pack, Q in (("sym", apx.PACK_SYM, 16), ("asym3", apx.PACK_ASYM3, 16), ("asym2", apx.PACK_ASYM2, 256)):
+            row = {"W_block": Wb, "method": method, "Sq": Q, "Kq": Q}
+            try:
+                t = timed(lambda: ctx.apx_conv_fixed(s, k, Wb, apx.CORE_DIRECT | pack, Q, Q, r, stream=stream))
+            except apx.ApxError as e:
+                row["skipped"] = "%s (exactness bound or shared memory)" % apx.strerror(e.status)
+                rows.append(row)
+                continue
+            d = r.double() - ref.double()
+            row.update(ms=t, value=n_out / (t * 1e-3) / 1e9,
+                       snr_vs_full_fp64_db=float(10 * torch.log10((ref.double() ** 2).sum() / (d * d).sum())),
+                       speedup_vs_full_fp64=t64 / t, speedup_vs_full_fp32=t32 / t)
+            rows.append(row)
+    out["e1"] = {"workload": "L = 8192*2^10 U[-128,128], N = 800, direct core", "rows": rows}
+    return out
+
+
 def bench_serving(tuner, dev, seconds):
     """Poisson arrivals at 2000 req/s, L log-uniform in [2^12, 2^22], N in
     [64, 8192], targets {30, 45, 60} dB, 40 GB admission budget, 4 streams."""
@@ -482,6 +562,7 @@ def main():
         tuner = tune.Tuner(ctx)
         extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
         extras["filterbank"] = bench_filterbank(ctx, tuner, dev, args.steps, flush, stream, peaks())
+        extras["paper_comparison"] = bench_paper_comparison(ctx, dev, flush, stream)
         extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
 
     if rank != 0:
@@ -536,6 +617,7 @@ def main():
         "serving": extras.get("serving", {"p50_ms": None, "p99_ms": None}),
         "batched": extras.get("batched"),
         "filterbank": extras.get("filterbank"),
+        "paper_comparison": extras.get("paper_comparison"),
         "kernel_ms_per_step": {ph: prof[ph][0] / args.steps for ph in prof},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (L + N),

@@ -59,6 +59,10 @@ extern "C" {
 #define APX_PACK_SYM     0x200u  /* symmetric packing, Eqs. (4)-(5)            */
 #define APX_PACK_ASYM2   0x300u  /* asymmetric packing, M = 2, Eq. (7)         */
 #define APX_PACK_ASYM3   0x400u  /* asymmetric packing, M = 3, Eq. (7)         */
+#define APX_FULL_FP64    0x1000u /* with APX_PACK_NONE and the direct core: the
+                                    full-precision convolution in FP64 (the
+                                    paper's full-precision baseline runs in FP64),
+                                    rounded once to FP32 on output              */
 
 /* ---- per-block modes reported in apx_block_stats.mode ----------------- */
 #define APX_BLK_FULL      0

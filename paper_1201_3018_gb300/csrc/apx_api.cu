@@ -182,7 +182,9 @@ struct Plan {
 int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
     if (L < 1 || N < 1) return APX_ERR_ARG;
     if ((mode & 0xFu) > APX_OP_XCORR || ((mode >> 4) & 0xFu) > 1u || ((mode >> 8) & 0xFu) > 4u ||
-        (mode & ~0xFFFu))
+        (mode & ~(0xFFFu | APX_FULL_FP64)))
+        return APX_ERR_ARG;
+    if ((mode & APX_FULL_FP64) && ((mode & 0xF00u) != APX_PACK_NONE || (mode & 0xF0u) != APX_CORE_DIRECT))
         return APX_ERR_ARG;
     int fft = (mode & 0xF0u) == APX_CORE_FFT;
     int Nodd = (N % 2) ? N : N + 1;
@@ -205,12 +207,22 @@ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 // Direct core shared-memory layout for the candidate set: window (zero front
 // pad), FP32 taps, and for packed blocks the packed signal, the packed outputs
 // and the packed taps.
-size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl) {
+size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl, bool full64 = false) {
     dl->padF = round_up(Nodd, 8);
     size_t off = (size_t)4 * (dl->padF + Wb + 8);
     dl->offK = (int)((off + 15) / 16 * 16);
     off = (size_t)dl->offK + (size_t)4 * round_up(Nodd, 8);
     int padS = 0, body = 0, nT = 0, nkb = 0;
+    if (full64) {  // the window and the taps as FP64
+        padS = nkb = round_up(Nodd, 4);
+        body = Wb + 4;
+        dl->offS = (int)((off + 15) / 16 * 16);
+        dl->padS = padS;
+        dl->nS = padS + body;
+        dl->offT = (int)(((size_t)dl->offS + (size_t)8 * dl->nS + 15) / 16 * 16);
+        dl->offKb = dl->offT;
+        return (size_t)dl->offKb + (size_t)8 * nkb;
+    }
     for (int i = 0; i < nc; ++i) {
         int nkp = round_up(c[i].nk, 4);
         if (nkp > padS) padS = nkp;
@@ -334,6 +346,7 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     p.P = pl.P; p.out_len = L + N - 1;
     p.r = r; p.rq = rq; p.st = st;
     p.autosel = sel_kind == 0;
+    p.full64 = (mode & APX_FULL_FP64) ? 1 : 0;
     p.thr = pow(10.0, snr_db / 10.0);
     int nc = 0;
     if (sel_kind == 0) {
@@ -352,7 +365,7 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     // Shared memory of the block kernel for this candidate set.
     size_t smem = 0;
     if (!pl.fft) {
-        smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
+        smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl, p.full64 != 0);
         while (smem > (size_t)kMaxSmem && nc > 0 && sel_kind == 0) {
             // drop the widest asymmetric candidate that does not fit
             int drop = -1;
@@ -692,8 +705,8 @@ int apx_conv_fixed(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, i
 
 int apx_conv_full(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
                   uint32_t mode, float* r_out, void* stream) {
-    return run(ctx, s_in, L, k, N, W_block, (mode & 0xFFu) | APX_PACK_NONE, 2, 0.0, 0, 0, r_out, nullptr,
-               nullptr, (cudaStream_t)stream);
+    return run(ctx, s_in, L, k, N, W_block, (mode & (0xFFu | APX_FULL_FP64)) | APX_PACK_NONE, 2, 0.0, 0, 0, r_out,
+               nullptr, nullptr, (cudaStream_t)stream);
 }
 
 int apx_sync(apx_ctx* ctx, void* stream) {

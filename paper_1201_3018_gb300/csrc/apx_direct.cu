@@ -97,6 +97,33 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     __syncthreads();
     const int ci = s_ci;
 
+    if (ci < 0 && p.full64) {
+        // Full precision in FP64, Eq. (1) over the window, rounded once to FP32.
+        double* sd = reinterpret_cast<double*>(smem + dl.offS) + dl.padS;
+        double* kd = reinterpret_cast<double*>(smem + dl.offKb);
+        const int nkp = round_up(p.Nodd, kRd);
+        for (int t = threadIdx.x; t < dl.padS; t += blockDim.x) sd[t - dl.padS] = 0.0;
+        for (int t = threadIdx.x; t < dl.nS - dl.padS; t += blockDim.x) sd[t] = t < p.Wb ? (double)xs[t] : 0.0;
+        for (int n = threadIdx.x; n < nkp; n += blockDim.x) kd[n] = (double)ktap(p, n);
+        __syncthreads();
+        const int nout = g.hi - g.lo;
+        for (int ch = threadIdx.x; ch * kRd < nout; ch += blockDim.x) {
+            const int j0 = g.lo + ch * kRd;
+            double acc[kRd];
+            conv_f64<kRd>(sd, kd, nkp, j0, acc);
+#pragma unroll
+            for (int r = 0; r < kRd; ++r) {
+                const int j = j0 + r;
+                const long long o = g.start + j;
+                if (j < g.hi && o >= 0 && o < p.out_len) {
+                    p.r[o] = __double2float_rn(acc[r]);
+                    if (p.rq) p.rq[o] = 0;
+                }
+            }
+        }
+        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        return;
+    }
     if (ci < 0) {
         // Full precision (FP32), Eq. (1) over the window, taps staged in shared memory.
         const int nkp = round_up(p.Nodd, kRf);

@@ -68,6 +68,7 @@ struct Params {
     unsigned* ready;      // FFT core, per candidate: last call whose spectrum is complete
     unsigned epoch;       // FFT core: this call's number (never 0)
     int autosel;          // 1: per-block selection under thr
+    int full64;           // direct core, no packing: full precision in FP64
     int ncand;
     double thr;           // 10^(target/10)
     Cand cand[kMaxCand];

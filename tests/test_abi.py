@@ -80,3 +80,23 @@ def test_null_arguments_rejected_without_gpu(libapx):
     assert L.apx_conv(None, None, 10, None, 3, 16, 0, 30.0, None, None, None, None) == libapx.APX_ERR_ARG
     assert L.apx_sync(None, None) == libapx.APX_ERR_ARG
     assert L.apx_create(None, 0, 0) == libapx.APX_ERR_ARG
+
+
+def test_header_constants_match_binding():
+    """Every mode, status, block-kind and phase constant of include/apx.h has
+    the same value in the Python binding."""
+    from paper_1201_3018_gb300 import apx
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "apx.h")).read()
+    defs = dict(re.findall(r"#define\s+APX_(\w+)\s+\(?(-?(?:0x)?[0-9A-Fa-f]+)u?\)?", hdr))
+    checked = 0
+    for name, val in defs.items():
+        v = int(val, 0)
+        py = name if name.startswith(("OK", "ERR_")) else name
+        if hasattr(apx, "APX_" + name):
+            assert getattr(apx, "APX_" + name) == v, name
+            checked += 1
+        elif hasattr(apx, py):
+            assert getattr(apx, py) == v, name
+            checked += 1
+    assert checked >= 25, checked
+    assert int(defs["NPHASES"]) == len(apx.PHASES)

@@ -224,3 +224,32 @@ def test_matching_xcorr_full_size(ctx):
     for target in (45.0, 20.0):
         r, rq, st, ro, rqo, so = run_both(ctx, case.s, case.k, case.Wblock, mode, snr=target, want=want)
         check(r, rq, st, ro, rqo, so, case.s, case.k, mode, case.Wblock, want=want)
+
+
+@pytest.mark.parametrize("op", [apx.OP_CONV, apx.OP_XCORR])
+@pytest.mark.parametrize("L,N,Wb", [(1000, 64, 256), (20000, 65, 1024), (5, 3, 16), (9000, 1024, 4096), (3000, 1, 64)])
+def test_full_fp64_direct(ctx, op, L, N, Wb):
+    """FP64 full-precision twin: Eq. (1) in FP64 rounded once to FP32; against
+    the FP64 definition the error is one FP32 rounding plus the FP64
+    accumulation error N 2^-52 sum|s||k|."""
+    s = wl.random_signal(L + 21, L, "normal")
+    k = wl.random_signal(N + 22, N, "uniform")
+    r = torch.empty(L + N - 1, device="cuda")
+    ctx.apx_conv_full(dev(s), dev(k), Wb, op | apx.CORE_DIRECT | apx.PACK_NONE | apx.FULL_FP64, r)
+    assert ctx.apx_sync() == 0
+    kk = k[::-1].copy() if op == apx.OP_XCORR else k
+    ref = O.conv_ref(s, kk)
+    mag = O.conv_ref(np.abs(s), np.abs(kk))
+    err = np.abs(r.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= 2.0 ** -24 * np.abs(ref) + N * 2.0 ** -52 * mag + 1e-300)
+
+
+def test_full_fp64_needs_direct_core_and_no_packing(ctx):
+    s, k = dev(np.ones(100, np.float32)), dev(np.ones(5, np.float32))
+    r = torch.empty(104, device="cuda")
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv_full(s, k, 64, apx.CORE_FFT | apx.PACK_NONE | apx.FULL_FP64, r)
+    assert e.value.status == apx.APX_ERR_ARG
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv(s, k, 64, apx.CORE_DIRECT | apx.PACK_AUTO | apx.FULL_FP64, 30.0, r)
+    assert e.value.status == apx.APX_ERR_ARG
