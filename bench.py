@@ -49,7 +49,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, filterbank, comparison and serving "
+                                                             "measurements")
+    ap.add_argument("--extras", default="batched,filterbank,paper,serving",
+                    help="comma-separated subset of batched, filterbank, paper, serving")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
 
@@ -560,10 +563,15 @@ def main():
     if world == 1 and not args.no_extras:
         from paper_1201_3018_gb300 import tune
         tuner = tune.Tuner(ctx)
-        extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
-        extras["filterbank"] = bench_filterbank(ctx, tuner, dev, args.steps, flush, stream, peaks())
-        extras["paper_comparison"] = bench_paper_comparison(ctx, dev, flush, stream)
-        extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
+        want = set(args.extras.split(","))
+        if "batched" in want:
+            extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
+        if "filterbank" in want:
+            extras["filterbank"] = bench_filterbank(ctx, tuner, dev, args.steps, flush, stream, peaks())
+        if "paper" in want:
+            extras["paper_comparison"] = bench_paper_comparison(ctx, dev, flush, stream)
+        if "serving" in want:
+            extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
 
     if rank != 0:
         ctx.close()
