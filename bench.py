@@ -117,6 +117,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(use), "in_timed_window": bool(inwin)}
 
 
+def traffic_for(name):
+    """DRAM bytes per launch of a kernel from the committed ncu capture, or
+    None once the kernel sources have changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    try:
+        ent = json.load(open(TRAFFIC_FILE)).get(name)
+    except (OSError, ValueError):
+        return None
+    if ent and ent.get("source_sha") == kernel_source_sha():
+        return ent.get("dram_bytes_per_launch")
+    return None
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1201_3018_gb300", "csrc")
@@ -334,7 +348,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
             "roofline_tc_mma": {"bound": "tensor", "achieved": useful / (mma_ms * 1e-3) / 1e12, "peak": peak,
                                 "unit": "TFLOP/s", "frac": useful / (mma_ms * 1e-3) / 1e12 / peak,
                                 "peak_source": "measured cuBLAS bf16 (FP16 runs at the same tensor rate)",
-                                "executed_over_useful": kpad / N},
+                                "executed_over_useful": kpad / N, "traffic": traffic_for("tc_mma")},
             "blocks": nb, "outputs_per_block": T}
 
 
@@ -601,16 +615,7 @@ def main():
         roof.update(bound="hbm", achieved=byts / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
                     peak_source=pk["source"])
     roof["frac"] = roof["achieved"] / roof["peak"]
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        try:
-            tf = json.load(open(TRAFFIC_FILE))
-            ent = tf.get(dom)
-            if ent and ent.get("source_sha") == kernel_source_sha():
-                traffic = ent.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            pass
-    roof["traffic"] = traffic
+    roof["traffic"] = traffic_for(dom)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
