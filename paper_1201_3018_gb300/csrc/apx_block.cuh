@@ -87,7 +87,11 @@ __device__ __forceinline__ long long fx_sq(const FxScale& f, float x) {
 }
 // sum q^2 * 2^(-2 sh) / n, one thread, broadcast through shared memory
 __device__ __forceinline__ double fx_moment(long long sum, const FxScale& f, int n, Shared& sh) {
-    if (threadIdx.x == 0) sh.bcast[0] = __ddiv_rn(ldexp(__ll2double_rn(sum), -2 * f.sh), (double)n);
+    if (threadIdx.x == 0) {
+        const double v = ldexp(__ll2double_rn(sum), -2 * f.sh);
+        // dividing by a power of two is exact: the same bits without the FP64 divide
+        sh.bcast[0] = (n & (n - 1)) == 0 ? ldexp(v, -(31 - __clz(n))) : __ddiv_rn(v, (double)n);
+    }
     __syncthreads();
     const double v = sh.bcast[0];
     __syncthreads();

@@ -65,16 +65,14 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
     load_window_regs(p, g.start, xv);
 
     // ||s||_inf and the fixed-point second moment, from registers
-    float m = 0.f;
-    int bad = 0;
+    // one integer reduction gives the maximum and whether a NaN (bits above
+    // +inf) is present
+    int mb = 0;
 #pragma unroll
-    for (int v = 0; v < kVals; ++v) {
-        float a = fabsf(xv[v]);
-        if (a != a) bad = 1;
-        m = fmaxf(m, a);
-    }
-    m = block_reduce<float, true>(m, sh.redf);
-    bad = block_reduce<int, true>(bad, sh.redi);
+    for (int v = 0; v < kVals; ++v) mb = max(mb, __float_as_int(xv[v]) & 0x7fffffff);
+    mb = block_reduce<int, true>(mb, sh.redi);
+    const int bad = mb > 0x7f800000;
+    const float m = bad ? 0.f : __int_as_float(mb);
     const bool finite = !bad && m <= 3.402823466e38f;
     double sig2 = 0.0;
     if (finite && m > 0.f) {

@@ -132,17 +132,14 @@ __device__ T block_reduce(T v, T* red) {
 
 // ||x||_inf over n samples in shared memory; returns NaN if any sample is NaN
 // and +inf if any is infinite.
+// One integer reduction: the bit patterns of non-negative floats order as the
+// values, and every NaN pattern lies above +inf (0x7f800000).
 __device__ inline float block_maxabs(const float* x, int n, float* redf, int* redi) {
-    float m = 0.f;
-    int bad = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        float a = fabsf(x[i]);
-        if (a != a) bad = 1;
-        m = fmaxf(m, a);
-    }
-    m = block_reduce<float, true>(m, redf);
-    bad = block_reduce<int, true>(bad, redi);
-    return bad ? __int_as_float(0x7fc00000) : m;
+    (void)redf;
+    int mb = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mb = max(mb, __float_as_int(x[i]) & 0x7fffffff);
+    mb = block_reduce<int, true>(mb, redi);
+    return mb > 0x7f800000 ? __int_as_float(0x7fc00000) : __int_as_float(mb);
 }
 
 // Table 1 model (derived from Eqs. 18-19), one IEEE operation at a time:
@@ -271,10 +268,13 @@ template <int RAD, typename C, bool INV> __device__ __forceinline__ void dft_sma
     else dft2<C, INV>(v);
 }
 
-// Shared-memory slot of complex element i: one pad element per 16 makes every
-// pass below use the minimum number of shared-memory wavefronts.
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int padded_len(int m) { return m + (m >> 4) + 1; }
+// Shared-memory slot of complex element i: one pad element per 16 and one more
+// per 256.  The passes below (strides 1, 16, 256 across a warp) and the
+// spectral product (digit-reversed slots, lanes 256 elements apart) then all
+// use the minimum number of shared-memory wavefronts; with the per-16 pad
+// alone the digit-reversed access put 16 lanes on one bank.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4) + (i >> 8); }
+__host__ __device__ constexpr int padded_len(int m) { return m + (m >> 4) + (m >> 8) + 1; }
 
 // Twiddles w[r] = W_M^(r j), r < RAD, from a table of exp(-2 pi i t / ntab).
 // FP32: one table load and products (at most four deep); FP64: one load each,
@@ -425,33 +425,71 @@ template <typename C>
 __device__ __forceinline__ C load_h(const C* H, int k, bool coherent) {
     return coherent ? __ldcg(&H[k]) : __ldg(&H[k]);
 }
-// `coherent`: H was written during this kernel (read around L1).
-template <typename C>
-__device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__ tw, int twn, bool coherent) {
-    for (int k = threadIdx.x; k <= m / 2; k += blockDim.x) {
-        if (k == 0) {
-            C z0 = Z[0];
-            C X0, Xm;
-            X0.x = 2 * (z0.x + z0.y); X0.y = 0;
-            Xm.x = 2 * (z0.x - z0.y); Xm.y = 0;
-            C Y0 = cmul(X0, load_h(H, 0, coherent)), Ym = cmul(Xm, load_h(H, m, coherent));
-            C cym = cconj(Ym);
-            Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
-        } else {
-            const int pk = pad16(fft_perm<C>(k, m)), pmk = pad16(fft_perm<C>(m - k, m));
-            C a = Z[pk], b = Z[pmk];
-            C w = __ldg(&tw[k * twn]);
-            C Xk, Xmk;
-            real_post(a, b, w, Xk, Xmk);
-            C Yk = cmul(Xk, load_h(H, k, coherent));
-            C Ymk = cmul(Xmk, load_h(H, m - k, coherent));
-            C Zk, Zmk;
-            real_pre(Yk, Ymk, w, Zk, Zmk);
-            Z[pk] = Zk;
-            if (k != m - k) Z[pmk] = Zmk;
+// fft_perm for a transform whose main passes have radix R (a compile-time
+// constant: the digit arithmetic becomes shifts and masks).
+template <int R>
+__device__ __forceinline__ int fft_perm_r(int k, int m) {
+    int pos = 0, S = m;
+    while (S >= R) { S /= R; pos += (k & (R - 1)) * S; k /= R; }
+    if (S > 1) pos += k & (S - 1);   // last pass: stride 1
+    return pos;
+}
+
+// One thread's frequencies k = t, t + nt, ... in rounds of B: every load of a
+// round (both spectrum entries and the twiddle) is issued before any is used,
+// so a round costs one memory latency.
+template <typename C, int R, int B>
+__device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, const C* __restrict__ tw, int twn,
+                                                    bool coherent) {
+    const int half = m / 2, nt = blockDim.x;
+    for (int k0 = threadIdx.x; k0 <= half; k0 += B * nt) {
+        C hk[B], hmk[B], w[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int k = k0 + u * nt;
+            if (k <= half) {
+                hk[u] = load_h(H, k, coherent);
+                hmk[u] = load_h(H, m - k, coherent);
+                w[u] = __ldg(&tw[k * twn]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int k = k0 + u * nt;
+            if (k > half) break;
+            if (k == 0) {
+                C z0 = Z[0];
+                C X0, Xm;
+                X0.x = 2 * (z0.x + z0.y); X0.y = 0;
+                Xm.x = 2 * (z0.x - z0.y); Xm.y = 0;
+                C Y0 = cmul(X0, hk[u]), Ym = cmul(Xm, hmk[u]);
+                C cym = cconj(Ym);
+                Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
+            } else {
+                const int pk = pad16(fft_perm_r<R>(k, m)), pmk = pad16(fft_perm_r<R>(m - k, m));
+                C a = Z[pk], b = Z[pmk];
+                C Xk, Xmk;
+                real_post(a, b, w[u], Xk, Xmk);
+                C Yk = cmul(Xk, hk[u]);
+                C Ymk = cmul(Xmk, hmk[u]);
+                C Zk, Zmk;
+                real_pre(Yk, Ymk, w[u], Zk, Zmk);
+                Z[pk] = Zk;
+                if (k != m - k) Z[pmk] = Zmk;
+            }
         }
     }
     __syncthreads();
+}
+
+// `coherent`: H was written during this kernel (read around L1).
+template <typename C>
+__device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__ tw, int twn, bool coherent) {
+    constexpr int B = sizeof(C) == 8 ? 5 : 3;
+    const int R = fft_radix<C>(m, blockDim.x);
+    if (R == 16) spectral_multiply_r<C, 16, B>(Z, m, H, tw, twn, coherent);
+    else if (R == 8) spectral_multiply_r<C, 8, B>(Z, m, H, tw, twn, coherent);
+    else spectral_multiply_r<C, 4, B>(Z, m, H, tw, twn, coherent);
 }
 
 // Programmatic dependent launch: let the next kernel in the stream start, and
