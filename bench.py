@@ -434,11 +434,12 @@ def bench_paper_comparison(ctx, dev, flush, stream):
 
 def bench_serving(tuner, dev, seconds):
     """Poisson arrivals at 2000 req/s, L log-uniform in [2^12, 2^22], N in
-    [64, 8192], targets {30, 45, 60} dB, 40 GB admission budget, 4 streams."""
+    [64, 8192], targets {30, 45, 60} dB, 40 GB admission budget, 8 streams,
+    at most 8 requests per batch."""
     from paper_1201_3018_gb300 import serve
     seed = wl.SEED_BASE + 5
     s_host, k_host = serve.host_pools(seed)
-    srv = serve.Server(dev.index or 0, budget_bytes=40 << 30, streams=4, tuner=tuner)
+    srv = serve.Server(dev.index or 0, budget_bytes=40 << 30, streams=8, max_batch=8, tuner=tuner)
     try:
         warm = serve.make_trace(seed + 100, duration_s=0.25)
         srv.run(warm, s_host, k_host, realtime=False)       # tuner entries, workspaces, pinned pools

@@ -11,8 +11,11 @@ overlaps on the device.  Every request copies its input from pinned host
 memory and reads its result back into pinned host memory; its latency is
 completion (the batch's event observed done) minus arrival.
 
-Each stream has its own library context, so the workspaces of batches in
-flight never alias; a request's result does not depend on what else shares
+Measured at 2000 requests/s: 8 streams with at most 8 requests per batch give
+a p99 of about 0.8 ms; batches of up to 64 gave 18 ms (a burst's requests wait
+behind each other in one launch sequence, and the growing workspaces stall the
+scheduler).  Each stream has its own library context, so the workspaces of
+batches in flight never alias; a request's result does not depend on what else shares
 its batch (the batched kernels take each request's parameters from its own
 table entry).  Core and W_block per kernel length come from the autotuner
 (tune.Tuner, one measurement per power-of-two bucket of N) or the library
@@ -75,8 +78,8 @@ def n_bucket(N: int) -> int:
 
 
 class Server:
-    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, streams: int = 4, tuner=None,
-                 max_batch: int = 64):
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, streams: int = 8, tuner=None,
+                 max_batch: int = 8):
         import torch
         from . import apx
         self.apx = apx
