@@ -194,3 +194,34 @@ def method_sweep(ctx, Ns=(32, 64, 128, 256, 512, 1024, 2048, 4096, 8192), L=1 <<
                              model_ratio=table1_flops("full", "time" if core == "direct" else "freq", N)
                              / table1_flops(method, "time" if core == "direct" else "freq", N)))
     return rows
+
+
+def calibrate_snr(ctx, s, k, W_block, mode, Q=8):
+    """One-point calibration of the SNR model (Fig. 5 of the paper offsets the
+    model by one measured SNR at S_q = K_q = 8): runs the packing `mode` with
+    S_q = K_q = Q through apx_conv_fixed and the full-precision twin, and
+    returns dict(offset_db = measured - model, measured_db, model_db).  The
+    model value for the whole output combines the per-block predictions as
+    noise powers (equal-power blocks).  A caller that wants the measured SNR to
+    meet a target passes target - offset_db to apx_conv.  Optional: the
+    library never applies it by itself."""
+    import torch
+    from . import apx
+    L, N = s.numel(), k.numel()
+    r = torch.empty(L + N - 1, dtype=torch.float32, device=s.device)
+    ref = torch.empty_like(r)
+    P, _ = apx.plan_blocks(L, N, W_block, mode)
+    st = torch.empty(P * apx.STATS_DTYPE.itemsize, dtype=torch.uint8, device=s.device)
+    ctx.apx_conv_fixed(s, k, W_block, mode, Q, Q, r, None, st)
+    ctx.apx_conv_full(s, k, W_block, (mode & 0xFF) | apx.PACK_NONE, ref)
+    rc = ctx.apx_sync()
+    if rc:
+        raise apx.ApxError("apx_sync", rc)
+    stats = np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)
+    packed = np.isin(stats["mode"], (apx.BLK_SYM, apx.BLK_ASYM2, apx.BLK_ASYM3))
+    if not packed.any():
+        raise ValueError("no block was packed at S_q = K_q = %d" % Q)
+    model = -10.0 * math.log10(float(np.mean(10.0 ** (-stats["snr_pred_db"][packed] / 10.0))))
+    d = (r.double() - ref.double())
+    measured = float(10.0 * torch.log10((ref.double() ** 2).sum() / (d * d).sum()))
+    return dict(offset_db=measured - model, measured_db=measured, model_db=model)

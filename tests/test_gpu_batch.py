@@ -138,3 +138,24 @@ def test_batched_uneven_graph_vs_oracle(ctx):
             ref = O.conv_ref_at(s, k, idx)
             err = np.linalg.norm(got[idx] - ref) / max(np.linalg.norm(ref), 1e-300)
             assert err <= 1e-5, (i, err)
+
+
+def test_one_point_snr_calibration(ctx):
+    """The calibration offset brings the model to the measured SNR at the
+    calibration point, and a target corrected by it is met."""
+    from paper_1201_3018_gb300 import tune
+    s = _dev(wl.random_signal(77, 1 << 16, "laplace", 0.1))
+    k = _dev(wl.random_signal(78, 64, "uniform"))
+    mode = apx.CORE_DIRECT | apx.PACK_ASYM2
+    cal = tune.calibrate_snr(ctx, s, k, 1024, mode)
+    assert abs(cal["offset_db"]) < 6.0, cal          # the model is a close, not exact, description
+    assert abs(cal["measured_db"] - (cal["model_db"] + cal["offset_db"])) < 1e-9
+    target = 40.0
+    r = torch.empty(s.numel() + k.numel() - 1, device="cuda")
+    ref = torch.empty_like(r)
+    ctx.apx_conv(s, k, 1024, apx.CORE_DIRECT | apx.PACK_AUTO, target - cal["offset_db"], r)
+    ctx.apx_conv_full(s, k, 1024, apx.CORE_DIRECT | apx.PACK_NONE, ref)
+    assert ctx.apx_sync() == 0
+    d = r.double() - ref.double()
+    snr = float(10 * torch.log10((ref.double() ** 2).sum() / (d * d).sum()))
+    assert snr >= target - 1.0, (snr, cal)
