@@ -119,25 +119,27 @@ class ClockSampler:
 
 def traffic_for(name):
     """DRAM bytes per launch of a kernel from the committed ncu capture, or
-    None once the kernel sources have changed since it was taken."""
+    None once any source file that kernel is compiled from has changed since
+    the capture (SHA-256 over the files the entry lists)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     try:
         ent = json.load(open(TRAFFIC_FILE)).get(name)
     except (OSError, ValueError):
         return None
-    if ent and ent.get("source_sha") == kernel_source_sha():
+    if ent and ent.get("source_sha") == kernel_source_sha(ent.get("files")):
         return ent.get("dram_bytes_per_launch")
     return None
 
 
-def kernel_source_sha():
+def kernel_source_sha(files=None):
+    """SHA-256 of the named kernel sources (default: every file of csrc/)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1201_3018_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    names = sorted(files) if files else sorted(n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
+    for name in names:
+        h.update(name.encode())
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()
 
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "apx_launch.h"
+#include "apx_tc.h"
 
 using namespace apx;
 

@@ -52,45 +52,4 @@ cudaError_t launch_spec_batch(const Params& any, const BatchTab& bt, int ctas, c
 cudaError_t launch_combine_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st);
 cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st);
 
-// Tensor-core time-domain core (filterbank).  A tile is kTcM rows of P output
-// phases by kTcN = G kernels x P phases; K runs over the Toeplitz band in
-// slices of kTcK.
-constexpr int kTcM = 128;
-constexpr int kTcN = 256;
-constexpr int kTcK = 64;
-constexpr int kTcMaxStages = 8;
-constexpr int kTcMaxN = 16384;
-constexpr int kTcMaxF = 1024;
-constexpr int kTcMaxQ = 2048;              // |q| <= 2048 is exact in FP16
-constexpr long long kTcExactSum = 1LL << 24;  // FP32 holds every integer up to 2^24
-
-struct TcGeom {
-    int P;            // output phases per row (64, 128 or 256)
-    int G;            // kernels per column group, kTcN / P
-    int F;            // kernels
-    int N;            // taps per kernel
-    int ngroups;      // ceil(F / G)
-    int Kpad;         // N + P - 1 rounded up to kTcK
-    int ktiles;       // Kpad / kTcK
-    int T;            // outputs per block, kTcM * P
-    int64_t out_len;  // L + N - 1
-    int64_t ldy;      // row pitch of the outputs (elements)
-    int64_t nb;       // blocks, ceil(out_len / T)
-    int64_t seg_rows; // rows of P samples in a block's segment
-    int stages;       // shared-memory ring depth
-    int a_loads;      // P = 64: 128-row TMA boxes that make up a tile's whole A operand
-    int abuf_bytes;   // P = 64: bytes of one A buffer (a_loads x 16 KB)
-    int smem_bytes;   // dynamic shared memory of the GEMM kernel
-};
-
-bool tc_geometry(int64_t L, int F, int N, TcGeom* g);
-size_t tc_seg_bytes(const TcGeom& g);
-size_t tc_b_bytes(const TcGeom& g);
-// Block companding into FP16 segments and the kernels' Toeplitz columns.
-cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
-                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st);
-// The persistent tensor-core GEMM with the Eq. (16) epilogue.
-cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* cs_tab, const float* ck_tab,
-                          float* y, int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed);
-
 }  // namespace apx

@@ -45,7 +45,7 @@
 
 #include <cstdint>
 
-#include "apx_launch.h"
+#include "apx_tc.h"
 
 namespace apx {
 
@@ -589,7 +589,7 @@ bool tc_geometry(int64_t L, int F, int N, TcGeom* g) {
     g->nb = (g->out_len + g->T - 1) / g->T;
     g->seg_rows = ((int64_t)g->T + g->Kpad + g->P - 1) / g->P;
     g->ldy = g->out_len;
-    const int budget = kMaxSmem - 1024;  // data bytes after the 1024-byte alignment slack
+    const int budget = kTcSmemCap - 1024;  // data bytes after the 1024-byte alignment slack
     if (g->P == 64) {
         g->a_loads = (kTcM - 1 + g->ktiles + kTcABoxRows - 1) / kTcABoxRows;
         g->abuf_bytes = g->a_loads * (int)kTcABoxBytes;
@@ -630,9 +630,9 @@ cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, cons
     }
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+            e = cudaFuncSetAttribute(k_tc_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
         if (e != cudaSuccess) return e;
         attr = true;
     }
