@@ -188,71 +188,68 @@ __device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64
 
 // Eq. (2) on the block's window, written as the block's FP16 segment
 // seg[u] = s~[t0 - N + 1 + u]; entries past the window (u >= T + N - 1) are 0.
-// Each thread handles runs of kRun consecutive samples with independent loads.
+// One coalesced pass stages the window in shared memory and finds its
+// maximum (one integer reduction of the magnitude bits: NaN lies above inf);
+// the companding then reads shared memory and writes 16-byte vectors.
 constexpr int kRun = 8;
 __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, int64_t L, TcGeom g, int Sq,
                                                   __half* __restrict__ seg, float* __restrict__ cs_tab,
                                                   float* __restrict__ cs_out, unsigned* __restrict__ status) {
-    __shared__ float red[8];
-    __shared__ int nfs;
+    extern __shared__ __align__(16) float win[];  // nwin window samples, padded to a multiple of kRun
+    __shared__ int red[8];
     const int64_t b = blockIdx.x;
-    const int64_t lo = b * g.T - g.N + 1, nwin = (int64_t)g.T + g.N - 1;
+    const int64_t lo = b * g.T - g.N + 1;
+    const int nwin = g.T + g.N - 1;
     const int64_t nseg = g.seg_rows * g.P;
-    if (threadIdx.x == 0) nfs = 0;
-    float m = 0.f;
-    bool nf = false;
-    for (int64_t u0 = (int64_t)threadIdx.x * kRun; u0 < nwin; u0 += (int64_t)blockDim.x * kRun) {
+    int mb = 0;
+    for (int u0 = threadIdx.x; u0 < nwin; u0 += kRun * blockDim.x) {
         float v[kRun];
 #pragma unroll
         for (int i = 0; i < kRun; ++i) {
-            const int64_t gi = lo + u0 + i;
-            v[i] = (u0 + i < nwin && gi >= 0 && gi < L) ? __ldg(s + gi) : 0.f;
+            const int u = u0 + i * blockDim.x;
+            const int64_t gi = lo + u;
+            v[i] = (u < nwin && gi >= 0 && gi < L) ? __ldg(s + gi) : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < kRun; ++i) {
-            const float a = fabsf(v[i]);
-            if (!(a <= 3.402823466e38f)) nf = true;
-            else m = fmaxf(m, a);
+            const int u = u0 + i * blockDim.x;
+            if (u < nwin) win[u] = v[i];
+            mb = max(mb, __float_as_int(v[i]) & 0x7fffffff);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        nf |= __shfl_xor_sync(0xffffffffu, (int)nf, o) != 0;
-    }
+    for (int u = nwin + threadIdx.x; u < (nwin + kRun - 1) / kRun * kRun; u += blockDim.x) win[u] = 0.f;
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5] = m;
-        if (nf) nfs = 1;
-    }
-    __syncthreads();
-    float M = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, red[w]);
-    const bool bad = nfs != 0;
+    int M = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = max(M, red[w]);
+    const bool bad = M > 0x7f800000;  // a NaN
+    const float Mf = __int_as_float(M);
     float c = 0.f;
-    if (bad) c = __int_as_float(0x7fc00000);
-    else if (M > 0.f) c = __fdiv_rn((float)Sq, M);
-    const bool live = !bad && M > 0.f;
+    if (bad || Mf > 3.402823466e38f) c = __int_as_float(0x7fc00000);
+    else if (Mf > 0.f) c = __fdiv_rn((float)Sq, Mf);
+    const bool live = Mf > 0.f && Mf <= 3.402823466e38f && !bad;
     __half* out = seg + b * nseg;
     for (int64_t u0 = (int64_t)threadIdx.x * kRun; u0 < nseg; u0 += (int64_t)blockDim.x * kRun) {
-        float v[kRun];
-#pragma unroll
-        for (int i = 0; i < kRun; ++i) {
-            const int64_t gi = lo + u0 + i;
-            v[i] = (live && u0 + i < nwin && gi >= 0 && gi < L) ? __ldg(s + gi) : 0.f;
-        }
         __align__(16) __half2 h[kRun / 2];
+        if (live && u0 < nwin) {
+            const float4 p = *reinterpret_cast<const float4*>(win + u0);
+            const float4 q = *reinterpret_cast<const float4*>(win + u0 + 4);
+            const float v[kRun] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int i = 0; i < kRun; i += 2)
-            h[i / 2] = __halves2half2(__float2half_rn(rintf(__fmul_rn(c, v[i]))),
-                                      __float2half_rn(rintf(__fmul_rn(c, v[i + 1]))));
-        if (!live) {
+            for (int i = 0; i < kRun; i += 2) {
+                const float a0 = u0 + i < nwin ? rintf(__fmul_rn(c, v[i])) : 0.f;
+                const float a1 = u0 + i + 1 < nwin ? rintf(__fmul_rn(c, v[i + 1])) : 0.f;
+                h[i / 2] = __halves2half2(__float2half_rn(a0), __float2half_rn(a1));
+            }
+        } else {
 #pragma unroll
             for (int i = 0; i < kRun / 2; ++i) h[i] = __float2half2_rn(0.f);
         }
         *reinterpret_cast<uint4*>(out + u0) = *reinterpret_cast<const uint4*>(h);  // nseg % 8 == 0
     }
     if (threadIdx.x == 0) {
-        if (bad) atomicOr(status, 1u);
+        if (bad || Mf > 3.402823466e38f) atomicOr(status, 1u);
         cs_tab[b] = c;
         if (cs_out) cs_out[b] = c;
     }
@@ -301,6 +298,74 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
             row[jj] = __halves2half2(kq[n0 + 64], kq[n1 + 64]);
         }
     }
+}
+
+// Epilogue of one tile for one warp (TMEM lane quarter lq, chunk parity
+// `half`): read the 128 x 256 FP32 accumulator rows of this quarter in 32-column
+// chunks, scale by (c_s c_k)^-1 (Eq. 16), stage each 32 x 32 chunk in the warp's
+// 4 KB buffer (16-byte slot i of row r at r * 128 + ((i ^ (r & 7)) * 16):
+// conflict-free both ways) and store four whole 128-byte rows per instruction.
+__device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int grp, uint32_t acc0, uint32_t stg,
+                                              int lane, int lq, int half, const float* __restrict__ cs_tab,
+                                              const float* __restrict__ ck_tab, float* __restrict__ y,
+                                              int32_t* __restrict__ yq) {
+    const int row = lq * 32 + lane;
+    const int rr = lane >> 3, ii = lane & 7;
+    const uint32_t acc = acc0 + ((uint32_t)(lq * 32) << 16);
+            const float cs = cs_tab[blk];
+            for (int fl = 0; fl < g.G; ++fl) {
+                const int f = grp * g.G + fl;
+                if (f >= g.F) break;
+                // (c_s c_k)^-1 once per warp (FP64 is a small fraction of the FP32 rate)
+                float inv = 0.f;
+                if (lane == 0) {
+                    const float ck = ck_tab[f];
+                    if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
+                }
+                inv = __shfl_sync(0xffffffffu, inv, 0);
+                float* yf = y + (int64_t)f * g.ldy;
+                int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
+                for (int c = 32 * half; c < g.P; c += 32 * (kTcEpiWarps / 4)) {
+                    uint32_t r[32];
+                    tmem_ld32_nowait(acc + (uint32_t)(fl * g.P + c), r);
+                    tmem_wait_ld();
+                    // scale (Eq. 16) and stage this lane's row
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
+                        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                         stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
+                                     "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                                     : "memory");
+                    }
+                    if (qf) {  // integer outputs (a test aid): straight from the row
+                        const int64_t t0 = blk * (int64_t)g.T + (int64_t)row * g.P + c;
+                        for (int i = 0; i < 32 && t0 + i < g.out_len; ++i)
+                            qf[t0 + i] = __float2int_rn(__uint_as_float(r[i]));
+                    }
+                    __syncwarp();
+                    // four whole rows (4 x 128 contiguous bytes) per store instruction
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int srow = 4 * j + rr;
+                        float4 v;
+                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                                     : "r"(stg + (uint32_t)srow * 128u + (uint32_t)((ii ^ (srow & 7)) * 16))
+                                     : "memory");
+                        const int64_t t = blk * (int64_t)g.T + (int64_t)(lq * 32 + srow) * g.P + c + 4 * ii;
+                        if (t + 4 <= g.out_len) {
+                            __stcs(reinterpret_cast<float4*>(yf + t), v);
+                        } else {
+                            const float w[4] = {v.x, v.y, v.z, v.w};
+                            for (int e = 0; e < 4 && t + e < g.out_len; ++e) yf[t + e] = w[e];
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
 }
 
 // Persistent: CTA c takes tiles u = c, c + gridDim.x, ...; tile u is block
@@ -439,11 +504,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (!ok) break;
             }
         }
-    } else {  // epilogue: warps 2..9, TMEM lane quarter warp % 4; the two warps of a
-              // quarter take alternate 32-column chunks
+    } else {  // epilogue: warps 2.., TMEM lane quarter warp % 4; with 8 epilogue warps
+              // the two warps of a quarter take alternate 32-column chunks
         const int lq = warp & 3;
         const int half = (warp - 2) >> 2;
-        const int row = lq * 32 + lane;
         int local = 0;
         for (int64_t u = blockIdx.x; u < nsets; u += gridDim.x, ++local) {
             const int a = local & 1;
@@ -456,65 +520,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             const int64_t blk = u / g.ngroups;
             const int grp = (int)(u % g.ngroups);
-            const float cs = cs_tab[blk];
-            const uint32_t acc = tmem + (uint32_t)(a * kTcTmemCols) + ((uint32_t)(lq * 32) << 16);
-            // this warp's 4 KB staging buffer: 32 rows x 32 floats, 16-byte slot i of
-            // row r at r * 128 + ((i ^ (r & 7)) * 16) (conflict-free both ways)
-            const uint32_t stg = base + (uint32_t)(warp - 2) * 4096u;
-            const int rr = lane >> 3, ii = lane & 7;
-            for (int fl = 0; fl < g.G; ++fl) {
-                const int f = grp * g.G + fl;
-                if (f >= g.F) break;
-                // (c_s c_k)^-1 once per warp (FP64 is a small fraction of the FP32 rate)
-                float inv = 0.f;
-                if (lane == 0) {
-                    const float ck = ck_tab[f];
-                    if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
-                }
-                inv = __shfl_sync(0xffffffffu, inv, 0);
-                float* yf = y + (int64_t)f * g.ldy;
-                int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
-                for (int c = 32 * half; c < g.P; c += 32 * (kTcEpiWarps / 4)) {
-                    uint32_t r[32];
-                    tmem_ld32_nowait(acc + (uint32_t)(fl * g.P + c), r);
-                    tmem_wait_ld();
-                    // scale (Eq. 16) and stage this lane's row
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float v[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
-                        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                         stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
-                                     "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-                                     : "memory");
-                    }
-                    if (qf) {  // integer outputs (a test aid): straight from the row
-                        const int64_t t0 = blk * (int64_t)g.T + (int64_t)row * g.P + c;
-                        for (int i = 0; i < 32 && t0 + i < g.out_len; ++i)
-                            qf[t0 + i] = __float2int_rn(__uint_as_float(r[i]));
-                    }
-                    __syncwarp();
-                    // four whole rows (4 x 128 contiguous bytes) per store instruction
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int srow = 4 * j + rr;
-                        float4 v;
-                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                                     : "r"(stg + (uint32_t)srow * 128u + (uint32_t)((ii ^ (srow & 7)) * 16))
-                                     : "memory");
-                        const int64_t t = blk * (int64_t)g.T + (int64_t)(lq * 32 + srow) * g.P + c + 4 * ii;
-                        if (t + 4 <= g.out_len) {
-                            __stcs(reinterpret_cast<float4*>(yf + t), v);
-                        } else {
-                            const float w[4] = {v.x, v.y, v.z, v.w};
-                            for (int e = 0; e < 4 && t + e < g.out_len; ++e) yf[t + e] = w[e];
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
+            epilogue_tile(g, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * 4096u, lane,
+                          lq, half, cs_tab, ck_tab, y, yq);
             // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
             tc_fence_before();
             __syncwarp();
@@ -612,7 +619,14 @@ size_t tc_b_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)g.ngroups *
 
 cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
                            void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st) {
-    k_tc_quant<<<(unsigned)g.nb, 256, 0, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
+    const size_t wsm = sizeof(float) * (size_t)((g.T + g.N - 1 + kRun - 1) / kRun * kRun);
+    static size_t wsm_set = 48 * 1024;
+    if (wsm > wsm_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_quant, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
+        if (e != cudaSuccess) return e;
+        wsm_set = kTcSmemCap;
+    }
+    k_tc_quant<<<(unsigned)g.nb, 256, wsm, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
     k_tc_kern<<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(__half) * (size_t)(g.N + 128),
                 st>>>(kb, g, Kq, (__half*)bt, ck_tab, status);
     return cudaGetLastError();
