@@ -453,6 +453,7 @@ def bench_serving(tuner, dev, seconds):
                     b *= 2
         trace = serve.make_trace(seed, duration_s=seconds)
         srv.peak_in_flight = srv.batches = srv.max_overlap = 0
+        srv.batch_sizes = []
         done = srv.run(trace, s_host, k_host, realtime=True)
         p50, p99 = serve.latency_ms(done)
         span = max(q.done for q in done) - min(q.arrival for q in done)
@@ -461,6 +462,10 @@ def bench_serving(tuner, dev, seconds):
                             "N log-uniform [64,8192], targets {30,45,60} dB, 40 GB budget" % seconds,
                 "requests": len(done), "p50_ms": p50, "p99_ms": p99, "value": outs / span / 1e9, "unit": UNIT,
                 "batches": srv.batches, "max_batches_in_flight": srv.max_overlap,
+                "batch_size_histogram": np.bincount(srv.batch_sizes).tolist(),
+                "tuned": {"N<=%d %s %gdB" % (b, "xcorr" if op else "conv", t):
+                          "%s/%d" % (lambda c: (c["core"], c["W_block"]))(tuner.choose(b, op, 0, t))
+                          for op in (0, 1) for t in (30.0, 45.0, 60.0) for b in (64, 512, 4096, 8192)},
                 "peak_in_flight_bytes": srv.peak_in_flight,
                 "latency": "arrival to result in pinned host memory (H2D, kernels, D2H included)"}
     finally:

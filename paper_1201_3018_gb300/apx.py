@@ -27,6 +27,10 @@ PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x
 FULL_FP64 = 0x1000
 BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
 
+# apx_request as a numpy record (64 bytes, natural C alignment)
+REQUEST_DTYPE = np.dtype({"names": ["s_in", "L", "k", "N", "r_out", "W_block", "mode", "snr_target_db", "S_q", "K_q"],
+                          "formats": ["<u8", "<i8", "<u8", "<i4", "<u8", "<i4", "<u4", "<f8", "<i4", "<i4"],
+                          "offsets": [0, 8, 16, 24, 32, 40, 44, 48, 56, 60], "itemsize": 64})
 STATS_DTYPE = np.dtype([("mode", "<i4"), ("Sq", "<i4"), ("Kq", "<i4"), ("b", "<i4"), ("cs", "<f4"),
                         ("maxabs", "<f4"), ("sigma2", "<f8"), ("snr_pred_db", "<f8"), ("fft_err", "<f8")])
 assert STATS_DTYPE.itemsize == 48
@@ -61,6 +65,7 @@ SIGNATURES = {
     "apx_graph_launch_count": (_i64, [_vp]),
     "apx_graph_destroy": (None, [_vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
+    "apx_conv_batch_host": (C.c_int, [_vp, _vp, _i32, _vp]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
@@ -261,6 +266,12 @@ class Context:
 
     def apx_conv_batch(self, reqs, stream=None):
         return _check("apx_conv_batch", lib().apx_conv_batch(self._h, reqs, len(reqs), _stream(stream)))
+
+    def apx_conv_batch_host(self, reqs, stream=None):
+        """reqs: a numpy array of REQUEST_DTYPE (or a ctypes array of Request)
+        whose pointers are host addresses."""
+        ptr = reqs.ctypes.data if isinstance(reqs, np.ndarray) else C.cast(reqs, C.c_void_p).value
+        return _check("apx_conv_batch_host", lib().apx_conv_batch_host(self._h, ptr, len(reqs), _stream(stream)))
 
     def graph(self, reqs, stream=None):
         """Capture the batch once; returns a Graph (launch() replays it)."""

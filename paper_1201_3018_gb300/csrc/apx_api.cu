@@ -35,6 +35,7 @@ struct apx_ctx {
     DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
     DevBuf tc_seg, tc_b, tc_cs, tc_ck;  // filterbank: FP16 block segments, Toeplitz B, c_s per block, c_k per kernel
+    DevBuf bhost;                       // batched calls from host buffers: device copies of inputs and outputs
     void* hstage = nullptr;             // pinned staging for batch parameters
     size_t hstage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
@@ -673,7 +674,7 @@ void apx_destroy(apx_ctx* c) {
         cudaDeviceSynchronize();
         DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
                          &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab,
-                         &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_ck};
+                         &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_ck, &c->bhost};
         for (DevBuf* b : all) release(c, *b);
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -806,14 +807,9 @@ struct apx_graph {
     int64_t launches = 0;
 };
 
-extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
-    if (!ctx) return APX_ERR_ARG;
-    BatchPlan bp;
-    int rc = plan_batch(reqs, n, &bp);
-    if (rc) return rc;
-    DeviceGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+// Launch a planned batch on the context's batch workspace.
+static int batch_run(apx_ctx* ctx, BatchPlan& bp, int32_t n, cudaStream_t st) {
+    int rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
     if (!rc && bp.max_wb > 0) rc = ensure_twiddles(ctx, bp.max_wb, st);
     if (!rc) rc = ensure(ctx, ctx->barena, bp.arena_bytes);
     if (!rc) rc = ensure(ctx, ctx->bparams, sizeof(Params) * (size_t)n);
@@ -828,6 +824,62 @@ extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, 
     cudaError_t e = cudaMemsetAsync(ctx->barena.p, 0, bp.flags_bytes, st);  // claim/ready words
     if (e == cudaSuccess) e = launch_batch(bp, (const Params*)ctx->bparams.p, (const int*)ctx->btab.p, st);
     for (const auto& G : bp.groups) ctx->launches += G.fft ? 3 : 1;
+    return cuda_status(e);
+}
+
+extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
+    if (!ctx) return APX_ERR_ARG;
+    BatchPlan bp;
+    int rc = plan_batch(reqs, n, &bp);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    return batch_run(ctx, bp, n, (cudaStream_t)stream);
+}
+
+extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
+    if (!ctx || n < 0 || (n > 0 && !reqs)) return APX_ERR_ARG;
+    // device copies of every request's signal, kernel and output, 256-byte aligned
+    std::vector<size_t> off(3 * (size_t)n);
+    size_t total = 0;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    for (int32_t i = 0; i < n; ++i) {
+        const apx_request& q = reqs[i];
+        if (!q.s_in || !q.k || !q.r_out || q.L < 1 || q.N < 1) return APX_ERR_ARG;
+        off[3 * i] = total;
+        total += al(sizeof(float) * (size_t)q.L);
+        off[3 * i + 1] = total;
+        total += al(sizeof(float) * (size_t)q.N);
+        off[3 * i + 2] = total;
+        total += al(sizeof(float) * (size_t)(q.L + q.N - 1));
+    }
+    DeviceGuard dg(ctx->device);
+    int rc = ensure(ctx, ctx->bhost, total > 0 ? total : 256);
+    if (rc) return rc;
+    unsigned char* base = (unsigned char*)ctx->bhost.p;
+    std::vector<apx_request> dq(reqs, reqs + n);
+    for (int32_t i = 0; i < n; ++i) {
+        dq[i].s_in = (const float*)(base + off[3 * i]);
+        dq[i].k = (const float*)(base + off[3 * i + 1]);
+        dq[i].r_out = (float*)(base + off[3 * i + 2]);
+    }
+    BatchPlan bp;
+    rc = plan_batch(dq.data(), n, &bp);  // reject before anything is enqueued
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync((void*)dq[i].s_in, reqs[i].s_in, sizeof(float) * (size_t)reqs[i].L,
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void*)dq[i].k, reqs[i].k, sizeof(float) * (size_t)reqs[i].N, cudaMemcpyHostToDevice,
+                                st);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = batch_run(ctx, bp, n, st);
+    if (rc) return rc;
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(reqs[i].r_out, dq[i].r_out, sizeof(float) * (size_t)(reqs[i].L + reqs[i].N - 1),
+                            cudaMemcpyDeviceToHost, st);
     return cuda_status(e);
 }
 

@@ -69,7 +69,7 @@ def candidates(N: int, max_wb: int = 16384):
 class Tuner:
     """Measured choice of (core, W_block) per kernel length."""
 
-    def __init__(self, ctx, cache_path: str | None = None, L: int = 1 << 18, top: int = 8, reps: int = 5):
+    def __init__(self, ctx, cache_path: str | None = None, L: int = 1 << 18, top: int = 8, reps: int = 9):
         self.ctx = ctx
         self.cache_path = cache_path
         self.L = L
@@ -89,7 +89,8 @@ class Tuner:
         from . import apx
         stream = torch.cuda.current_stream()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(self.reps)]
-        self.ctx.apx_conv(s, k, Wb, mode, target, r, stream=stream)  # warm-up (workspace, twiddles)
+        for _ in range(2):  # warm-up (workspace, twiddles, caches)
+            self.ctx.apx_conv(s, k, Wb, mode, target, r, stream=stream)
         for a, b in ev:
             a.record(stream)
             if (mode & 0xF00) == apx.PACK_NONE:

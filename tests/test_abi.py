@@ -100,3 +100,10 @@ def test_header_constants_match_binding():
             checked += 1
     assert checked >= 25, checked
     assert int(defs["NPHASES"]) == len(apx.PHASES)
+
+
+def test_request_record_matches_struct():
+    from paper_1201_3018_gb300 import apx
+    for name, _ in apx.Request._fields_:
+        assert apx.REQUEST_DTYPE.fields[name][1] == getattr(apx.Request, name).offset, name
+    assert apx.REQUEST_DTYPE.itemsize == C.sizeof(apx.Request) == 64

@@ -159,3 +159,24 @@ def test_one_point_snr_calibration(ctx):
     d = r.double() - ref.double()
     snr = float(10 * torch.log10((ref.double() ** 2).sum() / (d * d).sum()))
     assert snr >= target - 1.0, (snr, cal)
+
+
+def test_batch_from_host_buffers_equals_device_batch(ctx):
+    items = _mixed_requests(19, 16)
+    reqs = ctx.make_requests(items)
+    ctx.apx_conv_batch(reqs)
+    ctx.apx_sync()
+    host = []
+    recs = np.zeros(len(items), dtype=apx.REQUEST_DTYPE)
+    for j, it in enumerate(items):
+        s = it["s"].cpu().pin_memory()
+        k = it["k"].cpu().pin_memory()
+        r = torch.full((it["r"].numel(),), float("nan")).pin_memory()
+        host.append((s, k, r))
+        recs[j] = (s.data_ptr(), s.numel(), k.data_ptr(), k.numel(), r.data_ptr(), it["W_block"], it["mode"],
+                   it["snr_db"], 0, 0)
+    ctx.apx_conv_batch_host(recs)
+    torch.cuda.synchronize()
+    assert ctx.apx_sync() == 0
+    for it, (_, _, r) in zip(items, host):
+        assert torch.equal(r, it["r"].cpu())
