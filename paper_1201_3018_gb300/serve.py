@@ -81,7 +81,7 @@ def n_bucket(N: int) -> int:
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, streams: int = 8, tuner=None,
-                 max_batch: int = 8):
+                 max_batch: int = 8, pinned_bytes: int = 32 << 20):
         import torch
         from . import apx
         self.apx = apx
@@ -90,6 +90,9 @@ class Server:
         self.budget = budget_bytes
         self.ctxs = [apx.Context(device) for _ in range(streams)]
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(streams)]
+        # one pinned result buffer per stream, allocated once (a first-time pinned
+        # allocation of tens of MB takes milliseconds and would land in the latencies)
+        self.pinned = [torch.empty(pinned_bytes // 4, dtype=torch.float32, pin_memory=True) for _ in range(streams)]
         self.busy = [None] * streams   # (event, requests, bytes, device buffers, request table)
         self.tuner = tuner
         self.max_batch = max_batch
@@ -117,7 +120,9 @@ class Server:
         torch, apx = self.torch, self.apx
         st = self.streams[si]
         lens = [q.L + q.N - 1 for q in batch]
-        out = torch.empty(sum(lens), dtype=torch.float32, pin_memory=True)
+        out = self.pinned[si]
+        if sum(lens) > out.numel():  # a request larger than the stream's buffer (batched alone)
+            out = torch.empty(sum(lens), dtype=torch.float32, pin_memory=True)
         reqs = np.zeros(len(batch), dtype=apx.REQUEST_DTYPE)
         sb, kb, ob = s_host.data_ptr(), k_host.data_ptr(), out.data_ptr()
         krow = 4 * k_host.stride(0)
@@ -169,6 +174,12 @@ class Server:
             free = [i for i, b in enumerate(self.busy) if b is None]
             if waiting and free:
                 n = admit((device_bytes(q) for q in waiting), self.in_flight, self.budget, self.max_batch)
+                # and whose results fit the stream's pinned buffer (at least one request)
+                cap, used, m = self.pinned[free[0]].numel(), 0, 0
+                while m < n and (m == 0 or used + waiting[m].L + waiting[m].N - 1 <= cap):
+                    used += waiting[m].L + waiting[m].N - 1
+                    m += 1
+                n = m
                 if n:
                     batch = [waiting.popleft() for _ in range(n)]
                     self._launch(free[0], batch, s_host, k_host)
