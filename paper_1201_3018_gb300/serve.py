@@ -145,21 +145,26 @@ class Server:
         self.batch_sizes.append(len(batch))
         self.max_overlap = max(self.max_overlap, sum(b is not None for b in self.busy))
 
-    def _poll(self):
+    def _poll(self, on_done=None):
         done = []
         for si, b in enumerate(self.busy):
             if b is not None and b[0].query():
                 now = time.perf_counter()
                 for q in b[1]:
                     q.done = now
+                    if on_done is not None:
+                        on_done(q)  # q.out is valid until the stream's next batch
                 self.in_flight -= b[2]
                 done.extend(b[1])
                 self.busy[si] = None
         return done
 
-    def run(self, trace, s_host, k_host, realtime: bool = True):
+    def run(self, trace, s_host, k_host, realtime: bool = True, on_done=None):
         """Serve `trace` (Requests sorted by arrival time t).  With realtime
-        False every request arrives at once.  Returns the completed requests."""
+        False every request arrives at once.  Returns the completed requests.
+        A request's result q.out is a view of its stream's pinned buffer, valid
+        until that stream's next batch: `on_done(q)` runs at completion, before
+        the buffer is reused, for a consumer that keeps results."""
         pending = collections.deque(trace)
         waiting = collections.deque()
         finished = []
@@ -170,7 +175,7 @@ class Server:
                 q = pending.popleft()
                 q.arrival = t0 + q.t if realtime else now
                 waiting.append(q)
-            finished.extend(self._poll())
+            finished.extend(self._poll(on_done))
             free = [i for i, b in enumerate(self.busy) if b is None]
             if waiting and free:
                 n = admit((device_bytes(q) for q in waiting), self.in_flight, self.budget, self.max_batch)

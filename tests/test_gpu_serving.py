@@ -30,7 +30,8 @@ def test_serving_same_alone_and_in_mix(budget_mb, streams):
     budget = budget_mb << 20
     srv = serve.Server(0, budget_bytes=budget, streams=streams, max_batch=16)
     try:
-        done = srv.run(trace, s_host, k_host, realtime=True)
+        kept = {}
+        done = srv.run(trace, s_host, k_host, realtime=True, on_done=lambda q: kept.__setitem__(q.rid, q.out.clone()))
     finally:
         srv.close()
     assert sorted(q.rid for q in done) == list(range(len(trace)))
@@ -41,9 +42,10 @@ def test_serving_same_alone_and_in_mix(budget_mb, streams):
     assert 0 < p50 <= p99
     ctx = apx.Context(0)
     try:
+        assert sorted(kept) == list(range(len(trace)))
         for q in done:
             ref = _alone(ctx, q, s_host, k_host)
-            assert torch.isfinite(q.out).all()
-            assert torch.equal(q.out, ref), "request %d differs from its run alone" % q.rid
+            assert torch.isfinite(kept[q.rid]).all()
+            assert torch.equal(kept[q.rid], ref), "request %d differs from its run alone" % q.rid
     finally:
         ctx.close()
