@@ -231,10 +231,21 @@ def cpu_baseline(case, mode_bits):
     """The oracle as it stands on the host cores, on a bounded sample of the
     workload: the leading part of the signal, grown until one run takes about
     2.5 s or covers the whole signal, then repeated until about 5 s of wall
-    time (so 10-30 s of CPU work on a many-core host)."""
+    time (so 10-30 s of CPU work on a many-core host).  Also one thread on a
+    smaller sample, and the filterbank oracle on the first 2^18 samples."""
     import oracle as O
     cores = os.cpu_count() or 1
     mode = O.OP_XCORR | O.CORE_FFT | O.PACK_AUTO
+
+    def timed(Ls, threads, budget):
+        runs, total = 0, 0.0
+        while total < budget or runs == 0:
+            t0 = time.perf_counter()
+            O.apx_conv(case.s[:Ls], case.k, case.Wblock, mode, snr_db=TARGET_DB, nthreads=threads, want_int=False)
+            total += time.perf_counter() - t0
+            runs += 1
+        return runs, total
+
     Ls = 1 << 15
     while True:
         t0 = time.perf_counter()
@@ -243,16 +254,23 @@ def cpu_baseline(case, mode_bits):
         if dt > 2.5 or Ls >= len(case.s):
             break
         Ls = min(len(case.s), Ls * 2 if dt < 1.2 else Ls + Ls // 2)
-    runs, total = 1, dt
-    while total < 5.0:
-        t0 = time.perf_counter()
-        O.apx_conv(case.s[:Ls], case.k, case.Wblock, mode, snr_db=TARGET_DB, nthreads=cores, want_int=False)
-        total += time.perf_counter() - t0
-        runs += 1
+    runs, total = timed(Ls, cores, 5.0)
     out = Ls + len(case.k) - 1
-    return {"value": out * runs / total / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d samples of the signal (%d outputs), same template, W_block and target; "
-                      "%d runs, %.1f s wall on %d threads" % (Ls, out, runs, total, cores)}
+    res = {"value": out * runs / total / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "first %d samples of the signal (%d outputs), same template, W_block and target; "
+                     "%d runs, %.1f s wall on %d threads" % (Ls, out, runs, total, cores)}
+    L1 = 1 << 16
+    runs1, total1 = timed(L1, 1, 2.0)
+    res["single_thread"] = {"value": (L1 + len(case.k) - 1) * runs1 / total1 / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": "first %d samples, %d runs" % (L1, runs1)}
+    s_fb, k_fb = wl.filterbank()
+    Lf = 1 << 18
+    t0 = time.perf_counter()
+    O.filterbank(s_fb[:Lf], k_fb, 8192, 127, 127, nthreads=cores)
+    tf = time.perf_counter() - t0
+    res["filterbank"] = {"value": k_fb.shape[0] * (Lf + k_fb.shape[1] - 1) / tf / 1e9, "unit": UNIT, "cores": cores,
+                         "sample": "first %d samples through the 32-kernel bank, one run (%.1f s)" % (Lf, tf)}
+    return res
 
 
 # ---------------------------------------------------------------------------- batched and serving
@@ -394,6 +412,24 @@ def bench_paper_comparison(ctx, dev, flush, stream):
     modes = np.bincount(np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)["mode"], minlength=6)
     res["block_modes_45db"] = {"full": int(modes[0]), "sym": int(modes[1]), "asym2": int(modes[2]),
                                "asym3": int(modes[3])}
+    # SNR of the packed result against the FP32 full-precision twin: global and per block
+    ref = torch.empty(n_out, device=dev)
+    ctx.apx_conv_full(s, k, case.Wblock, apx.CORE_DIRECT | apx.PACK_NONE, ref, stream=stream)
+    ctx.apx_sync(stream)
+    rr, dd = ref.double(), (rbuf[0].double() - ref.double())
+    Wb, Nodd = case.Wblock, len(case.k) | 1
+    W = Wb - Nodd - 1
+    per = []
+    for w in range(P):
+        lo, hi = (0, W + Nodd - 1) if w == 0 else (w * W - 2 + Nodd + 1, w * W - 2 + Wb)
+        lo, hi = max(lo, 0), min(hi, n_out)
+        if hi > lo:
+            num, den = float((rr[lo:hi] ** 2).sum()), float((dd[lo:hi] ** 2).sum())
+            if den > 0:
+                per.append(10 * math.log10(num / den))
+    res["snr_vs_full_db"] = float(10 * torch.log10((rr ** 2).sum() / (dd * dd).sum()))
+    res["snr_per_block_db"] = {"min": float(min(per)), "mean": float(np.mean(per)), "blocks": len(per),
+                               "at_or_above_target": int(sum(x >= 45.0 for x in per))}
     res["speedup_packed_vs_full_fp64"] = res["full_fp64"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
     res["speedup_packed_vs_full_fp32"] = res["full_fp32"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
     res["copies"] = R
