@@ -47,6 +47,8 @@ extern "C" {
 #define APX_ERR_BUDGET     (-6)  /* request needs more workspace than the context's budget */
 #define APX_ERR_CUDA       (-7)  /* a CUDA runtime call failed                  */
 #define APX_ERR_TIMEOUT    (-8)  /* a bounded device wait gave up               */
+#define APX_ERR_CHECK      (-9)  /* a device bounds check failed (builds with
+                                    APX_CHECKED only; the access was skipped)  */
 
 /* ---- mode word: op | core | pack ------------------------------------- */
 #define APX_OP_CONV      0x000u  /* Eq. (1)                                   */
@@ -141,8 +143,9 @@ int apx_conv_host(apx_ctx* ctx, const float* s_in_host, int64_t L, const float* 
                   float* r_out_host, void* stream);
 
 /* Wait for `stream` and return the data-dependent status of the calls issued
- * since the previous apx_sync (APX_OK, APX_ERR_NONFINITE, or APX_ERR_TIMEOUT when
- * a bounded device-side wait gave up), then clear it. */
+ * since the previous apx_sync (APX_OK, APX_ERR_NONFINITE, APX_ERR_TIMEOUT when
+ * a bounded device-side wait gave up, or APX_ERR_CHECK when a bounds check of
+ * a checked build failed), then clear it. */
 int apx_sync(apx_ctx* ctx, void* stream);
 
 /* Number of CUDA kernel launches this context has issued since creation. */
@@ -162,6 +165,15 @@ int64_t apx_launch_count(const apx_ctx* ctx);
 #define APX_NPHASES       5
 int apx_profile(apx_ctx* ctx, int enable);
 int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
+
+/* Test hook for the failure path (the paper has no counterpart).  The next
+ * FFT-core call of this context finds every packed kernel spectrum claimed by
+ * a builder that never publishes it, so each block that selects a packing
+ * waits in its bounded spin, gives up after about one second of SM clock,
+ * writes NaN for its outputs and sets the timeout bit: apx_sync then returns
+ * APX_ERR_TIMEOUT, and the context stays usable for the next call.  Nothing
+ * faults or hangs.  Errors: APX_ERR_ARG. */
+int apx_test_stall_next(apx_ctx* ctx);
 
 /* Static string naming a status code. */
 const char* apx_strerror(int status);

@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 APX_OK, APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE, APX_ERR_NONFINITE = 0, -1, -2, -3, -4
-APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA, APX_ERR_TIMEOUT = -5, -6, -7, -8
+APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA, APX_ERR_TIMEOUT, APX_ERR_CHECK = -5, -6, -7, -8, -9
 OP_CONV, OP_XCORR = 0x000, 0x001
 CORE_DIRECT, CORE_FFT, CORE_AUTO = 0x000, 0x010, 0x020
 PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
@@ -66,6 +66,7 @@ SIGNATURES = {
     "apx_graph_destroy": (None, [_vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "apx_conv_batch_host": (C.c_int, [_vp, _vp, _i32, _vp]),
+    "apx_test_stall_next": (C.c_int, [_vp]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
@@ -89,9 +90,12 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError("libapx.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
-            L = C.CDLL(LIB_PATH)
+            # APX_LIB selects another build of the same library (the bounds-checked
+            # libapx_checked.so in the tests)
+            path = os.environ.get("APX_LIB") or LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError("libapx.so is not built (%s); run __graft_entry__.build()" % path)
+            L = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)
                 fn.restype = res
@@ -266,6 +270,10 @@ class Context:
 
     def apx_conv_batch(self, reqs, stream=None):
         return _check("apx_conv_batch", lib().apx_conv_batch(self._h, reqs, len(reqs), _stream(stream)))
+
+    def test_stall_next(self):
+        """Failure-path test hook (apx_test_stall_next)."""
+        return _check("apx_test_stall_next", lib().apx_test_stall_next(self._h))
 
     def apx_conv_batch_host(self, reqs, stream=None):
         """reqs: a numpy array of REQUEST_DTYPE (or a ctypes array of Request)

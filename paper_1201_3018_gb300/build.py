@@ -42,15 +42,24 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+CHECKED_LIB = os.path.join(PKG, "libapx_checked.so")
+
+
+def build(verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Build libapx.so; with checked=True build libapx_checked.so instead, with
+    -DAPX_CHECKED (device-side bounds checks that report APX_ERR_CHECK)."""
+    build_dir = BUILD + ("_checked" if checked else "")
+    lib = CHECKED_LIB if checked else LIB
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DAPX_CHECKED",)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     cc = nvcc()
     jobs = []
     objs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if _stale(obj, [src] + hdrs):
             cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
@@ -68,11 +77,11 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or _stale(LIB, objs):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if jobs or _stale(lib, objs):
+        tmp = lib + ".%d.tmp" % os.getpid()
         run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

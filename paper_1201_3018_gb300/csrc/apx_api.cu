@@ -4,6 +4,7 @@
 // candidates (largest S_q = K_q within each packing's exactness bound, reading
 // c5; Section IV.D), then enqueue the kernel preparation and the block kernels
 // on the caller's stream.  Nothing here touches sample data on the host.
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -41,6 +42,7 @@ struct apx_ctx {
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
     int tw_wb = 0;          // W_block the twiddle tables were built for
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
+    int stall_next = 0;     // test hook: pre-claim the next call's packed spectra
     // tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;          // event pool, pairs
@@ -275,11 +277,23 @@ int ensure_twiddles(apx_ctx* c, int Wb, cudaStream_t st) {
 }
 
 // Record an event pair around one launch when profiling is on.
+// Host-side NVTX range (visible to Nsight tools when one is attached; a few
+// nanoseconds otherwise).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+const char* const kPhaseName[APX_NPHASES] = {"apx.direct", "apx.spectra", "apx.fft", "apx.tc_prep", "apx.tc_mma"};
+
+// One phase: an NVTX range and, while profiling is on, a pair of CUDA events on
+// the launching stream.
 struct Trace {
     apx_ctx* c;
     cudaStream_t st;
     size_t pair = (size_t)-1;
-    Trace(apx_ctx* c_, cudaStream_t st_, int phase) : c(c_), st(st_) {
+    Range range;
+    Trace(apx_ctx* c_, cudaStream_t st_, int phase) : c(c_), st(st_), range(kPhaseName[phase]) {
         if (!c->profiling) return;
         if (2 * (c->ev_used + 1) > c->ev.size()) {
             cudaEvent_t a, b;
@@ -390,6 +404,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
         apx_block_stats* st, cudaStream_t stream) {
     if (!ctx) return APX_ERR_ARG;
+    Range range(sel_kind == 2 ? "apx_conv_full" : (sel_kind == 1 ? "apx_conv_fixed" : "apx_conv"));
     Params p;
     size_t smem = 0;
     int rc = make_params(s, L, k, N, Wb, mode, sel_kind, snr_db, S, K, r, rq, st, &p, &smem);
@@ -430,6 +445,13 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     } else {
         if (++ctx->epoch == 0) ctx->epoch = 1;  // 0 marks "never"
         p.epoch = ctx->epoch;
+        if (ctx->stall_next) {  // claimed by no one who will build them: blocks that pick a packing time out
+            ctx->stall_next = 0;
+            const unsigned ep[kMaxCand] = {p.epoch, p.epoch, p.epoch};
+            cudaError_t e0 = cudaMemcpyAsync(p.claim, ep, sizeof ep, cudaMemcpyHostToDevice, stream);
+            if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(stream);  // the host array goes out of scope
+            if (e0 != cudaSuccess) return cuda_status(e0);
+        }
         {
             Trace t(ctx, stream, APX_PHASE_SPECTRA);
             e = launch_spec(p, stream);
@@ -721,6 +743,7 @@ int apx_sync(apx_ctx* ctx, void* stream) {
     if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->flags.p, 0, sizeof(unsigned), st);
     if (e == cudaSuccess && h) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
+    if (h & 4u) return APX_ERR_CHECK;
     if (h & 2u) return APX_ERR_TIMEOUT;
     return (h & 1u) ? APX_ERR_NONFINITE : APX_OK;
 }
@@ -791,6 +814,7 @@ const char* apx_strerror(int s) {
         case APX_ERR_BUDGET: return "workspace budget exceeded";
         case APX_ERR_CUDA: return "CUDA runtime error";
         case APX_ERR_TIMEOUT: return "bounded device wait timed out";
+        case APX_ERR_CHECK: return "device bounds check failed (checked build)";
         default: return "unknown status";
     }
 }
@@ -809,6 +833,7 @@ struct apx_graph {
 
 // Launch a planned batch on the context's batch workspace.
 static int batch_run(apx_ctx* ctx, BatchPlan& bp, int32_t n, cudaStream_t st) {
+    Range range("apx.batch");
     int rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
     if (!rc && bp.max_wb > 0) rc = ensure_twiddles(ctx, bp.max_wb, st);
     if (!rc) rc = ensure(ctx, ctx->barena, bp.arena_bytes);
@@ -838,6 +863,7 @@ extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, 
 
 extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
     if (!ctx || n < 0 || (n > 0 && !reqs)) return APX_ERR_ARG;
+    Range range("apx_conv_batch_host");
     // device copies of every request's signal, kernel and output, 256-byte aligned
     std::vector<size_t> off(3 * (size_t)n);
     size_t total = 0;
@@ -881,6 +907,12 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
         e = cudaMemcpyAsync(reqs[i].r_out, dq[i].r_out, sizeof(float) * (size_t)(reqs[i].L + reqs[i].N - 1),
                             cudaMemcpyDeviceToHost, st);
     return cuda_status(e);
+}
+
+extern "C" int apx_test_stall_next(apx_ctx* ctx) {
+    if (!ctx) return APX_ERR_ARG;
+    ctx->stall_next = 1;
+    return APX_OK;
 }
 
 extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_bank, int32_t F,

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         const int nout = g.hi - g.lo;
         for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
             const int j0 = g.lo + ch * kRf;
+            if (!APX_IN_BOUNDS(j0 - nkp >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
             float acc[kRf];
             conv_f32<kRf>(xs, kf, nkp, j0, acc);
 #pragma unroll

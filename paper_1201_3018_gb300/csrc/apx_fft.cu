@@ -22,7 +22,7 @@
 
 namespace apx {
 
-constexpr int kSpinLimit = 1 << 22;
+constexpr long long kSpinCycles = 2000000000LL;  // about one second at the maximum SM clock
 
 // Thread t holds window samples 2(t + i NT) and 2(t + i NT) + 1 (pair t + i NT)
 // for pairs below W_block/2; other slots hold zeros, which leave the maximum,
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
         for (int v = 0; v < kVals / 2; ++v)
             if (pair_ok(p, v)) Zf[pad16(threadIdx.x + v * blockDim.x)] = make_float2(xv[2 * v], xv[2 * v + 1]);
         __syncthreads();
-        fft_smem<float2, false>(Zf, mf, p.tw32, p.ntab);
+        fft_smem<float2, false>(Zf, mf, p.tw32, p.ntab, p.status);
     }
 
     pdl_wait();  // kernel statistics and FP32 kernel spectrum from the preparation launch
@@ -150,11 +150,12 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
 
     if (ci < 0) {
         // Full precision: finish the FP32 real-FFT convolution.
-        spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, p.ntab / p.Wb, true);
-        fft_smem<float2, true>(Zf, mf, p.tw32, p.ntab);
+        spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, p.ntab / p.Wb, true, p.status);
+        fft_smem<float2, true>(Zf, mf, p.tw32, p.ntab, p.status);
         for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
             const long long o = g.start + j;
             if (o < 0 || o >= p.out_len) continue;
+            if (!APX_IN_BOUNDS(j >= 0 && j < p.Wb, p.status)) continue;
             p.r[o] = word<float>(Zf, j);
             if (p.rq) p.rq[o] = 0;
         }
@@ -221,13 +222,15 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
         }
     }
     __syncthreads();
-    fft_smem<double2, false>(Z, mm, p.tw64, p.ntab);
+    fft_smem<double2, false>(Z, mm, p.tw64, p.ntab, p.status);
 
     if (role == 2) {
         if (threadIdx.x == 0) {
             int ok = 0;
-            for (int it = 0; it < kSpinLimit; ++it) {
+            const long long t0 = clock64();
+            while (true) {
                 if (ld_acquire(&p.ready[ci]) == p.epoch) { ok = 1; break; }
+                if (clock64() - t0 > kSpinCycles) break;
                 __nanosleep(256);
             }
             if (!ok) atomicOr(p.status, 2u);
@@ -239,8 +242,8 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
             return;
         }
     }
-    spectral_multiply(Z, mm, static_cast<const double2*>(c.H), p.tw64, p.ntab / n, true);
-    fft_smem<double2, true>(Z, mm, p.tw64, p.ntab);
+    spectral_multiply(Z, mm, static_cast<const double2*>(c.H), p.tw64, p.ntab / n, true, p.status);
+    fft_smem<double2, true>(Z, mm, p.tw64, p.ntab, p.status);
 
     if (threadIdx.x == 0) sh.bcast[2] = 1.0 / ((double)cs * (double)ck);
     __syncthreads();

@@ -12,6 +12,16 @@
 
 #include "../../include/apx.h"
 
+
+// Device-side bounds checks of builds with -DAPX_CHECKED: a failed check sets
+// bit 2 of the status word (APX_ERR_CHECK from apx_sync) and the guarded
+// access is skipped.  Other builds compile the checks away.
+#ifdef APX_CHECKED
+#define APX_IN_BOUNDS(cond, status) ((cond) ? true : ((status) ? (atomicOr((status), 4u), false) : false))
+#else
+#define APX_IN_BOUNDS(cond, status) true
+#endif
+
 namespace apx {
 
 constexpr int kMaxWblock = 16384;
@@ -322,13 +332,14 @@ __host__ __device__ constexpr int fft_radix(int m, int nt) {
 // inverse DFT.  Each butterfly reads and writes the same slots, so a pass needs
 // no barrier inside; callers separate passes with __syncthreads().
 template <typename C, int RAD, bool INV>
-__device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab) {
+__device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab, unsigned* st) {
     const int S = M / RAD, nbf = m / RAD;
     const int tstep = ntab / M;
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
         const int g = b / S, j = b - g * S;
         const int base = g * M + j;
         C v[RAD], w[RAD];
+        if (!APX_IN_BOUNDS(base + (RAD - 1) * S < m, st)) continue;
 #pragma unroll
         for (int q = 0; q < RAD; ++q) v[q] = Z[pad16(base + q * S)];
         if (S > 1) twiddles<C, RAD, INV>(w, tw, j * tstep);
@@ -351,23 +362,23 @@ __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict
 }
 
 template <typename C, int R, bool INV>
-__device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw, int ntab) {
+__device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw, int ntab, unsigned* st) {
     int a = 0, t = m;
     while (t >= R) { t /= R; ++a; }   // m = R^a * t, t < R
     if (!INV) {
         int M = m;
-        for (int s = 0; s < a; ++s) { fft_pass<C, R, false>(Z, m, M, tw, ntab); __syncthreads(); M /= R; }
-        if (t == 8) fft_pass<C, 8, false>(Z, m, 8, tw, ntab);
-        else if (t == 4) fft_pass<C, 4, false>(Z, m, 4, tw, ntab);
-        else if (t == 2) fft_pass<C, 2, false>(Z, m, 2, tw, ntab);
+        for (int s = 0; s < a; ++s) { fft_pass<C, R, false>(Z, m, M, tw, ntab, st); __syncthreads(); M /= R; }
+        if (t == 8) fft_pass<C, 8, false>(Z, m, 8, tw, ntab, st);
+        else if (t == 4) fft_pass<C, 4, false>(Z, m, 4, tw, ntab, st);
+        else if (t == 2) fft_pass<C, 2, false>(Z, m, 2, tw, ntab, st);
         if (t > 1) __syncthreads();
     } else {
-        if (t == 8) fft_pass<C, 8, true>(Z, m, 8, tw, ntab);
-        else if (t == 4) fft_pass<C, 4, true>(Z, m, 4, tw, ntab);
-        else if (t == 2) fft_pass<C, 2, true>(Z, m, 2, tw, ntab);
+        if (t == 8) fft_pass<C, 8, true>(Z, m, 8, tw, ntab, st);
+        else if (t == 4) fft_pass<C, 4, true>(Z, m, 4, tw, ntab, st);
+        else if (t == 2) fft_pass<C, 2, true>(Z, m, 2, tw, ntab, st);
         if (t > 1) __syncthreads();
         int M = t * R;
-        for (int s = 0; s < a; ++s) { fft_pass<C, R, true>(Z, m, M, tw, ntab); __syncthreads(); M *= R; }
+        for (int s = 0; s < a; ++s) { fft_pass<C, R, true>(Z, m, M, tw, ntab, st); __syncthreads(); M *= R; }
     }
 }
 
@@ -375,11 +386,11 @@ __device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw
 // CTA.  Forward: natural order in, digit-reversed order out (see fft_perm).
 // Inverse: that order in, natural order out, unnormalised.
 template <typename C, bool INV>
-__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab) {
+__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab, unsigned* st = nullptr) {
     const int R = fft_radix<C>(m, blockDim.x);
-    if (sizeof(C) == 8 && R == 16) fft_passes<C, 16, INV>(Z, m, tw, ntab);
-    else if (sizeof(C) == 8 && R == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab);
-    else fft_passes<C, 4, INV>(Z, m, tw, ntab);
+    if (sizeof(C) == 8 && R == 16) fft_passes<C, 16, INV>(Z, m, tw, ntab, st);
+    else if (sizeof(C) == 8 && R == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab, st);
+    else fft_passes<C, 4, INV>(Z, m, tw, ntab, st);
 }
 
 // Slot of frequency k after the forward FFT: k = r1 + R1 r2 + R1 R2 r3 + ...
@@ -440,7 +451,7 @@ __device__ __forceinline__ int fft_perm_r(int k, int m) {
 // so a round costs one memory latency.
 template <typename C, int R, int B>
 __device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, const C* __restrict__ tw, int twn,
-                                                    bool coherent) {
+                                                    bool coherent, unsigned* st) {
     const int half = m / 2, nt = blockDim.x;
     for (int k0 = threadIdx.x; k0 <= half; k0 += B * nt) {
         C hk[B], hmk[B], w[B];
@@ -466,7 +477,9 @@ __device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, con
                 C cym = cconj(Ym);
                 Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
             } else {
-                const int pk = pad16(fft_perm_r<R>(k, m)), pmk = pad16(fft_perm_r<R>(m - k, m));
+                const int qk = fft_perm_r<R>(k, m), qmk = fft_perm_r<R>(m - k, m);
+                if (!APX_IN_BOUNDS(qk < m && qmk < m, st)) continue;
+                const int pk = pad16(qk), pmk = pad16(qmk);
                 C a = Z[pk], b = Z[pmk];
                 C Xk, Xmk;
                 real_post(a, b, w[u], Xk, Xmk);
@@ -484,12 +497,13 @@ __device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, con
 
 // `coherent`: H was written during this kernel (read around L1).
 template <typename C>
-__device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__ tw, int twn, bool coherent) {
+__device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__ tw, int twn, bool coherent,
+                                  unsigned* st = nullptr) {
     constexpr int B = sizeof(C) == 8 ? 5 : 3;
     const int R = fft_radix<C>(m, blockDim.x);
-    if (R == 16) spectral_multiply_r<C, 16, B>(Z, m, H, tw, twn, coherent);
-    else if (R == 8) spectral_multiply_r<C, 8, B>(Z, m, H, tw, twn, coherent);
-    else spectral_multiply_r<C, 4, B>(Z, m, H, tw, twn, coherent);
+    if (R == 16) spectral_multiply_r<C, 16, B>(Z, m, H, tw, twn, coherent, st);
+    else if (R == 8) spectral_multiply_r<C, 8, B>(Z, m, H, tw, twn, coherent, st);
+    else spectral_multiply_r<C, 4, B>(Z, m, H, tw, twn, coherent, st);
 }
 
 // Programmatic dependent launch: let the next kernel in the stream start, and

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const Ba
     float2* Z = reinterpret_cast<float2*>(smem);
     for (int j = threadIdx.x; j < ns; j += blockDim.x) Z[pad16(j)] = make_float2(ktap(p, r + j * R1), 0.f);
     __syncthreads();
-    fft_smem<float2, false>(Z, ns, p.tw32, p.ntab);
+    fft_smem<float2, false>(Z, ns, p.tw32, p.ntab, p.status);
     for (int k = threadIdx.x; k < ns; k += blockDim.x) p.Ysub[r * ns + k] = Z[pad16(fft_perm<float2>(k, ns))];
 }
 

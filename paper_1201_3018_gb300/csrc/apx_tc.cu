@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
 __device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int grp, uint32_t acc0, uint32_t stg,
                                               int lane, int lq, int half, const float* __restrict__ cs_tab,
                                               const float* __restrict__ ck_tab, float* __restrict__ y,
-                                              int32_t* __restrict__ yq) {
+                                              int32_t* __restrict__ yq, unsigned* status) {
     const int row = lq * 32 + lane;
     const int rr = lane >> 3, ii = lane & 7;
     const uint32_t acc = acc0 + ((uint32_t)(lq * 32) << 16);
@@ -327,6 +327,7 @@ __device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int 
                 int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
                 for (int c = 32 * half; c < g.P; c += 32 * (kTcEpiWarps / 4)) {
                     uint32_t r[32];
+                    if (!APX_IN_BOUNDS(fl * g.P + c + 32 <= kTcN, status)) continue;  // warp-uniform
                     tmem_ld32_nowait(acc + (uint32_t)(fl * g.P + c), r);
                     tmem_wait_ld();
                     // scale (Eq. 16) and stage this lane's row
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t blk = u / g.ngroups;
             const int grp = (int)(u % g.ngroups);
             epilogue_tile(g, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * 4096u, lane,
-                          lq, half, cs_tab, ck_tab, y, yq);
+                          lq, half, cs_tab, ck_tab, y, yq, status);
             // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
             tc_fence_before();
             __syncwarp();

@@ -5,6 +5,16 @@
 
 #include <cstdint>
 
+
+// Device-side bounds checks of builds with -DAPX_CHECKED: a failed check sets
+// bit 2 of the status word (APX_ERR_CHECK from apx_sync) and the guarded
+// access is skipped.  Other builds compile the checks away.
+#ifdef APX_CHECKED
+#define APX_IN_BOUNDS(cond, status) ((cond) ? true : ((status) ? (atomicOr((status), 4u), false) : false))
+#else
+#define APX_IN_BOUNDS(cond, status) true
+#endif
+
 namespace apx {
 
 // Tensor-core time-domain core (filterbank).  A tile is kTcM rows of P output

@@ -32,7 +32,7 @@ def dev(x):
 
 def run_both(ctx, s, k, Wb, mode, snr=None, Sq=None, Kq=None, want=None):
     r, rq, st = ctx.conv(dev(s), dev(k), Wb, mode, snr_db=snr, Sq=Sq, Kq=Kq, want_int=True, want_stats=True)
-    ctx.apx_sync()
+    assert ctx.apx_sync() == 0
     ro, rqo, sto, rc = O.apx_conv(s, k, Wb, mode, snr_db=snr or 0.0, Sq=Sq or 0, Kq=Kq or 0, nthreads=0,
                                   want=want)
     assert rc == 0
@@ -253,3 +253,21 @@ def test_full_fp64_needs_direct_core_and_no_packing(ctx):
     with pytest.raises(apx.ApxError) as e:
         ctx.apx_conv(s, k, 64, apx.CORE_DIRECT | apx.PACK_AUTO | apx.FULL_FP64, 30.0, r)
     assert e.value.status == apx.APX_ERR_ARG
+
+
+def test_bounded_wait_times_out_and_context_recovers(ctx):
+    """Failure path without a GPU fault: the blocks that pick a packing wait
+    for a packed spectrum nobody publishes, give up after their bounded spin,
+    write NaN and report APX_ERR_TIMEOUT; the next call is normal."""
+    L, N, Wb = 20000, 65, 1024
+    s = wl.random_signal(L + 31, L, "laplace", 0.1)
+    k = wl.random_signal(N + 32, N, "uniform")
+    mode = apx.CORE_FFT | apx.PACK_AUTO
+    sd, kd = dev(s), dev(k)
+    ctx.test_stall_next()
+    r, rq, st = ctx.conv(sd, kd, Wb, mode, snr_db=12.0, want_int=True, want_stats=True)
+    assert ctx.apx_sync() == apx.APX_ERR_TIMEOUT
+    assert np.isnan(r.cpu().numpy()).any()
+    r2, rq2, st2, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=12.0)
+    assert ctx.apx_sync() == 0
+    check(r2, rq2, st2, ro, rqo, so, s, k, mode, Wb)
