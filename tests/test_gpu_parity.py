@@ -266,7 +266,9 @@ def test_bounded_wait_times_out_and_context_recovers(ctx):
     sd, kd = dev(s), dev(k)
     ctx.test_stall_next()
     r, rq, st = ctx.conv(sd, kd, Wb, mode, snr_db=12.0, want_int=True, want_stats=True)
-    assert ctx.apx_sync() == apx.APX_ERR_TIMEOUT
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_sync()
+    assert e.value.status == apx.APX_ERR_TIMEOUT
     assert np.isnan(r.cpu().numpy()).any()
     r2, rq2, st2, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=12.0)
     assert ctx.apx_sync() == 0
