@@ -273,3 +273,64 @@ def test_bounded_wait_times_out_and_context_recovers(ctx):
     r2, rq2, st2, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=12.0)
     assert ctx.apx_sync() == 0
     check(r2, rq2, st2, ro, rqo, so, s, k, mode, Wb)
+
+
+def test_large_input_indices(ctx):
+    """2^30 + 12345 samples (4 GB in, 4 GB out): block origins, window loads and
+    output offsets beyond 2^31 elements' bytes stay exact; outputs sampled at the
+    start, the middle and the end against Eq. (1) in FP64."""
+    L, N, Wb = (1 << 30) + 12345, 257, 4096
+    g = torch.Generator(device="cuda").manual_seed(7)
+    s = torch.randn(L, device="cuda", generator=g)
+    k = dev(wl.random_signal(91, N, "uniform"))
+    r = torch.empty(L + N - 1, device="cuda")
+    ctx.apx_conv_full(s, k, Wb, apx.CORE_FFT | apx.PACK_NONE, r)
+    assert ctx.apx_sync() == 0
+    idx = np.concatenate([np.arange(0, 300), np.arange(L // 2, L // 2 + 300), np.arange(L + N - 1 - 600, L + N - 1)])
+    lo, hi = int(idx.min()), int(idx.max())
+    # the samples these outputs touch, gathered on the host
+    kh = k.cpu().numpy()
+    got = r[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    for part in (idx[:300], idx[300:600], idx[600:]):
+        a, b = max(0, int(part.min()) - N + 1), min(L, int(part.max()) + 1)
+        seg = s[a:b].cpu().numpy()
+        ref = O.conv_ref_at(seg, kh, part - a)
+        sel = np.isin(idx, part)
+        err = np.linalg.norm(got[sel] - ref) / max(np.linalg.norm(ref), 1e-300)
+        assert err <= 1e-5, err
+    del s, r
+    torch.cuda.empty_cache()
+
+
+def test_filterbank_large_input(ctx):
+    """Filterbank over 2^28 samples (4 kernels, 4 GB of outputs): the first and
+    the last block against the oracle."""
+    L, F, N = 1 << 28, 4, 64
+    g = torch.Generator(device="cuda").manual_seed(8)
+    s = torch.randn(L, device="cuda", generator=g)
+    kb = np.stack([wl.random_signal(200 + f, N, "uniform") for f in range(F)])
+    out_len = L + N - 1
+    ldy = (out_len + 3) // 4 * 4
+    y = torch.empty(F, ldy, device="cuda")
+    T, nb = apx.filterbank_blocks(L, F, N)
+    cs = torch.empty(nb, device="cuda")
+    ctx.apx_filterbank(s, torch.from_numpy(kb).cuda(), 127, 127, y, None, cs)
+    assert ctx.apx_sync() == 0
+    csh = cs.cpu().numpy()
+    for b in (0, nb - 1):
+        shift = b * T
+        a1 = min(L, shift + T)
+        if b == 0:
+            yo, _, cso = O.filterbank(s[:a1].cpu().numpy(), kb, T, 127, 127, blocks=(0, 1))
+            ref, c_ref = yo[:, :T], cso[0]
+        else:
+            # a shifted problem whose block 1 has this block's window: T - N + 1 zeros,
+            # then s[bT - N + 1 .. a1)
+            x = np.concatenate([np.zeros(T - N + 1, np.float32), s[shift - N + 1:a1].cpu().numpy()])
+            yo, _, cso = O.filterbank(x, kb, T, 127, 127, blocks=(1, 2))
+            ref, c_ref = yo[:, T:T + min(T, out_len - shift)], cso[1]
+        assert c_ref == csh[b]
+        got = y[:, shift:shift + ref.shape[1]].cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=1e-6, atol=0)
+    del s, y
+    torch.cuda.empty_cache()
