@@ -334,3 +334,29 @@ def test_filterbank_large_input(ctx):
         np.testing.assert_allclose(got, ref, rtol=1e-6, atol=0)
     del s, y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("core,L,N,Wb,mode_bits,snr", [
+    (apx.CORE_FFT, 1 << 20, 4096, 8192, apx.OP_XCORR | apx.PACK_AUTO, 45.0),   # the matching workload
+    (apx.CORE_FFT, (1 << 19) + 777, 257, 2048, apx.PACK_AUTO, 20.0),           # packed blocks
+    (apx.CORE_DIRECT, (1 << 19) + 3, 65, 1024, apx.PACK_AUTO, 45.0),
+    (apx.CORE_DIRECT, 1 << 18, 64, 1024, apx.PACK_NONE | apx.FULL_FP64, 0.0),
+])
+def test_host_pipelined_equals_device_path(ctx, core, L, N, Wb, mode_bits, snr):
+    """apx_conv_host cuts enough blocks into chunks whose copies and kernels
+    overlap; every block keeps its global geometry, so the result equals the
+    device-buffer call bit for bit (two calls with different inputs)."""
+    for rep in range(2):
+        s = wl.random_signal(L + 41 + rep, L, "laplace", 0.1)
+        k = wl.random_signal(N + 42, N, "uniform")
+        mode = core | mode_bits
+        sh, kh = torch.from_numpy(s).pin_memory(), torch.from_numpy(k).pin_memory()
+        out = torch.full((L + N - 1,), float("nan")).pin_memory()
+        ctx.apx_conv_host(sh, kh, Wb, mode, snr, 0, 0, out)
+        r = torch.empty(L + N - 1, device="cuda")
+        if (mode & 0xF00) == apx.PACK_NONE:
+            ctx.apx_conv_full(dev(s), dev(k), Wb, mode, r)
+        else:
+            ctx.apx_conv(dev(s), dev(k), Wb, mode, snr, r)
+        assert ctx.apx_sync() == 0
+        np.testing.assert_array_equal(out.numpy(), r.cpu().numpy())
