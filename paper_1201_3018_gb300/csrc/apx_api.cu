@@ -37,8 +37,8 @@ struct apx_ctx {
     DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
     DevBuf tc_seg, tc_b, tc_cs, tc_ck;  // filterbank: FP16 block segments, Toeplitz B, c_s per block, c_k per kernel
     DevBuf bhost;                       // batched calls from host buffers: device copies of inputs and outputs
-    cudaStream_t hp_in = nullptr, hp_out = nullptr;  // host-pipelined calls: copy-in and copy-out streams
-    std::vector<cudaEvent_t> hp_ev;                  // and their events
+    cudaStream_t hp_in = nullptr;       // calls from host buffers: the signal's copy stream
+    std::vector<cudaEvent_t> hp_ev;     // and its events
     void* hstage = nullptr;             // pinned staging for batch parameters
     size_t hstage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
@@ -401,93 +401,27 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     return APX_OK;
 }
 
-// A call from host buffers, pipelined: the blocks are cut into `nchunk` ranges;
-// chunk c's input samples are copied in on one stream, its block kernel runs
-// on the caller's stream as soon as its window samples are resident, and its
-// outputs are copied out on a third stream while later chunks compute.  Every
-// block keeps its global geometry (Params::blk0), so the results equal those
-// of one launch over all blocks.
-struct HostPipe {
-    const float* s_h;
-    float* r_h;
-    int nchunk;
-};
-constexpr int kMaxChunks = 8;
-
-// The copy streams and events of host-pipelined calls (created on first use);
-// the copy streams then wait for the work already on the caller's stream,
-// which may still read the context's device buffers.
-cudaError_t pipeline_begin(apx_ctx* ctx, cudaStream_t st) {
+// A call from host buffers: the signal's host-to-device copy runs on a copy
+// stream while the caller's stream copies the kernel and (FFT core) prepares
+// its spectrum; the block kernel then waits for the signal copy.
+cudaError_t copy_stream_begin(apx_ctx* ctx, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (!ctx->hp_in) e = cudaStreamCreateWithFlags(&ctx->hp_in, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !ctx->hp_out) e = cudaStreamCreateWithFlags(&ctx->hp_out, cudaStreamNonBlocking);
-    while (e == cudaSuccess && ctx->hp_ev.size() < (size_t)(2 * kMaxChunks + 2)) {
+    while (e == cudaSuccess && ctx->hp_ev.size() < 2) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) ctx->hp_ev.push_back(ev);
     }
-    if (e != cudaSuccess) return e;
-    const cudaEvent_t ev_start = ctx->hp_ev[2 * kMaxChunks];
-    e = cudaEventRecord(ev_start, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hp_in, ev_start, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hp_out, ev_start, 0);
-    return e;
-}
-
-cudaError_t pipeline(apx_ctx* ctx, const Params& p, size_t smem, cudaStream_t st, const HostPipe& hp,
-                     cudaError_t (*launch)(const Params&, size_t, cudaStream_t)) {
-    const int nc = hp.nchunk;
-    cudaError_t e = cudaSuccess;
-    cudaEvent_t* ev_in = ctx->hp_ev.data();
-    cudaEvent_t* ev_comp = ev_in + kMaxChunks;
-    cudaEvent_t ev_done = ev_in[2 * kMaxChunks + 1];
-    auto start = [&](long long i) -> long long {
-        return p.fft ? (i - p.head) * (long long)p.W - 2 : (i == 0 ? 0 : i * (long long)p.W - 2);
-    };
-    auto clampll = [](long long v, long long lo, long long hi) { return v < lo ? lo : (v > hi ? hi : v); };
-    auto in_lo = [&](long long i) { return clampll(start(i), 0, p.L); };
-    auto out_lo = [&](long long i) {
-        return (p.fft || i > 0) ? clampll(start(i) + p.Nodd + 1, 0, p.out_len) : 0ll;
-    };
-    long long b[kMaxChunks + 1];
-    for (int c = 0; c <= nc; ++c) b[c] = p.P * c / nc;
-    long long cin[kMaxChunks + 1];
-    for (int c = 0; c < nc; ++c) cin[c] = in_lo(b[c]);
-    cin[nc] = p.L;
-    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-        if (cin[c + 1] > cin[c])
-            e = cudaMemcpyAsync((void*)(p.s + cin[c]), hp.s_h + cin[c], sizeof(float) * (size_t)(cin[c + 1] - cin[c]),
-                                cudaMemcpyHostToDevice, ctx->hp_in);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], ctx->hp_in);
-    }
-    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-        // window samples of this chunk's blocks: every copy that starts below its end
-        const long long need = p.P > 0 ? (long long)(start(b[c + 1] - 1) + p.Wb) : 0;
-        for (int c2 = 0; c2 < nc && e == cudaSuccess; ++c2)
-            if (c2 >= c && cin[c2] < need && cin[c2 + 1] > cin[c2]) e = cudaStreamWaitEvent(st, ev_in[c2], 0);
-        if (e != cudaSuccess) break;
-        Params q = p;
-        q.blk0 = b[c];
-        q.P = b[c + 1] - b[c];
-        e = launch(q, smem, st);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_comp[c], st);
-    }
-    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-        const long long o0 = out_lo(b[c]), o1 = c + 1 < nc ? out_lo(b[c + 1]) : p.out_len;
-        e = cudaStreamWaitEvent(ctx->hp_out, ev_comp[c], 0);
-        if (e == cudaSuccess && o1 > o0)
-            e = cudaMemcpyAsync(hp.r_h + o0, p.r + o0, sizeof(float) * (size_t)(o1 - o0), cudaMemcpyDeviceToHost,
-                                ctx->hp_out);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(ev_done, ctx->hp_out);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_done, 0);
+    // the device buffers may still be read by earlier work on the caller's stream
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->hp_ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hp_in, ctx->hp_ev[0], 0);
     return e;
 }
 
 // Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
 int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
         int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
-        apx_block_stats* st, cudaStream_t stream, const HostPipe* hp = nullptr) {
+        apx_block_stats* st, cudaStream_t stream, cudaEvent_t before_blocks = nullptr) {
     if (!ctx) return APX_ERR_ARG;
     Range range(sel_kind == 2 ? "apx_conv_full" : (sel_kind == 1 ? "apx_conv_fixed" : "apx_conv"));
     Params p;
@@ -525,8 +459,9 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     cudaError_t e;
     if (!pl.fft) {
         Trace t(ctx, stream, APX_PHASE_DIRECT);
-        e = hp ? pipeline(ctx, p, smem, stream, *hp, launch_direct) : launch_direct(p, smem, stream);
-        ctx->launches += hp ? hp->nchunk : 1;
+        e = before_blocks ? cudaStreamWaitEvent(stream, before_blocks, 0) : cudaSuccess;
+        if (e == cudaSuccess) e = launch_direct(p, smem, stream);
+        ctx->launches += 1;
     } else {
         if (++ctx->epoch == 0) ctx->epoch = 1;  // 0 marks "never"
         p.epoch = ctx->epoch;
@@ -545,8 +480,9 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         }
         if (e == cudaSuccess) {
             Trace t(ctx, stream, APX_PHASE_FFT);
-            e = hp ? pipeline(ctx, p, smem, stream, *hp, launch_fft) : launch_fft(p, smem, stream);
-            ctx->launches += hp ? hp->nchunk : 1;
+            if (before_blocks) e = cudaStreamWaitEvent(stream, before_blocks, 0);
+            if (e == cudaSuccess) e = launch_fft(p, smem, stream);
+            ctx->launches += 1;
         }
     }
     return cuda_status(e);
@@ -740,7 +676,6 @@ int stage_upload(apx_ctx* c, const void* src1, size_t n1, void* dst1, const void
     if (c->hstage_bytes < need) {
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->hp_in) cudaStreamDestroy(c->hp_in);
-        if (c->hp_out) cudaStreamDestroy(c->hp_out);
         for (cudaEvent_t e : c->hp_ev) cudaEventDestroy(e);
         c->hstage = nullptr;
         c->hstage_bytes = 0;
@@ -788,7 +723,6 @@ void apx_destroy(apx_ctx* c) {
         for (DevBuf* b : all) release(c, *b);
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->hp_in) cudaStreamDestroy(c->hp_in);
-        if (c->hp_out) cudaStreamDestroy(c->hp_out);
         for (cudaEvent_t e : c->hp_ev) cudaEventDestroy(e);
         if (c->stage_ev) cudaEventDestroy(c->stage_ev);
         for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -850,26 +784,15 @@ int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, i
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t pack = mode & 0xF00u;
     const int sel = pack == APX_PACK_NONE ? 2 : ((S_q > 0 && K_q > 0 && pack != APX_PACK_AUTO) ? 1 : 0);
-    int64_t P = 0;
-    int32_t W = 0;
-    rc = apx_plan_blocks(L, N, W_block, mode, &P, &W);
-    if (rc) return rc;
-    // enough blocks: overlap the input copy, the block kernels and the output copy
-    const int nchunk = (P >= 64 && L >= (1 << 18)) ? 4 : 1;
-    cudaError_t e = nchunk > 1 ? pipeline_begin(ctx, st) : cudaSuccess;
+    // the signal copy overlaps the kernel copy and the spectrum preparation
+    cudaError_t e = copy_stream_begin(ctx, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->hs.p, s_h, sizeof(float) * (size_t)L, cudaMemcpyHostToDevice, ctx->hp_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->hp_ev[1], ctx->hp_in);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hk.p, k_h, sizeof(float) * (size_t)N, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
-    if (nchunk > 1) {
-        const HostPipe hp = {s_h, r_h, nchunk};
-        rc = run(ctx, (const float*)ctx->hs.p, L, (const float*)ctx->hk.p, N, W_block, mode, sel, snr_target_db, S_q,
-                 K_q, (float*)ctx->hr.p, nullptr, nullptr, st, &hp);
-        if (rc) return rc;
-        return apx_sync(ctx, stream);
-    }
-    e = cudaMemcpyAsync(ctx->hs.p, s_h, sizeof(float) * (size_t)L, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_status(e);
     rc = run(ctx, (const float*)ctx->hs.p, L, (const float*)ctx->hk.p, N, W_block, mode, sel, snr_target_db, S_q, K_q,
-             (float*)ctx->hr.p, nullptr, nullptr, st);
+             (float*)ctx->hr.p, nullptr, nullptr, st, ctx->hp_ev[1]);
     if (rc) return rc;
     e = cudaMemcpyAsync(r_h, ctx->hr.p, sizeof(float) * (size_t)(L + N - 1), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_status(e);

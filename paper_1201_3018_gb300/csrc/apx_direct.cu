@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     __shared__ Shared sh;
     __shared__ int s_ci;
     __shared__ Params sp;
-    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x + p0.blk0;
+    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
     const Params& p = BATCH ? sp : p0;
     const BlockGeom g = block_geom(p, i);
     const DirectLayout& dl = p.dl;

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
     __shared__ Shared sh;
     __shared__ int s_flag;
     __shared__ Params sp;
-    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x + p0.blk0;
+    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
     const Params& p = BATCH ? sp : p0;
     const BlockGeom g = block_geom(p, i);
     float xv[kVals];

@@ -77,7 +77,6 @@ struct Params {
     unsigned* claim;      // FFT core, per candidate: last call that claimed building its spectrum
     unsigned* ready;      // FFT core, per candidate: last call whose spectrum is complete
     unsigned epoch;       // FFT core: this call's number (never 0)
-    long long blk0;       // first block of this launch (a host-pipelined call launches block ranges)
     int autosel;          // 1: per-block selection under thr
     int full64;           // direct core, no packing: full precision in FP64
     int ncand;

@@ -342,10 +342,10 @@ def test_filterbank_large_input(ctx):
     (apx.CORE_DIRECT, (1 << 19) + 3, 65, 1024, apx.PACK_AUTO, 45.0),
     (apx.CORE_DIRECT, 1 << 18, 64, 1024, apx.PACK_NONE | apx.FULL_FP64, 0.0),
 ])
-def test_host_pipelined_equals_device_path(ctx, core, L, N, Wb, mode_bits, snr):
-    """apx_conv_host cuts enough blocks into chunks whose copies and kernels
-    overlap; every block keeps its global geometry, so the result equals the
-    device-buffer call bit for bit (two calls with different inputs)."""
+def test_host_entry_equals_device_path_large(ctx, core, L, N, Wb, mode_bits, snr):
+    """apx_conv_host (signal copied on a second stream while the kernel is
+    prepared) equals the device-buffer call bit for bit, on two calls with
+    different inputs."""
     for rep in range(2):
         s = wl.random_signal(L + 41 + rep, L, "laplace", 0.1)
         k = wl.random_signal(N + 42, N, "uniform")
