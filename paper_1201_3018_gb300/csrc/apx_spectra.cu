@@ -29,8 +29,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const Ba
         const KStats ks = kernel_stats(p, sh);
         double l1s[kMaxCand] = {0.0, 0.0, 0.0};
         const bool ok = !ks.bad && ks.Mk > 0.f;
-        for (int c = 0; c < p.ncand; ++c)
-            if (ok) l1s[c] = (double)kbar_l1(p, p.cand[c], compand_factor(p.cand[c].K, ks.Mk), sh);
+        for (int c = 0; c < p.ncand; ++c) {
+            // Under per-block selection a candidate whose model SNR misses the target even for
+            // the best window (second moment = squared maximum; the model depends on the window
+            // only through that ratio) is never chosen: skip its norm (1 % margin for rounding).
+            const bool reachable = !p.autosel || snr_feasible(1.0, 1.f, ks.sig2k, ks.Mk, p.cand[c].S, p.cand[c].K,
+                                                              __dmul_rn(p.thr, 1.01));
+            if (ok && reachable) l1s[c] = (double)kbar_l1(p, p.cand[c], compand_factor(p.cand[c].K, ks.Mk), sh);
+        }
         if (threadIdx.x == 0) {
             KInfo o;
             o.Mk = ks.Mk;
