@@ -356,6 +356,34 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
     kpad = -(-(N + 63) // 64) * 64
     useful = 2.0 * F * out_len * N
     peak = float(pk.get("bf16_tflops", 1899.0))
+
+    # S_q = K_q = 16: every companded integer is exact in FP8 E4M3 (the paper's
+    # 16-level setting), and the library runs the FP8 tensor-core path
+    y8 = torch.empty(F, ldy, device=dev)
+
+    def step8():
+        ctx.apx_filterbank(sd, kd, 16, 16, y8, stream=stream)
+
+    for _ in range(3):
+        step8()
+    t8 = time_steps(step8, steps, flush, stream) / steps
+    ctx.profile(True)
+    time_steps(step8, min(steps, 20), flush, stream)
+    prof8 = ctx.profile_read()
+    ctx.profile(False)
+    mma8 = prof8["tc_mma"][0] / max(prof8["tc_mma"][1], 1)
+    assert ctx.apx_sync(stream) == 0
+    d8 = (y8[:, :out_len].double() - yfull.double())
+    snr8 = (10 * torch.log10((yfull.double() ** 2).sum(1) / (d8 * d8).sum(1))).cpu().numpy()
+    del y8
+    fp8 = {"S_q": 16, "K_q": 16, "operands": "FP8 E4M3 (kind::f8f6f4)", "ms_per_step": t8,
+           "value": F * out_len / (t8 * 1e-3) / 1e9, "unit": UNIT, "tflops_useful": useful / (t8 * 1e-3) / 1e12,
+           "speedup_vs_full_precision": tf / t8,
+           "snr_vs_full_db": {"min": float(snr8.min()), "median": float(np.median(snr8)), "max": float(snr8.max())},
+           "roofline_tc_mma": {"bound": "tensor", "achieved": useful / (mma8 * 1e-3) / 1e12, "peak": 2 * peak,
+                               "unit": "TFLOP/s", "frac": useful / (mma8 * 1e-3) / 1e12 / (2 * peak),
+                               "peak_source": "measured cuBLAS bf16 x 2 (nominal FP8 : FP16 dense ratio)",
+                               "kernel_ms": mma8}}
     return {"workload": "filterbank: 2^22 N(0,1) samples, 32 Hann-windowed-sinc band-pass kernels of 1024 taps "
                         "(log-spaced 50 Hz - 20 kHz at 44.1 kHz), S_q = K_q = 127, FP16 integers on the tensor cores",
             "outputs_per_step": F * out_len, "value": F * out_len / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
@@ -369,7 +397,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
                                 "unit": "TFLOP/s", "frac": useful / (mma_ms * 1e-3) / 1e12 / peak,
                                 "peak_source": "measured cuBLAS bf16 (FP16 runs at the same tensor rate)",
                                 "executed_over_useful": kpad / N, "traffic": traffic_for("tc_mma")},
-            "blocks": nb, "outputs_per_block": T}
+            "blocks": nb, "outputs_per_block": T, "fp8_sq16": fp8}
 
 
 def bench_paper_comparison(ctx, dev, flush, stream):

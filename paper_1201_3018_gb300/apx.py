@@ -72,9 +72,11 @@ SIGNATURES = {
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
 
 
-def filterbank_blocks(L, F, N):
-    """(outputs per block T, number of blocks) of apx_filterbank."""
-    P = 256 if F == 1 else (128 if F == 2 else 64)
+def filterbank_blocks(L, F, N, Sq=127, Kq=127):
+    """(outputs per block T, number of blocks) of apx_filterbank (FP8 operands
+    when S_q, K_q <= 16: 128 phases per row for two or more kernels)."""
+    fp8 = Sq <= 16 and Kq <= 16
+    P = 256 if F == 1 else (128 if (F == 2 or fp8) else 64)
     T = 128 * P
     return T, (L + N - 1 + T - 1) // T
 

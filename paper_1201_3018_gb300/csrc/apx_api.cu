@@ -949,7 +949,9 @@ extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const 
     if (S_q < 1 || K_q < 1 || S_q > kTcMaxQ || K_q > kTcMaxQ) return APX_ERR_RANGE;
     if ((long long)N * S_q * K_q > kTcExactSum) return APX_ERR_RANGE;
     TcGeom g;
-    if (!tc_geometry(L, F, N, &g)) return APX_ERR_ARG;
+    // the narrowest operand type that holds every companded integer exactly
+    const int esize = (S_q <= kTcMaxQ8 && K_q <= kTcMaxQ8) ? 1 : 2;
+    if (!tc_geometry(L, F, N, esize, &g)) return APX_ERR_ARG;
     if (ldy < g.out_len || (ldy & 3) || ((uintptr_t)y_out & 15) || ((uintptr_t)yq_out & 15)) return APX_ERR_ARG;
     g.ldy = ldy;
     DeviceGuard dg(ctx->device);

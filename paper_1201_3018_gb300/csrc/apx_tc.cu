@@ -42,6 +42,7 @@
 // stream, one 128 x 64 A box per K step.
 #include <cuda.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cstdint>
 
@@ -53,8 +54,8 @@ namespace {
 
 constexpr int kTcEpiWarps = 4;   // one per tensor-memory lane quarter
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
-constexpr uint32_t kTcABytes = kTcM * kTcK * 2;
-constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;
+constexpr uint32_t kTcABytes = kTcM * 128;  // a K slice: one 128-byte row per operand row
+constexpr uint32_t kTcBBytes = kTcN * 128;
 constexpr uint32_t kTcTmemCols = kTcN;
 constexpr uint32_t kTcStageOut = kTcEpiWarps * 4096;  // output staging, 4 KB per epilogue warp
 constexpr int kTcABoxRows = 64;                     // resident A: TMA box rows
@@ -133,6 +134,17 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same with FP8 E4M3 operands (kind::f8f6f4: format code 0 = E4M3 in the same
+// descriptor fields, K = 32 per instruction, still 32 bytes of each row).
+__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -186,14 +198,28 @@ __device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64
     return r;
 }
 
-// Eq. (2) on the block's window, written as the block's FP16 segment
+// Operand element types: FP16, or FP8 E4M3 when S_q, K_q <= 16 (every
+// companded integer is then exact in E4M3, and the tensor core takes twice the
+// K per instruction).  from_int converts an exact small integer.
+template <typename E> struct TcElem;
+template <> struct TcElem<__half> {
+    static __device__ __forceinline__ __half from_int(float q) { return __float2half_rn(q); }
+};
+template <> struct TcElem<uint8_t> {
+    static __device__ __forceinline__ uint8_t from_int(float q) {
+        return (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    }
+};
+
+// Eq. (2) on the block's window, written as the block's segment (FP16 or FP8)
 // seg[u] = s~[t0 - N + 1 + u]; entries past the window (u >= T + N - 1) are 0.
 // One coalesced pass stages the window in shared memory and finds its
 // maximum (one integer reduction of the magnitude bits: NaN lies above inf);
-// the companding then reads shared memory and writes 16-byte vectors.
+// the companding then reads shared memory and writes 8-element vectors.
 constexpr int kRun = 8;
+template <typename E>
 __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, int64_t L, TcGeom g, int Sq,
-                                                  __half* __restrict__ seg, float* __restrict__ cs_tab,
+                                                  E* __restrict__ seg, float* __restrict__ cs_tab,
                                                   float* __restrict__ cs_out, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) float win[];  // nwin window samples, padded to a multiple of kRun
     __shared__ int red[8];
@@ -229,24 +255,23 @@ __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, i
     if (bad || Mf > 3.402823466e38f) c = __int_as_float(0x7fc00000);
     else if (Mf > 0.f) c = __fdiv_rn((float)Sq, Mf);
     const bool live = Mf > 0.f && Mf <= 3.402823466e38f && !bad;
-    __half* out = seg + b * nseg;
+    E* out = seg + b * nseg;
     for (int64_t u0 = (int64_t)threadIdx.x * kRun; u0 < nseg; u0 += (int64_t)blockDim.x * kRun) {
-        __align__(16) __half2 h[kRun / 2];
+        __align__(16) E h[kRun];
         if (live && u0 < nwin) {
             const float4 p = *reinterpret_cast<const float4*>(win + u0);
             const float4 q = *reinterpret_cast<const float4*>(win + u0 + 4);
             const float v[kRun] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int i = 0; i < kRun; i += 2) {
-                const float a0 = u0 + i < nwin ? rintf(__fmul_rn(c, v[i])) : 0.f;
-                const float a1 = u0 + i + 1 < nwin ? rintf(__fmul_rn(c, v[i + 1])) : 0.f;
-                h[i / 2] = __halves2half2(__float2half_rn(a0), __float2half_rn(a1));
-            }
+            for (int i = 0; i < kRun; ++i)
+                h[i] = TcElem<E>::from_int(u0 + i < nwin ? rintf(__fmul_rn(c, v[i])) : 0.f);
         } else {
 #pragma unroll
-            for (int i = 0; i < kRun / 2; ++i) h[i] = __float2half2_rn(0.f);
+            for (int i = 0; i < kRun; ++i) h[i] = TcElem<E>::from_int(0.f);
         }
-        *reinterpret_cast<uint4*>(out + u0) = *reinterpret_cast<const uint4*>(h);  // nseg % 8 == 0
+        // nseg % 8 == 0: one 16-byte (FP16) or 8-byte (FP8) store
+        if (sizeof(E) == 2) *reinterpret_cast<uint4*>(out + u0) = *reinterpret_cast<const uint4*>(h);
+        else *reinterpret_cast<uint2*>(out + u0) = *reinterpret_cast<const uint2*>(h);
     }
     if (threadIdx.x == 0) {
         if (bad || Mf > 3.402823466e38f) atomicOr(status, 1u);
@@ -258,11 +283,12 @@ __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, i
 // Eq. (2) on kernel f and its Toeplitz columns: row n = group * 256 + fl * P + p
 // of the K-major B operand holds k~_f[p + N - 1 - j] at column j.  CTA
 // (f, y) writes the rows of phases p = y, y + gridDim.y, ...
+template <typename E>
 __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, TcGeom g, int Kq,
-                                                 __half* __restrict__ bt, float* __restrict__ ck_tab,
+                                                 E* __restrict__ bt, float* __restrict__ ck_tab,
                                                  unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char tc_kern_smem[];
-    __half* kq = reinterpret_cast<__half*>(tc_kern_smem);  // kq[n + 64] = k~[n], zero outside [0, N)
+    E* kq = reinterpret_cast<E*>(tc_kern_smem);  // kq[n + 64] = k~[n], zero outside [0, N)
     __shared__ float red[8];
     const int f = blockIdx.x;  // 0 .. ngroups * G - 1 (past F: zero columns)
     const int kpadded = g.N + 128;
@@ -274,28 +300,29 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
         if (!bad && M > 0.f) c = __fdiv_rn((float)Kq, M);
         for (int n = threadIdx.x; n < kpadded; n += blockDim.x) {
             const int t = n - 64;
-            kq[n] = __float2half_rn((c > 0.f && t >= 0 && t < g.N) ? rintf(__fmul_rn(c, k[t])) : 0.f);
+            kq[n] = TcElem<E>::from_int((c > 0.f && t >= 0 && t < g.N) ? rintf(__fmul_rn(c, k[t])) : 0.f);
         }
         if (threadIdx.x == 0 && blockIdx.y == 0) {
             ck_tab[f] = bad ? __int_as_float(0x7fc00000) : c;
             if (bad) atomicOr(status, 1u);
         }
     } else {
-        for (int n = threadIdx.x; n < kpadded; n += blockDim.x) kq[n] = __float2half_rn(0.f);
+        for (int n = threadIdx.x; n < kpadded; n += blockDim.x) kq[n] = TcElem<E>::from_int(0.f);
     }
     __syncthreads();
     const int grp = f / g.G, fl = f % g.G;
-    __half* rows = bt + ((int64_t)grp * kTcN + (int64_t)fl * g.P) * g.Kpad;
+    E* rows = bt + ((int64_t)grp * kTcN + (int64_t)fl * g.P) * g.Kpad;
     const int half_row = g.Kpad / 2;
     for (int p = blockIdx.y; p < g.P; p += gridDim.y) {
-        __half2* row = reinterpret_cast<__half2*>(rows + (int64_t)p * g.Kpad);
+        E* row = rows + (int64_t)p * g.Kpad;
         for (int jj = threadIdx.x; jj < half_row; jj += blockDim.x) {
             const int j = 2 * jj;
             // taps n = p + N - 1 - j and n - 1; past the band they read the zero pad
             int n0 = p + g.N - 1 - j;
             n0 = n0 < -64 ? -64 : (n0 > g.N + 63 ? g.N + 63 : n0);
             const int n1 = n0 - 1 < -64 ? -64 : n0 - 1;
-            row[jj] = __halves2half2(kq[n0 + 64], kq[n1 + 64]);
+            row[j] = kq[n0 + 64];
+            row[j + 1] = kq[n1 + 64];
         }
     }
 }
@@ -375,7 +402,7 @@ __device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int 
 // runs across tiles; the accumulator is double-buffered in tensor memory
 // (2 x 256 columns) so that the epilogue of one tile overlaps the MMAs of the
 // next.
-template <bool RESIDENT_A>
+template <bool RESIDENT_A, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGeom g,
              const float* __restrict__ cs_tab, const float* __restrict__ ck_tab, float* __restrict__ y,
@@ -454,7 +481,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (*(volatile int*)&abort_sh) break;
                     const uint32_t st = ring + (uint32_t)s * stage_bytes;
                     const uint32_t fb = smem_u32(&full_bar[s]);
-                    const int j0 = kt * kTcK;
+                    const int j0 = kt * g.ktile;
                     mbar_expect_tx(fb, stage_bytes);
                     if (!RESIDENT_A) tma_load_2d(st + kTcBBytes, &tmA, j0 % g.P, arow0 + j0 / g.P, fb);
                     tma_load_2d(st, &tmB, j0, grp * kTcN, fb);
@@ -496,8 +523,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const uint32_t sb = ring + (uint32_t)s * stage_bytes;
                     const uint32_t sa = RESIDENT_A ? abase + (uint32_t)kt * 128u : sb + kTcBBytes;
 #pragma unroll
-                    for (int k = 0; k < kTcK / 16; ++k)
-                        umma_f16(acc, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
+                    for (int k = 0; k < 4; ++k) {  // four 32-byte K steps per 128-byte row
+                        if (F8) umma_f8(acc, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
+                        else umma_f16(acc, sdesc_sw128(sa + 32u * k), sdesc_sw128(sb + 32u * k), (kt | k) != 0);
+                    }
                     umma_commit(smem_u32(&empty_bar[s]));
                 }
                 umma_commit(smem_u32(&accf_bar[a]));  // this tile's MMAs done
@@ -569,36 +598,42 @@ EncodeTiledFn encode_fn() {
 
 // 2-D FP16 map: inner extent `inner` (contiguous), `rows` rows `pitch` bytes
 // apart, box 64 x box_rows, 128-byte swizzle.
-bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch, uint32_t box_rows) {
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch, uint32_t box_rows,
+               int esize) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {inner, rows};
     const cuuint64_t strides[1] = {pitch};
-    const cuuint32_t box[2] = {(cuuint32_t)kTcK, box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows};  // one 128-byte row
     const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    return fn(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-bool tc_geometry(int64_t L, int F, int N, TcGeom* g) {
-    if (L < 1 || F < 1 || N < 1 || N > kTcMaxN || F > kTcMaxF) return false;
-    g->P = F == 1 ? 256 : (F == 2 ? 128 : 64);
+bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g) {
+    if (L < 1 || F < 1 || N < 1 || N > kTcMaxN || F > kTcMaxF || (esize != 1 && esize != 2)) return false;
+    g->esize = esize;
+    g->ktile = 128 / esize;  // a K slice is one 128-byte row
+    // P phases per row: 128-byte rows (P = 64 FP16 or 128 FP8 samples) keep the
+    // whole Toeplitz operand resident; one or two kernels use longer rows
+    const int prow = 128 / esize;
+    g->P = F == 1 ? 256 : (F == 2 ? (prow > 128 ? prow : 128) : prow);
     g->G = kTcN / g->P;
     g->F = F;
     g->N = N;
     g->ngroups = (F + g->G - 1) / g->G;
-    g->Kpad = ((N + g->P - 1) + kTcK - 1) / kTcK * kTcK;
-    g->ktiles = g->Kpad / kTcK;
+    g->Kpad = ((N + g->P - 1) + g->ktile - 1) / g->ktile * g->ktile;
+    g->ktiles = g->Kpad / g->ktile;
     g->T = kTcM * g->P;
     g->out_len = L + N - 1;
     g->nb = (g->out_len + g->T - 1) / g->T;
     g->seg_rows = ((int64_t)g->T + g->Kpad + g->P - 1) / g->P;
     g->ldy = g->out_len;
     const int budget = kTcSmemCap - 1024;  // data bytes after the 1024-byte alignment slack
-    if (g->P == 64) {
+    if (g->P * esize == 128) {
         g->a_loads = (kTcM - 1 + g->ktiles + kTcABoxRows - 1) / kTcABoxRows;
         g->abuf_bytes = g->a_loads * (int)kTcABoxBytes;
         g->stages = (budget - (int)kTcStageOut - 2 * g->abuf_bytes) / (int)kTcBBytes;
@@ -610,44 +645,62 @@ bool tc_geometry(int64_t L, int F, int N, TcGeom* g) {
     if (g->stages > kTcMaxStages) g->stages = kTcMaxStages;
     if (g->stages < 2) return false;
     g->smem_bytes = (int)kTcStageOut +
-                    (g->P == 64 ? 2 * g->abuf_bytes + g->stages * (int)kTcBBytes
-                                : g->stages * (int)(kTcABytes + kTcBBytes)) + 1024;
+                    (g->P * esize == 128 ? 2 * g->abuf_bytes + g->stages * (int)kTcBBytes
+                                         : g->stages * (int)(kTcABytes + kTcBBytes)) + 1024;
     return true;
 }
 
-size_t tc_seg_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)(g.nb * g.seg_rows * g.P); }
-size_t tc_b_bytes(const TcGeom& g) { return sizeof(__half) * (size_t)g.ngroups * kTcN * (size_t)g.Kpad; }
+size_t tc_seg_bytes(const TcGeom& g) { return (size_t)g.esize * (size_t)(g.nb * g.seg_rows * g.P); }
+size_t tc_b_bytes(const TcGeom& g) { return (size_t)g.esize * (size_t)g.ngroups * kTcN * (size_t)g.Kpad; }
 
-cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
-                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st) {
+template <typename E>
+static cudaError_t launch_prep_e(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq,
+                                 void* seg, void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status,
+                                 cudaStream_t st) {
     const size_t wsm = sizeof(float) * (size_t)((g.T + g.N - 1 + kRun - 1) / kRun * kRun);
     static size_t wsm_set = 48 * 1024;
     if (wsm > wsm_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_quant, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_quant<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
         if (e != cudaSuccess) return e;
         wsm_set = kTcSmemCap;
     }
-    k_tc_quant<<<(unsigned)g.nb, 256, wsm, st>>>(s, L, g, Sq, (__half*)seg, cs_tab, cs_out, status);
-    k_tc_kern<<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(__half) * (size_t)(g.N + 128),
-                st>>>(kb, g, Kq, (__half*)bt, ck_tab, status);
+    k_tc_quant<E><<<(unsigned)g.nb, 256, wsm, st>>>(s, L, g, Sq, (E*)seg, cs_tab, cs_out, status);
+    k_tc_kern<E><<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(E) * (size_t)(g.N + 128), st>>>(
+        kb, g, Kq, (E*)bt, ck_tab, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
+                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st) {
+    if (g.esize == 1) return launch_prep_e<uint8_t>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, ck_tab, cs_out, status, st);
+    return launch_prep_e<__half>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, ck_tab, cs_out, status, st);
+}
+
+template <bool RA, bool F8>
+static void launch_mma_e(unsigned grid, const TcGeom& g, const CUtensorMap& ma, const CUtensorMap& mb,
+                         const float* cs_tab, const float* ck_tab, float* y, int32_t* yq, unsigned* status,
+                         cudaStream_t st) {
+    k_tc_mma<RA, F8><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
 }
 
 cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* cs_tab, const float* ck_tab,
                           float* y, int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed) {
     *encode_failed = false;
+    const bool resident = g.P * g.esize == 128;
     CUtensorMap ma, mb;
-    if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * 2,
-                   g.P == 64 ? kTcABoxRows : kTcM) ||
-        !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * 2, kTcN)) {
+    if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * g.esize,
+                   resident ? kTcABoxRows : kTcM, g.esize) ||
+        !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * g.esize, kTcN, g.esize)) {
         *encode_failed = true;
         return cudaErrorInvalidValue;
     }
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
+        cudaError_t e = cudaSuccess;
+        void (*ks[4])(CUtensorMap, CUtensorMap, TcGeom, const float*, const float*, float*, int32_t*, unsigned*) = {
+            k_tc_mma<true, false>, k_tc_mma<false, false>, k_tc_mma<true, true>, k_tc_mma<false, true>};
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -659,10 +712,13 @@ cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, cons
     }
     const int64_t nsets = g.nb * g.ngroups;
     const unsigned grid = (unsigned)(nsets < sms ? nsets : sms);
-    if (g.P == 64)
-        k_tc_mma<true><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
-    else
-        k_tc_mma<false><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
+    if (g.esize == 1) {
+        if (resident) launch_mma_e<true, true>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+        else launch_mma_e<false, true>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+    } else {
+        if (resident) launch_mma_e<true, false>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+        else launch_mma_e<false, false>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+    }
     return cudaGetLastError();
 }
 

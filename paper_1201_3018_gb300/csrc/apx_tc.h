@@ -19,15 +19,15 @@ namespace apx {
 
 // Tensor-core time-domain core (filterbank).  A tile is kTcM rows of P output
 // phases by kTcN = G kernels x P phases; K runs over the Toeplitz band in
-// slices of kTcK.
+// slices of one 128-byte row (64 FP16 or 128 FP8 elements).
 constexpr int kTcSmemCap = 227 * 1024 - 1024;  // dynamic shared memory cap (static needs the rest)
 constexpr int kTcM = 128;
 constexpr int kTcN = 256;
-constexpr int kTcK = 64;
 constexpr int kTcMaxStages = 8;
 constexpr int kTcMaxN = 16384;
 constexpr int kTcMaxF = 1024;
 constexpr int kTcMaxQ = 2048;              // |q| <= 2048 is exact in FP16
+constexpr int kTcMaxQ8 = 16;               // |q| <= 16 is exact in FP8 E4M3
 constexpr long long kTcExactSum = 1LL << 24;  // FP32 holds every integer up to 2^24
 
 struct TcGeom {
@@ -36,8 +36,10 @@ struct TcGeom {
     int F;            // kernels
     int N;            // taps per kernel
     int ngroups;      // ceil(F / G)
-    int Kpad;         // N + P - 1 rounded up to kTcK
-    int ktiles;       // Kpad / kTcK
+    int esize;        // operand bytes: 2 (FP16) or 1 (FP8 E4M3, S_q and K_q <= 16)
+    int ktile;        // elements per K slice, 128 / esize
+    int Kpad;         // N + P - 1 rounded up to ktile
+    int ktiles;       // Kpad / ktile
     int T;            // outputs per block, kTcM * P
     int64_t out_len;  // L + N - 1
     int64_t ldy;      // row pitch of the outputs (elements)
@@ -49,7 +51,7 @@ struct TcGeom {
     int smem_bytes;   // dynamic shared memory of the GEMM kernel
 };
 
-bool tc_geometry(int64_t L, int F, int N, TcGeom* g);
+bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g);
 size_t tc_seg_bytes(const TcGeom& g);
 size_t tc_b_bytes(const TcGeom& g);
 // Block companding into FP16 segments and the kernels' Toeplitz columns.

@@ -28,7 +28,7 @@ def run_gpu(ctx, s, kb, Sq, Kq, pad=0):
     L = len(s)
     out_len = L + N - 1
     ldy = (out_len + 3) // 4 * 4 + pad
-    T, nb = apx.filterbank_blocks(L, F, N)
+    T, nb = apx.filterbank_blocks(L, F, N, Sq, Kq)
     sd = torch.from_numpy(s).cuda()
     kd = torch.from_numpy(np.ascontiguousarray(kb)).cuda()
     y = torch.full((F, ldy), float("nan"), device="cuda")
@@ -50,8 +50,12 @@ def check_blocks(y, yq, cs, yo, yqo, cso, T, blocks):
         np.testing.assert_allclose(y[:, sl], yo[:, sl], rtol=1e-6, atol=0)
 
 
-CASES = [  # L, F, N, Sq, Kq
+CASES = [  # L, F, N, Sq, Kq (S_q, K_q <= 16: FP8 operands)
     (20000, 5, 100, 127, 127),     # P = 64, three blocks, ragged tail, partial kernel group
+    (50000, 5, 100, 16, 16),       # FP8: P = 128, partial group of two
+    (70000, 1, 300, 16, 9),        # FP8, one kernel: P = 256
+    (40000, 2, 1023, 12, 16),      # FP8, two kernels, N + P - 1 not a multiple of 128
+    (20000, 3, 16384, 16, 16),     # FP8, the longest kernel
     (70000, 1, 300, 200, 200),     # P = 256
     (5000, 2, 1, 2048, 2048),      # P = 128, one tap
     (9000, 3, 1023, 127, 127),     # N + P - 1 not a multiple of 64
