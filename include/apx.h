@@ -233,10 +233,12 @@ void apx_graph_destroy(apx_graph* graph);
  * c_s = S_q / ||window||_inf; kernel f is quantized once with
  * c_k = K_q / ||k_f||_inf (Eq. 2, round half to even on the FP32 product); the
  * integer convolution is exact; y = r~ / (c_s c_k) (Eq. 16).  The exact
- * integer arithmetic runs on the tensor cores (FP16 integers, FP32
- * accumulation), which is exact because N * S_q * K_q <= 2^24; it replaces the
- * FP64 packing of Section III, whose gain does not carry over to a GPU whose
- * FP64 rate is a small fraction of its FP32 and tensor rates.
+ * integer arithmetic runs on the tensor cores (FP16 integers, or FP8 E4M3
+ * integers when S_q, K_q <= 16, with FP32 accumulation), which is exact because
+ * every companded integer is exact in the operand type and N * S_q * K_q <=
+ * 2^24; it replaces the FP64 packing of Section III, whose gain does not carry
+ * over to a GPU whose FP64 rate is a small fraction of its FP32 and tensor
+ * rates.
  *   s_in     : device, L samples (FP32)
  *   k_bank   : device, F x N taps, row-major (FP32)
  *   S_q, K_q : 1 .. 2048 with N * S_q * K_q <= 2^24, else APX_ERR_RANGE
@@ -244,12 +246,14 @@ void apx_graph_destroy(apx_graph* graph);
  *              t < L+N-1; ldy >= L+N-1, a multiple of 4, y_out 16-byte aligned
  *   yq_out   : NULL or device int32 like y_out: the integer outputs r~
  *   block_cs : NULL or device, one float per block: c_s (0 for an all-zero window)
- * T = 128 * P outputs per block with P = 256 (F = 1), 128 (F = 2) or 64 (F >= 3);
- * the number of blocks is ceil((L+N-1) / T).  Limits: F <= 1024, N <= 16384
+ * T = 128 * P outputs per block with P = 256 (F = 1), 128 (F = 2) or 64 (F >= 3)
+ * for FP16 operands and P = 256 (F = 1) or 128 (F >= 2) for FP8 operands; the
+ * number of blocks is ceil((L+N-1) / T).  Limits: F <= 1024, N <= 16384
  * (APX_ERR_ARG beyond).  A window holding a non-finite sample gives zero
  * outputs for its block and APX_ERR_NONFINITE from the next apx_sync.  The
- * context's filterbank workspace (about 2.3 bytes per output of one kernel
- * plus the FP16 Toeplitz columns) is reused by the next call on any stream.
+ * context's filterbank workspace (about 2.3 bytes per output of one kernel in
+ * FP16, half that in FP8, plus the Toeplitz columns and one float per block and
+ * kernel) is reused by the next call on any stream.
  * Errors: APX_ERR_ARG, APX_ERR_RANGE, APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA. */
 int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_bank, int32_t F, int32_t N,
                    int32_t S_q, int32_t K_q, float* y_out, int64_t ldy, int32_t* yq_out, float* block_cs,

@@ -35,7 +35,7 @@ struct apx_ctx {
     int64_t launches = 0;
     DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
-    DevBuf tc_seg, tc_b, tc_cs, tc_ck;  // filterbank: FP16 block segments, Toeplitz B, c_s per block, c_k per kernel
+    DevBuf tc_seg, tc_b, tc_cs, tc_inv;  // filterbank: block segments, Toeplitz B, c_s per block, 1/(c_s c_k) per block and kernel
     DevBuf bhost;                       // batched calls from host buffers: device copies of inputs and outputs
     cudaStream_t hp_in = nullptr;       // calls from host buffers: the signal's copy stream
     std::vector<cudaEvent_t> hp_ev;     // and its events
@@ -719,7 +719,7 @@ void apx_destroy(apx_ctx* c) {
         cudaDeviceSynchronize();
         DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
                          &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab,
-                         &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_ck, &c->bhost};
+                         &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_inv, &c->bhost};
         for (DevBuf* b : all) release(c, *b);
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->hp_in) cudaStreamDestroy(c->hp_in);
@@ -959,21 +959,21 @@ extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const 
     if (!rc) rc = ensure(ctx, ctx->tc_seg, tc_seg_bytes(g));
     if (!rc) rc = ensure(ctx, ctx->tc_b, tc_b_bytes(g));
     if (!rc) rc = ensure(ctx, ctx->tc_cs, sizeof(float) * (size_t)g.nb);
-    if (!rc) rc = ensure(ctx, ctx->tc_ck, sizeof(float) * (size_t)g.ngroups * g.G);
+    if (!rc) rc = ensure(ctx, ctx->tc_inv, sizeof(float) * (size_t)g.nb * g.ngroups * g.G);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     {
         Trace t(ctx, st, APX_PHASE_TC_PREP);
         e = launch_tc_prep(g, s_in, L, k_bank, S_q, K_q, ctx->tc_seg.p, ctx->tc_b.p, (float*)ctx->tc_cs.p,
-                           (float*)ctx->tc_ck.p, block_cs, (unsigned*)ctx->flags.p, st);
+                           (float*)ctx->tc_inv.p, block_cs, (unsigned*)ctx->flags.p, st);
     }
     if (e != cudaSuccess) return cuda_status(e);
     bool enc_failed = false;
     {
         Trace t(ctx, st, APX_PHASE_TC_MMA);
-        e = launch_tc_mma(g, ctx->tc_seg.p, ctx->tc_b.p, (const float*)ctx->tc_cs.p, (const float*)ctx->tc_ck.p, y_out,
-                          yq_out, (unsigned*)ctx->flags.p, st, &enc_failed);
+        e = launch_tc_mma(g, ctx->tc_seg.p, ctx->tc_b.p, (const float*)ctx->tc_inv.p, y_out, yq_out,
+                          (unsigned*)ctx->flags.p, st, &enc_failed);
     }
     if (enc_failed) return APX_ERR_CUDA;
     if (e == cudaSuccess) ctx->launches += 3;

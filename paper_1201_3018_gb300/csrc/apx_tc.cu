@@ -26,13 +26,15 @@
 //   k_tc_quant  one CTA per block: ||window||_inf, c_s, companding into the
 //               block's FP16 segment (Eq. 2), c_s to the block table.
 //   k_tc_kern   one CTA per kernel: c_k, companding, the Toeplitz columns of B
-//               (K-major, FP16).
+//               (K-major, FP16 or FP8), and the Eq. (16) factors
+//               fl32(1 / (c_s c_k)) of the kernel for every block.
 //   k_tc_mma    persistent, one CTA per SM over the (block, kernel group)
 //               tiles: warp 0 streams operands with TMA into a shared-memory
-//               ring, warp 1 issues tcgen05.mma (M 128, N 256, K 16, FP32
-//               accumulators in tensor memory, double-buffered), warps 2-5
-//               read the accumulators back with tcgen05.ld, scale by
-//               (c_s c_k)^-1 (Eq. 16) and store.
+//               ring, warp 1 issues tcgen05.mma (M 128, N 256, K 16 in FP16
+//               or 32 in FP8, FP32 accumulators in tensor memory,
+//               double-buffered), warps 2-5 read the accumulators back with
+//               tcgen05.ld, scale them (Eq. 16) and write them out with TMA
+//               tensor stores.
 //
 // With P = 64 a row of S is exactly one 128-byte swizzle row, and the A slice
 // of K step kt is rows kt .. kt+127 of S: the whole A operand of a tile (its
@@ -52,7 +54,7 @@ namespace apx {
 
 namespace {
 
-constexpr int kTcEpiWarps = 4;   // one per tensor-memory lane quarter
+constexpr int kTcEpiWarps = 4;   // one per tensor-memory lane quarter (warp % 4 selects the quarter)
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t kTcABytes = kTcM * 128;  // a K slice: one 128-byte row per operand row
 constexpr uint32_t kTcBBytes = kTcN * 128;
@@ -162,7 +164,31 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[3
         : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Wait for this thread's tcgen05.ld to land.  The registers are operands so
+// that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Bulk tensor store of a staged shared-memory box (one bulk group per call).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n\t"
+        "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(z), "r"(src)
+        : "memory");
+}
+// The bulk stores of this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and their writes are performed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ float block_max_abs(const float* x, int64_t lo, int64_t hi, int64_t L, bool* bad,
                                                float* red) {
@@ -283,10 +309,16 @@ __global__ void __launch_bounds__(256) k_tc_quant(const float* __restrict__ s, i
 // Eq. (2) on kernel f and its Toeplitz columns: row n = group * 256 + fl * P + p
 // of the K-major B operand holds k~_f[p + N - 1 - j] at column j.  CTA
 // (f, y) writes the rows of phases p = y, y + gridDim.y, ...
+//
+// CTA (f, 0) also writes fl32(1 / (c_s c_k)) of kernel f for every block b to
+// inv_tab[b * ngroups * G + f] (0 for an all-zero or non-finite window or
+// kernel, and for the zero columns past F): the epilogue's Eq. (16) factor,
+// computed once here in FP64 (c_s c_k is exact in FP64) instead of per tile.
+// The block table cs_tab is complete: k_tc_quant runs before on the stream.
 template <typename E>
 __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, TcGeom g, int Kq,
-                                                 E* __restrict__ bt, float* __restrict__ ck_tab,
-                                                 unsigned* __restrict__ status) {
+                                                 E* __restrict__ bt, const float* __restrict__ cs_tab,
+                                                 float* __restrict__ inv_tab, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char tc_kern_smem[];
     E* kq = reinterpret_cast<E*>(tc_kern_smem);  // kq[n + 64] = k~[n], zero outside [0, N)
     __shared__ float red[8];
@@ -302,12 +334,16 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
             const int t = n - 64;
             kq[n] = TcElem<E>::from_int((c > 0.f && t >= 0 && t < g.N) ? rintf(__fmul_rn(c, k[t])) : 0.f);
         }
-        if (threadIdx.x == 0 && blockIdx.y == 0) {
-            ck_tab[f] = bad ? __int_as_float(0x7fc00000) : c;
-            if (bad) atomicOr(status, 1u);
-        }
+        if (threadIdx.x == 0 && blockIdx.y == 0 && bad) atomicOr(status, 1u);
     } else {
         for (int n = threadIdx.x; n < kpadded; n += blockDim.x) kq[n] = TcElem<E>::from_int(0.f);
+    }
+    if (blockIdx.y == 0) {
+        const int64_t gs = (int64_t)g.ngroups * g.G;
+        for (int64_t b = threadIdx.x; b < g.nb; b += blockDim.x) {
+            const float cs = cs_tab[b];
+            inv_tab[b * gs + f] = (cs > 0.f && c > 0.f && !bad) ? (float)(1.0 / ((double)cs * (double)c)) : 0.f;
+        }
     }
     __syncthreads();
     const int grp = f / g.G, fl = f % g.G;
@@ -327,73 +363,68 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
     }
 }
 
-// Epilogue of one tile for one warp (TMEM lane quarter lq, chunk parity
-// `half`): read the 128 x 256 FP32 accumulator rows of this quarter in 32-column
-// chunks, scale by (c_s c_k)^-1 (Eq. 16), stage each 32 x 32 chunk in the warp's
-// 4 KB buffer (16-byte slot i of row r at r * 128 + ((i ^ (r & 7)) * 16):
-// conflict-free both ways) and store four whole 128-byte rows per instruction.
-__device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int grp, uint32_t acc0, uint32_t stg,
-                                              int lane, int lq, int half, const float* __restrict__ cs_tab,
-                                              const float* __restrict__ ck_tab, float* __restrict__ y,
+// Epilogue of one tile for one warp (TMEM lane quarter lq): read the warp's
+// 32 accumulator rows in 32-column chunks (chunk ch is columns 32 ch .. 32 ch
+// + 31, kernel fl = ch / (P / 32)), the load of the next chunk in flight while
+// this one is processed; scale by the block's and kernel's (c_s c_k)^-1
+// (Eq. 16); stage the 32 x 32 chunk in the warp's 4 KB buffer in the 128-byte
+// swizzled layout (16-byte slot i of row r at r * 128 + ((i ^ (r & 7)) * 16):
+// conflict-free writes) and write it with one TMA store of the box (columns
+// c .. c + 31 of P, time rows row0 .. row0 + 31, kernel f) of the output map.
+// The map covers the out_len / P whole rows of each kernel, so TMA drops rows
+// past them; the one partial row at the end (out_len % P outputs) is written
+// by its lane with plain stores.
+__device__ __forceinline__ void epilogue_tile(const TcGeom& g, const CUtensorMap* tmY, int64_t blk, int grp,
+                                              uint32_t acc0, uint32_t stg, int lane, int lq,
+                                              const float* __restrict__ inv_tab, float* __restrict__ y,
                                               int32_t* __restrict__ yq, unsigned* status) {
-    const int row = lq * 32 + lane;
-    const int rr = lane >> 3, ii = lane & 7;
+    const int64_t row0 = blk * kTcM + lq * 32;  // first time row of this warp's quarter
+    const int64_t rows_full = g.out_len / g.P;  // rows the output map covers
+    const int64_t tail_row = (g.out_len % g.P) ? rows_full : -1;
     const uint32_t acc = acc0 + ((uint32_t)(lq * 32) << 16);
-            const float cs = cs_tab[blk];
-            for (int fl = 0; fl < g.G; ++fl) {
-                const int f = grp * g.G + fl;
-                if (f >= g.F) break;
-                // (c_s c_k)^-1 once per warp (FP64 is a small fraction of the FP32 rate)
-                float inv = 0.f;
-                if (lane == 0) {
-                    const float ck = ck_tab[f];
-                    if (cs > 0.f && ck > 0.f) inv = (float)(1.0 / ((double)cs * (double)ck));
-                }
-                inv = __shfl_sync(0xffffffffu, inv, 0);
-                float* yf = y + (int64_t)f * g.ldy;
-                int32_t* qf = yq ? yq + (int64_t)f * g.ldy : nullptr;
-                for (int c = 32 * half; c < g.P; c += 32 * (kTcEpiWarps / 4)) {
-                    uint32_t r[32];
-                    if (!APX_IN_BOUNDS(fl * g.P + c + 32 <= kTcN, status)) continue;  // warp-uniform
-                    tmem_ld32_nowait(acc + (uint32_t)(fl * g.P + c), r);
-                    tmem_wait_ld();
-                    // scale (Eq. 16) and stage this lane's row
+    const int nf = g.F - grp * g.G < g.G ? g.F - grp * g.G : g.G;  // kernels of this group
+    const float inv_l = lane < nf ? inv_tab[blk * (int64_t)(g.ngroups * g.G) + grp * g.G + lane] : 0.f;
+    const int cpk = g.P / 32;  // chunks per kernel
+    const int nchunks = nf * cpk;
+    uint32_t rn[32];
+    if (!APX_IN_BOUNDS(nchunks * 32 <= kTcN, status)) return;
+    tmem_ld32_nowait(acc, rn);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int fl = ch / cpk, c = (ch - fl * cpk) * 32;
+        const int f = grp * g.G + fl;
+        uint32_t r[32];
+        tmem_wait_ld(rn);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float v[4];
+        for (int i = 0; i < 32; ++i) r[i] = rn[i];
+        if (ch + 1 < nchunks) tmem_ld32_nowait(acc + (uint32_t)(32 * (ch + 1)), rn);
+        const float inv = __shfl_sync(0xffffffffu, inv_l, fl);
+        // the previous chunk's store has read the staging buffer
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
-                        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                         stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
-                                     "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-                                     : "memory");
-                    }
-                    if (qf) {  // integer outputs (a test aid): straight from the row
-                        const int64_t t0 = blk * (int64_t)g.T + (int64_t)row * g.P + c;
-                        for (int i = 0; i < 32 && t0 + i < g.out_len; ++i)
-                            qf[t0 + i] = __float2int_rn(__uint_as_float(r[i]));
-                    }
-                    __syncwarp();
-                    // four whole rows (4 x 128 contiguous bytes) per store instruction
+        for (int i = 0; i < 8; ++i) {
+            float v[4];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int srow = 4 * j + rr;
-                        float4 v;
-                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                                     : "r"(stg + (uint32_t)srow * 128u + (uint32_t)((ii ^ (srow & 7)) * 16))
-                                     : "memory");
-                        const int64_t t = blk * (int64_t)g.T + (int64_t)(lq * 32 + srow) * g.P + c + 4 * ii;
-                        if (t + 4 <= g.out_len) {
-                            __stcs(reinterpret_cast<float4*>(yf + t), v);
-                        } else {
-                            const float w[4] = {v.x, v.y, v.z, v.w};
-                            for (int e = 0; e < 4 && t + e < g.out_len; ++e) yf[t + e] = w[e];
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
+            for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
+                         "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                         : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
+        __syncwarp();
+        if (lane == 0 && row0 < rows_full) tma_store_3d(tmY, stg, c, (int)row0, f);
+        const int64_t t0 = (row0 + lane) * g.P + c;  // this lane's first output
+        if (row0 + lane == tail_row) {
+            float* yf = y + (int64_t)f * g.ldy;
+            for (int i = 0; i < 32 && t0 + i < g.out_len; ++i) yf[t0 + i] = __fmul_rn(__uint_as_float(r[i]), inv);
+        }
+        if (yq && t0 < g.out_len) {
+            // integer outputs (a test aid): straight from the row
+            int32_t* qf = yq + (int64_t)f * g.ldy;
+            for (int i = 0; i < 32 && t0 + i < g.out_len; ++i) qf[t0 + i] = __float2int_rn(__uint_as_float(r[i]));
+        }
+    }
 }
 
 // Persistent: CTA c takes tiles u = c, c + gridDim.x, ...; tile u is block
@@ -404,9 +435,9 @@ __device__ __forceinline__ void epilogue_tile(const TcGeom& g, int64_t blk, int 
 // next.
 template <bool RESIDENT_A, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGeom g,
-             const float* __restrict__ cs_tab, const float* __restrict__ ck_tab, float* __restrict__ y,
-             int32_t* __restrict__ yq, unsigned* __restrict__ status) {
+    k_tc_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             const __grid_constant__ CUtensorMap tmY, const TcGeom g, const float* __restrict__ inv_tab,
+             float* __restrict__ y, int32_t* __restrict__ yq, unsigned* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], accf_bar[2], acce_bar[2],
         afull_bar[2], aempty_bar[2];
@@ -534,10 +565,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (!ok) break;
             }
         }
-    } else {  // epilogue: warps 2.., TMEM lane quarter warp % 4; with 8 epilogue warps
-              // the two warps of a quarter take alternate 32-column chunks
+    } else {  // epilogue: warps 2-5, tensor-memory lane quarter warp % 4
         const int lq = warp & 3;
-        const int half = (warp - 2) >> 2;
         int local = 0;
         for (int64_t u = blockIdx.x; u < nsets; u += gridDim.x, ++local) {
             const int a = local & 1;
@@ -550,14 +579,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             const int64_t blk = u / g.ngroups;
             const int grp = (int)(u % g.ngroups);
-            epilogue_tile(g, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * 4096u, lane,
-                          lq, half, cs_tab, ck_tab, y, yq, status);
+            epilogue_tile(g, &tmY, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * 4096u,
+                          lane, lq, inv_tab, y, yq, status);
             // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
             tc_fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[a]))
                                         : "memory");
         }
+        if (lane == 0) bulk_wait_all();  // the output stores are done before the CTA exits
     }
 
     tc_fence_before();
@@ -611,6 +641,24 @@ bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The FP32 outputs as a 3-D map for the epilogue's stores: P phases (inner), the
+// out_len / P whole rows of a kernel (row pitch P floats), F kernels (pitch ldy
+// floats); box 32 x 32 x 1 (one 32-row, 128-byte-wide chunk), 128-byte swizzle.
+// With fewer than P outputs there is no whole row: the map gets one row and the
+// epilogue stores nothing through it.
+bool encode_out(CUtensorMap* m, float* y, const TcGeom& g) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const int64_t rows = g.out_len / g.P;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)(rows > 0 ? rows : 1), (cuuint64_t)g.F};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4u, (cuuint64_t)g.ldy * 4u};
+    const cuuint32_t box[3] = {32, 32, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g) {
@@ -655,7 +703,7 @@ size_t tc_b_bytes(const TcGeom& g) { return (size_t)g.esize * (size_t)g.ngroups 
 
 template <typename E>
 static cudaError_t launch_prep_e(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq,
-                                 void* seg, void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status,
+                                 void* seg, void* bt, float* cs_tab, float* inv_tab, float* cs_out, unsigned* status,
                                  cudaStream_t st) {
     const size_t wsm = sizeof(float) * (size_t)((g.T + g.N - 1 + kRun - 1) / kRun * kRun);
     static size_t wsm_set = 48 * 1024;
@@ -666,38 +714,39 @@ static cudaError_t launch_prep_e(const TcGeom& g, const float* s, int64_t L, con
     }
     k_tc_quant<E><<<(unsigned)g.nb, 256, wsm, st>>>(s, L, g, Sq, (E*)seg, cs_tab, cs_out, status);
     k_tc_kern<E><<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(E) * (size_t)(g.N + 128), st>>>(
-        kb, g, Kq, (E*)bt, ck_tab, status);
+        kb, g, Kq, (E*)bt, cs_tab, inv_tab, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
-                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st) {
-    if (g.esize == 1) return launch_prep_e<uint8_t>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, ck_tab, cs_out, status, st);
-    return launch_prep_e<__half>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, ck_tab, cs_out, status, st);
+                           void* bt, float* cs_tab, float* inv_tab, float* cs_out, unsigned* status, cudaStream_t st) {
+    if (g.esize == 1) return launch_prep_e<uint8_t>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, inv_tab, cs_out, status, st);
+    return launch_prep_e<__half>(g, s, L, kb, Sq, Kq, seg, bt, cs_tab, inv_tab, cs_out, status, st);
 }
 
 template <bool RA, bool F8>
 static void launch_mma_e(unsigned grid, const TcGeom& g, const CUtensorMap& ma, const CUtensorMap& mb,
-                         const float* cs_tab, const float* ck_tab, float* y, int32_t* yq, unsigned* status,
+                         const CUtensorMap& my, const float* inv_tab, float* y, int32_t* yq, unsigned* status,
                          cudaStream_t st) {
-    k_tc_mma<RA, F8><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, g, cs_tab, ck_tab, y, yq, status);
+    k_tc_mma<RA, F8><<<grid, kTcThreads, (size_t)g.smem_bytes, st>>>(ma, mb, my, g, inv_tab, y, yq, status);
 }
 
-cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* cs_tab, const float* ck_tab,
+cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* inv_tab,
                           float* y, int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed) {
     *encode_failed = false;
     const bool resident = g.P * g.esize == 128;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, my;
     if (!encode_2d(&ma, seg, (uint64_t)g.P, (uint64_t)(g.nb * g.seg_rows), (uint64_t)g.P * g.esize,
                    resident ? kTcABoxRows : kTcM, g.esize) ||
-        !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * g.esize, kTcN, g.esize)) {
+        !encode_2d(&mb, bt, (uint64_t)g.Kpad, (uint64_t)g.ngroups * kTcN, (uint64_t)g.Kpad * g.esize, kTcN, g.esize) ||
+        !encode_out(&my, y, g)) {
         *encode_failed = true;
         return cudaErrorInvalidValue;
     }
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaSuccess;
-        void (*ks[4])(CUtensorMap, CUtensorMap, TcGeom, const float*, const float*, float*, int32_t*, unsigned*) = {
+        void (*ks[4])(CUtensorMap, CUtensorMap, CUtensorMap, TcGeom, const float*, float*, int32_t*, unsigned*) = {
             k_tc_mma<true, false>, k_tc_mma<false, false>, k_tc_mma<true, true>, k_tc_mma<false, true>};
         for (int i = 0; i < 4 && e == cudaSuccess; ++i)
             e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
@@ -713,11 +762,11 @@ cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, cons
     const int64_t nsets = g.nb * g.ngroups;
     const unsigned grid = (unsigned)(nsets < sms ? nsets : sms);
     if (g.esize == 1) {
-        if (resident) launch_mma_e<true, true>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
-        else launch_mma_e<false, true>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+        if (resident) launch_mma_e<true, true>(grid, g, ma, mb, my, inv_tab, y, yq, status, st);
+        else launch_mma_e<false, true>(grid, g, ma, mb, my, inv_tab, y, yq, status, st);
     } else {
-        if (resident) launch_mma_e<true, false>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
-        else launch_mma_e<false, false>(grid, g, ma, mb, cs_tab, ck_tab, y, yq, status, st);
+        if (resident) launch_mma_e<true, false>(grid, g, ma, mb, my, inv_tab, y, yq, status, st);
+        else launch_mma_e<false, false>(grid, g, ma, mb, my, inv_tab, y, yq, status, st);
     }
     return cudaGetLastError();
 }

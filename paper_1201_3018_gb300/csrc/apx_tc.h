@@ -55,10 +55,12 @@ bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g);
 size_t tc_seg_bytes(const TcGeom& g);
 size_t tc_b_bytes(const TcGeom& g);
 // Block companding into FP16 segments and the kernels' Toeplitz columns.
+// cs_tab: c_s per block; inv_tab: fl32(1 / (c_s c_k)) per block and kernel
+// slot (nb x ngroups * G floats).
 cudaError_t launch_tc_prep(const TcGeom& g, const float* s, int64_t L, const float* kb, int Sq, int Kq, void* seg,
-                           void* bt, float* cs_tab, float* ck_tab, float* cs_out, unsigned* status, cudaStream_t st);
+                           void* bt, float* cs_tab, float* inv_tab, float* cs_out, unsigned* status, cudaStream_t st);
 // The persistent tensor-core GEMM with the Eq. (16) epilogue.
-cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* cs_tab, const float* ck_tab,
-                          float* y, int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed);
+cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, const float* inv_tab, float* y,
+                          int32_t* yq, unsigned* status, cudaStream_t st, bool* encode_failed);
 
 }  // namespace apx
