@@ -383,7 +383,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
            "roofline_tc_mma": {"bound": "tensor", "achieved": useful / (mma8 * 1e-3) / 1e12, "peak": 2 * peak,
                                "unit": "TFLOP/s", "frac": useful / (mma8 * 1e-3) / 1e12 / (2 * peak),
                                "peak_source": "measured cuBLAS bf16 x 2 (nominal FP8 : FP16 dense ratio)",
-                               "kernel_ms": mma8}}
+                               "kernel_ms": mma8, "traffic": traffic_for("tc_mma_fp8")}}
     return {"workload": "filterbank: 2^22 N(0,1) samples, 32 Hann-windowed-sinc band-pass kernels of 1024 taps "
                         "(log-spaced 50 Hz - 20 kHz at 44.1 kHz), S_q = K_q = 127, FP16 integers on the tensor cores",
             "outputs_per_step": F * out_len, "value": F * out_len / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
