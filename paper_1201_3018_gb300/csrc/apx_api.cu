@@ -26,7 +26,26 @@ struct DevBuf {
 
 }  // namespace
 
-constexpr int kFlagWords = 1 + 2 * kMaxCand;  // status, claim[3], ready[3]
+// status, claim[3], ready[3], (pad), ticket counter (64-bit, words 8-9), job ready[kMaxJobs]
+constexpr int kMaxJobs = 40;
+constexpr int kFlagWords = 10 + kMaxJobs;
+// A single FFT-core call runs the kernel preparation inside the block kernel
+// when it has at least this many blocks (fewer CTAs would take the jobs one
+// after another); below, the two preparation launches run ahead of it.
+constexpr long long kFuseMinBlocks = 64;
+static_assert(kFlagWords * sizeof(unsigned) <= 512, "the static scratch holds 512 bytes of flag words");
+
+// Flag-word pointers of a call (ctx->flags or the static scratch).
+void set_flag_ptrs(Params& p, unsigned* flags) {
+    p.status = flags;
+    p.claim = flags + 1;
+    p.ready = flags + 1 + kMaxCand;
+    p.ticket = reinterpret_cast<unsigned long long*>(flags + 8);
+    p.jobready = flags + 10;
+}
+bool use_fused(const Params& p) {
+    return p.fft && p.P >= kFuseMinBlocks && prep_jobs_count(p.Wb, fft_threads(p.Wb)) <= kMaxJobs;
+}
 
 struct apx_ctx {
     int device = 0;
@@ -44,6 +63,7 @@ struct apx_ctx {
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
     int tw_wb = 0;          // W_block the twiddle tables were built for
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
+    unsigned long long tickets = 0;  // CTA tickets handed out by fused launches (the device counter's value)
     int stall_next = 0;     // test hook: pre-claim the next call's packed spectra
     // tracing
     bool profiling = false;
@@ -445,9 +465,9 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     if (rc) return rc;
 
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
-    p.status = (unsigned*)ctx->flags.p;
-    p.claim = (unsigned*)ctx->flags.p + 1;
-    p.ready = (unsigned*)ctx->flags.p + 1 + kMaxCand;
+    set_flag_ptrs(p, (unsigned*)ctx->flags.p);
+    p.fused = use_fused(p);
+    p.ticket_base = ctx->tickets;
     p.Hfull = (float2*)ctx->Hfull.p;
     p.ki = (KInfo*)ctx->ki.p;
     p.Ysub = (float2*)ctx->Ysub.p;
@@ -472,7 +492,8 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
             if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(stream);  // the host array goes out of scope
             if (e0 != cudaSuccess) return cuda_status(e0);
         }
-        {
+        e = cudaSuccess;
+        if (!p.fused) {
             Trace t(ctx, stream, APX_PHASE_SPECTRA);
             e = launch_spec(p, stream);
             if (e == cudaSuccess) e = launch_spec_combine(p, stream);
@@ -481,7 +502,8 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         if (e == cudaSuccess) {
             Trace t(ctx, stream, APX_PHASE_FFT);
             if (before_blocks) e = cudaStreamWaitEvent(stream, before_blocks, 0);
-            if (e == cudaSuccess) e = launch_fft(p, smem, stream);
+            if (e == cudaSuccess) e = p.fused ? launch_fft_fused(p, smem, stream) : launch_fft(p, smem, stream);
+            if (e == cudaSuccess && p.fused) ctx->tickets += fused_grid(p);
             ctx->launches += 1;
         }
     }
@@ -1061,8 +1083,8 @@ namespace {
 
 constexpr int kStaticWbMax = 8192;
 constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
-constexpr size_t kSOffFlags = 0;  // status, claim[3], ready[3]
-constexpr size_t kSOffKInfo = kSOffFlags + 256;
+constexpr size_t kSOffFlags = 0;  // the flag words (kFlagWords <= 64)
+constexpr size_t kSOffKInfo = kSOffFlags + 512;
 constexpr size_t kSOffHfull = kSOffKInfo + al256(sizeof(KInfo));
 constexpr size_t kSOffYsub = kSOffHfull + al256(sizeof(float2) * (kStaticWbMax / 2 + 1));
 constexpr size_t kSOffTw32 = kSOffYsub + al256(sizeof(float2) * kStaticWbMax);
@@ -1081,6 +1103,7 @@ struct StaticDevice {
     unsigned char* base = nullptr;  // device address of g_apx_scratch on this device
     int tw_wb = 0;                  // W_block the twiddle tables hold
     unsigned epoch = 0;             // call number (claims of on-demand spectra)
+    unsigned long long tickets = 0; // CTA tickets handed out by fused launches
 };
 std::mutex g_static_mu;
 StaticDevice g_static[64];
@@ -1118,6 +1141,8 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
         if (!sd.base) {  // first call on this device: the array's device address
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_apx_scratch) != cudaSuccess || !ptr) return APX_ERR_CUDA;
+            // the flag words start from zero (the ticket counter matches `tickets`)
+            if (cudaMemsetAsync(ptr, 0, kSOffKInfo, st) != cudaSuccess) return APX_ERR_CUDA;
             sd.base = (unsigned char*)ptr;
         }
         if (++sd.epoch == 0) sd.epoch = 1;
@@ -1152,9 +1177,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     p.fft = 1; p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
     p.P = pl.P; p.out_len = L + N - 1;
     p.r = r_out;
-    p.status = (unsigned*)(base + kSOffFlags);
-    p.claim = p.status + 1;
-    p.ready = p.status + 1 + kMaxCand;
+    set_flag_ptrs(p, (unsigned*)(base + kSOffFlags));
     p.epoch = epoch;
     p.ki = (KInfo*)(base + kSOffKInfo);
     p.Hfull = (float2*)(base + kSOffHfull);
@@ -1165,6 +1188,12 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)(base + kSOffHc + j * kSHcBytes);
     const size_t smem = fft_smem_bytes(p);
     if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
+    p.fused = use_fused(p);
+    if (p.fused) {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        p.ticket_base = g_static[dev].tickets;
+        g_static[dev].tickets += fused_grid(p);
+    }
 
     cudaError_t e = cudaSuccess;
     if (need_tw) {
@@ -1172,9 +1201,13 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
                                                           W_block);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = launch_spec(p, st);
-    if (e == cudaSuccess) e = launch_spec_combine(p, st);
-    if (e == cudaSuccess) e = launch_fft(p, smem, st);
+    if (e == cudaSuccess && !p.fused) e = launch_spec(p, st);
+    if (e == cudaSuccess && !p.fused) e = launch_spec_combine(p, st);
+    if (e == cudaSuccess) e = p.fused ? launch_fft_fused(p, smem, st) : launch_fft(p, smem, st);
+    if (e != cudaSuccess && p.fused) {  // not launched: its tickets were never taken
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        g_static[dev].tickets -= fused_grid(p);
+    }
     return cuda_status(e);
 }
 

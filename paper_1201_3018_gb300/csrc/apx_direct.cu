@@ -66,7 +66,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
-    __shared__ int s_ci;
+    __shared__ unsigned s_feas;
     __shared__ Params sp;
     const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
     const Params& p = BATCH ? sp : p0;
@@ -85,17 +85,8 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
 
     // Section IV.D: first candidate (in the Table 1 order) whose model SNR meets
     // the target; with a fixed quantiser the single candidate is taken.
-    if (threadIdx.x == 0) {
-        int ci = -1;
-        for (int c = 0; c < p.ncand; ++c)
-            if (!p.autosel || snr_feasible(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, p.cand[c].S, p.cand[c].K, p.thr)) {
-                ci = c;
-                break;
-            }
-        s_ci = ci;
-    }
-    __syncthreads();
-    const int ci = s_ci;
+    const unsigned feas = feasible_mask(p, pr.sig2, pr.Ms, ks.sig2k, ks.Mk, &s_feas);
+    const int ci = feas ? __ffs(feas) - 1 : -1;
 
     if (ci < 0 && p.full64) {
         // Full precision in FP64, Eq. (1) over the window, rounded once to FP32.

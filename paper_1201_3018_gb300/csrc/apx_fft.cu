@@ -1,11 +1,15 @@
 // apx_fft.cu -- the frequency-domain (FFT) block kernel.
 //
-// One CTA per overlap-save block, launched as the programmatic dependent of
-// k_spec (kernel statistics and the FP32 kernel spectrum).  Each CTA:
+// One CTA per overlap-save block.  The kernel preparation (kernel statistics
+// and the FP32 kernel spectrum, apx_prep.cuh) either ran in the launches
+// before (batched calls and single calls with few blocks: this kernel is their
+// programmatic dependent) or runs here: in a fused single call each CTA first
+// claims preparation jobs until none is left, so the preparation is spread
+// over the first CTAs to start and no launch waits for another.  Each CTA:
 //   1. fetches its W_block window into registers and computes the block
 //      statistics,
 //   2. starts the FP32 forward real FFT of the window (full precision is every
-//      block's fallback) before griddepcontrol.wait, overlapping k_spec,
+//      block's fallback) before it waits for the preparation,
 //   3. runs the Section IV.D selection; for a packing candidate it companded
 //      the block and checks the FFT error bound (reading c7) with the exact
 //      integer norms sum(s~^2) and ||kbar||_1, so rounding recovers the digits,
@@ -17,12 +21,11 @@
 // A packed candidate's FP64 spectrum is built on demand by the first CTA that
 // selects it; later CTAs wait for it with a bounded spin and report a timeout
 // in the status word instead of hanging.
-#include "apx_block.cuh"
-#include "apx_launch.h"
+#include "apx_prep.cuh"
 
 namespace apx {
 
-constexpr long long kSpinCycles = 2000000000LL;  // about one second at the maximum SM clock
+constexpr long long kSpinCycles = kPrepSpinCycles;
 
 // Thread t holds window samples 2(t + i NT) and 2(t + i NT) + 1 (pair t + i NT)
 // for pairs below W_block/2; other slots hold zeros, which leave the maximum,
@@ -57,8 +60,32 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int s_flag;
+    __shared__ unsigned s_feas;
+    __shared__ int s_job;
+    __shared__ long long s_ticket;
     __shared__ Params sp;
-    const long long i = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
+    // fused single call: tickets below nj are preparation jobs, the rest blocks
+    const int nj = (!BATCH && p0.fused) ? prep_jobs_count(p0.Wb, blockDim.x) : 0;
+    long long i;
+    if (BATCH) {
+        i = batch_enter(bt, sp);
+    } else if (nj) {
+        // a programmatic dependent of whatever ran before on the stream: its
+        // launch is prepared early, and nothing is read before that work is done
+        pdl_wait();
+        const long long t = prep_ticket(p0, &s_ticket);
+        if (t < 0 || t >= nj + p0.P) {  // the host's count of tickets is off: touch nothing
+            if (threadIdx.x == 0) atomicOr(p0.status, 4u);
+            return;
+        }
+        if (t < nj) {
+            prep_job(p0, (int)t, reinterpret_cast<float2*>(smem), sh, &s_job);
+            return;
+        }
+        i = t - nj;
+    } else {
+        i = blockIdx.x;
+    }
     const Params& p = BATCH ? sp : p0;
     const BlockGeom g = block_geom(p, i);
     float xv[kVals];
@@ -97,7 +124,14 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
         fft_smem<float2, false>(Zf, mf, p.tw32, p.ntab, p.status);
     }
 
-    pdl_wait();  // kernel statistics and FP32 kernel spectrum from the preparation launch
+    // kernel statistics and FP32 kernel spectrum: from the preparation launches,
+    // or from the preparation jobs of this launch
+    if (BATCH || !p.fused) {
+        pdl_wait();
+    } else if (!wait_jobs(p, 0, nj, &s_job)) {
+        store_constant(p, g, __int_as_float(0x7fc00000));
+        return;
+    }
     const float Mk = __ldcg(&p.ki->Mk);
     const int kbad = __ldcg(&p.ki->bad);
     const double sig2k = __ldcg(&p.ki->sig2k);
@@ -116,13 +150,10 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
     float cs = 0.f, ck = 0.f;
     double ferr = 0.0;
     bool have_window = false;
+    const unsigned feas = feasible_mask(p, sig2, m, sig2k, Mk, &s_feas);
     for (int c = 0; c < p.ncand; ++c) {
+        if (!((feas >> c) & 1u)) continue;
         const Cand& cd = p.cand[c];
-        if (threadIdx.x == 0) s_flag = !p.autosel || snr_feasible(sig2, m, sig2k, Mk, cd.S, cd.K, p.thr);
-        __syncthreads();
-        const int go = s_flag;
-        __syncthreads();
-        if (!go) continue;
         if (!have_window) { load_window_regs(p, g.start, xv); have_window = true; }
         const float cs_c = compand_factor(cd.S, m);
         const float ck_c = compand_factor(cd.K, Mk);
@@ -293,6 +324,22 @@ cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
     if (p.Wb / fft_threads(p.Wb) > 16)
         return launch_k(k_fft<32, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
     return launch_k(k_fft<16, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
+}
+
+// Fused single call: nj preparation CTAs ahead of the P block CTAs in one
+// launch, a programmatic dependent of the stream's previous work (the kernel
+// waits for it before reading anything).  Every CTA takes one ticket: the
+// caller advances its copy of the counter by the grid size.
+unsigned fused_grid(const Params& p) { return (unsigned)(p.P + prep_jobs_count(p.Wb, fft_threads(p.Wb))); }
+
+cudaError_t launch_fft_fused(const Params& p, size_t smem, cudaStream_t st) {
+    if (p.P <= 0) return cudaSuccess;
+    cudaError_t e = fft_attrs<false>();
+    if (e != cudaSuccess) return e;
+    const int nt = fft_threads(p.Wb);
+    const BatchTab none = {nullptr, nullptr, 0};
+    if (p.Wb / nt > 16) return launch_k(k_fft<32, false>, dim3(fused_grid(p)), dim3(nt), smem, st, true, p, none);
+    return launch_k(k_fft<16, false>, dim3(fused_grid(p)), dim3(nt), smem, st, true, p, none);
 }
 
 cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {

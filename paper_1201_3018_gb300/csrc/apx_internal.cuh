@@ -77,6 +77,10 @@ struct Params {
     unsigned* claim;      // FFT core, per candidate: last call that claimed building its spectrum
     unsigned* ready;      // FFT core, per candidate: last call whose spectrum is complete
     unsigned epoch;       // FFT core: this call's number (never 0)
+    int fused;            // FFT core, single call: the block kernel's first CTAs run the kernel preparation
+    unsigned long long* ticket;     // fused: CTA ticket counter (only grows)
+    unsigned long long ticket_base; // fused: its value before this launch
+    unsigned* jobready;   // fused, per preparation job: last call in which it completed
     int autosel;          // 1: per-block selection under thr
     int full64;           // direct core, no packing: full precision in FP64
     int ncand;
@@ -169,6 +173,25 @@ __device__ inline double snr_model_db(double s2s, float Ms, double s2k, float Mk
     double num = 144.0 * (s2s * s2k) * (S2 * K2);
     double den = 12.0 * (s2s * S2 * Mk2 + s2k * K2 * Ms2) + Ms2 * Mk2;
     return 10.0 * log10(num / den);
+}
+
+// Section IV.D model check of every candidate at once: bit c of the result is
+// set when candidate c's model SNR meets the target (every candidate when
+// selection is off).  Lane c of warp 0 evaluates candidate c, so the FP64
+// chain (a slow pipe on this part) runs once per block, not once per
+// candidate; the same decisions, bit for bit.  `slot` is a shared word that no
+// thread writes again before every thread has returned.
+__device__ inline unsigned feasible_mask(const Params& p, double s2s, float Ms, double s2k, float Mk,
+                                         unsigned* slot) {
+    if (threadIdx.x < 32) {
+        const int c = threadIdx.x;
+        bool ok = false;
+        if (c < p.ncand) ok = !p.autosel || snr_feasible(s2s, Ms, s2k, Mk, p.cand[c].S, p.cand[c].K, p.thr);
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (c == 0) *slot = m;
+    }
+    __syncthreads();
+    return *slot;
 }
 
 // Eq. (2): c = Q / ||x||_inf (correctly rounded FP32) and x~ = rint(c x).
@@ -331,17 +354,30 @@ __host__ __device__ constexpr int fft_radix(int m, int nt) {
 // Inverse (decimation in time, the exact reverse): conjugate twiddle then
 // inverse DFT.  Each butterfly reads and writes the same slots, so a pass needs
 // no barrier inside; callers separate passes with __syncthreads().
+//
+// Slot addresses: pad16 adds i >> 4 and i >> 8, which is linear over a
+// butterfly's slots base + q S when S is a multiple of 256, or when the
+// sub-transform lies inside one 256-entry span (M <= 256) and S is a multiple
+// of 16 or the sub-transform inside one 16-entry run (M <= 16): then slot q is
+// pad16(base) + q (S + S/16 + S/256) (the terms present), one multiply-add
+// instead of a pad16 per slot.  The choice is uniform over the pass.
 template <typename C, int RAD, bool INV>
 __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab, unsigned* st) {
     const int S = M / RAD, nbf = m / RAD;
     const int tstep = ntab / M;
+    const bool lin = (S & 255) == 0 || (M <= 256 && ((S & 15) == 0 || M <= 16));
+    const int pstride = S + ((S & 15) == 0 ? S >> 4 : 0) + ((S & 255) == 0 ? S >> 8 : 0);
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
         const int g = b / S, j = b - g * S;
         const int base = g * M + j;
         C v[RAD], w[RAD];
         if (!APX_IN_BOUNDS(base + (RAD - 1) * S < m, st)) continue;
+        int slot[RAD];
+        const int p0 = pad16(base);
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) v[q] = Z[pad16(base + q * S)];
+        for (int q = 0; q < RAD; ++q) slot[q] = lin ? p0 + q * pstride : pad16(base + q * S);
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) v[q] = Z[slot[q]];
         if (S > 1) twiddles<C, RAD, INV>(w, tw, j * tstep);
         if (!INV) {
             dft_small<RAD, C, false>(v);
@@ -357,7 +393,7 @@ __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict
             dft_small<RAD, C, true>(v);
         }
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) Z[pad16(base + q * S)] = v[q];
+        for (int q = 0; q < RAD; ++q) Z[slot[q]] = v[q];
     }
 }
 
@@ -383,26 +419,36 @@ __device__ __forceinline__ void fft_passes(C* Z, int m, const C* __restrict__ tw
 }
 
 // Length-m (power of two) complex FFT of the padded buffer Z by the whole
-// CTA.  Forward: natural order in, digit-reversed order out (see fft_perm).
-// Inverse: that order in, natural order out, unnormalised.
+// CTA, with the radix a CTA of nt threads would use (the result depends on
+// the radix, not on the CTA size).  Forward: natural order in, digit-reversed
+// order out (see fft_perm).  Inverse: that order in, natural order out,
+// unnormalised.
 template <typename C, bool INV>
-__device__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab, unsigned* st = nullptr) {
-    const int R = fft_radix<C>(m, blockDim.x);
+__device__ void fft_smem_nt(C* Z, int m, int nt, const C* __restrict__ tw, int ntab, unsigned* st = nullptr) {
+    const int R = fft_radix<C>(m, nt);
     if (sizeof(C) == 8 && R == 16) fft_passes<C, 16, INV>(Z, m, tw, ntab, st);
     else if (sizeof(C) == 8 && R == 8) fft_passes<C, 8, INV>(Z, m, tw, ntab, st);
     else fft_passes<C, 4, INV>(Z, m, tw, ntab, st);
+}
+template <typename C, bool INV>
+__device__ __forceinline__ void fft_smem(C* Z, int m, const C* __restrict__ tw, int ntab, unsigned* st = nullptr) {
+    fft_smem_nt<C, INV>(Z, m, blockDim.x, tw, ntab, st);
 }
 
 // Slot of frequency k after the forward FFT: k = r1 + R1 r2 + R1 R2 r3 + ...
 // (r_s the output digit of pass s) sits at r1 S1 + r2 S2 + ..., S_s the
 // stride of pass s.
 template <typename C>
-__device__ __forceinline__ int fft_perm(int k, int m) {
-    const int R = fft_radix<C>(m, blockDim.x);
+__device__ __forceinline__ int fft_perm_nt(int k, int m, int nt) {
+    const int R = fft_radix<C>(m, nt);
     int pos = 0, S = m;
     while (S >= R) { S /= R; pos += (k % R) * S; k /= R; }
     if (S > 1) pos += k % S;   // last pass: stride 1
     return pos;
+}
+template <typename C>
+__device__ __forceinline__ int fft_perm(int k, int m) {
+    return fft_perm_nt<C>(k, m, blockDim.x);
 }
 
 // Real-signal step.  Z holds FFT_m of z[j] = x[2j] + i x[2j+1] (n = 2m real
@@ -445,13 +491,27 @@ __device__ __forceinline__ int fft_perm_r(int k, int m) {
     if (S > 1) pos += k & (S - 1);   // last pass: stride 1
     return pos;
 }
+// ... and for a length known at compile time (MM > 0; 0: the runtime m)
+template <int R, int MM>
+__device__ __forceinline__ int fft_perm_rc(int k, int m) {
+    if constexpr (MM == 0) {
+        return fft_perm_r<R>(k, m);
+    } else {
+        int pos = 0, S = MM;
+#pragma unroll
+        for (int it = 0; it < 32 && S >= R; ++it) { S /= R; pos += (k & (R - 1)) * S; k /= R; }
+        if (S > 1) pos += k & (S - 1);
+        return pos;
+    }
+}
 
 // One thread's frequencies k = t, t + nt, ... in rounds of B: every load of a
 // round (both spectrum entries and the twiddle) is issued before any is used,
 // so a round costs one memory latency.
-template <typename C, int R, int B>
-__device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, const C* __restrict__ tw, int twn,
+template <typename C, int R, int B, int MM = 0>
+__device__ __forceinline__ void spectral_multiply_r(C* Z, int m_rt, const C* H, const C* __restrict__ tw, int twn,
                                                     bool coherent, unsigned* st) {
+    const int m = MM > 0 ? MM : m_rt;
     const int half = m / 2, nt = blockDim.x;
     for (int k0 = threadIdx.x; k0 <= half; k0 += B * nt) {
         C hk[B], hmk[B], w[B];
@@ -477,7 +537,7 @@ __device__ __forceinline__ void spectral_multiply_r(C* Z, int m, const C* H, con
                 C cym = cconj(Ym);
                 Z[0] = cadd(cadd(Y0, cym), mul_mi<C, true>(csub(Y0, cym)));
             } else {
-                const int qk = fft_perm_r<R>(k, m), qmk = fft_perm_r<R>(m - k, m);
+                const int qk = fft_perm_rc<R, MM>(k, m), qmk = fft_perm_rc<R, MM>(m - k, m);
                 if (!APX_IN_BOUNDS(qk < m && qmk < m, st)) continue;
                 const int pk = pad16(qk), pmk = pad16(qmk);
                 C a = Z[pk], b = Z[pmk];
@@ -501,7 +561,15 @@ __device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__
                                   unsigned* st = nullptr) {
     constexpr int B = sizeof(C) == 8 ? 5 : 3;
     const int R = fft_radix<C>(m, blockDim.x);
-    if (R == 16) spectral_multiply_r<C, 16, B>(Z, m, H, tw, twn, coherent, st);
+    if (R == 16) {
+        switch (m) {  // the lengths with compile-time FFT passes
+            case 1024: spectral_multiply_r<C, 16, B, 1024>(Z, m, H, tw, twn, coherent, st); return;
+            case 2048: spectral_multiply_r<C, 16, B, 2048>(Z, m, H, tw, twn, coherent, st); return;
+            case 4096: spectral_multiply_r<C, 16, B, 4096>(Z, m, H, tw, twn, coherent, st); return;
+            case 8192: spectral_multiply_r<C, 16, B, 8192>(Z, m, H, tw, twn, coherent, st); return;
+            default: spectral_multiply_r<C, 16, B>(Z, m, H, tw, twn, coherent, st); return;
+        }
+    }
     else if (R == 8) spectral_multiply_r<C, 8, B>(Z, m, H, tw, twn, coherent, st);
     else spectral_multiply_r<C, 4, B>(Z, m, H, tw, twn, coherent, st);
 }

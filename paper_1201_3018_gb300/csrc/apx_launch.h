@@ -16,6 +16,12 @@ __host__ __device__ constexpr int fft_threads(int Wb) { return Wb / 32 > 32 ? Wb
 // FFT core kernel spectrum: R1 decimated sub-transforms of n / R1 points.
 __host__ __device__ constexpr int spec_r1(int n) { return n / 2 < 16 ? n / 2 : 16; }
 constexpr int kSpecThreads = 256;
+// Preparation jobs of a fused single call (apx_prep.cuh) for a block kernel of
+// nt threads: R1 sub-transforms, the combine in slices of nt frequencies, the
+// kernel statistics.
+__host__ __device__ constexpr int prep_jobs_count(int Wb, int nt) {
+    return spec_r1(Wb) + (Wb / 2 + 1 + nt - 1) / nt + 1;
+}
 
 // Launch through cudaLaunchKernelEx; `pdl` marks the launch as a programmatic
 // dependent of the previous kernel in the stream (the kernel calls
@@ -40,6 +46,8 @@ cudaError_t launch_spec(const Params& p, cudaStream_t st);
 cudaError_t launch_spec_combine(const Params& p, cudaStream_t st);
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
+cudaError_t launch_fft_fused(const Params& p, size_t smem, cudaStream_t st);
+unsigned fused_grid(const Params& p);
 size_t fft_smem_bytes(const Params& p);
 
 // Batched launches: `any` is one request's parameters (for the launch shape and
