@@ -21,6 +21,8 @@
 // A packed candidate's FP64 spectrum is built on demand by the first CTA that
 // selects it; later CTAs wait for it with a bounded spin and report a timeout
 // in the status word instead of hanging.
+#include <type_traits>
+
 #include "apx_prep.cuh"
 
 namespace apx {
@@ -231,26 +233,34 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
         // Eq. (7): word w = sum_q eps^q s~[w + q Ls], zero past Ls
         Ls = (p.Wb + c.M - 1) / c.M;
         nr = Ls + p.Nodd - 1;
-        int* sq = reinterpret_cast<int*>(smem + sizeof(double2) * padded_len(p.Wb / 2));
+        // the companded block, in the narrowest integer type that holds +-S_q
+        unsigned char* sqb = smem + sizeof(double2) * padded_len(p.Wb / 2);
+        auto pack = [&](auto* sq) {
+            using T = typename std::remove_pointer<decltype(sq)>::type;
 #pragma unroll
-        for (int v = 0; v < kVals / 2; ++v)
-            if (pair_ok(p, v)) {
-                const int e = 2 * (threadIdx.x + v * blockDim.x);
-                sq[e] = compand(cs, xv[2 * v]);
-                sq[e + 1] = compand(cs, xv[2 * v + 1]);
-            }
-        __syncthreads();
-        for (int w = threadIdx.x; w < n; w += blockDim.x) {
-            double acc = 0.0, ep = 1.0;
-            if (w < Ls) {
-                for (int q = 0; q < c.M; ++q) {
-                    const int t = w + q * Ls;
-                    if (t < p.Wb) acc = __dadd_rn(acc, __dmul_rn(ep, (double)sq[t]));
-                    ep = __dmul_rn(ep, eps);
+            for (int v = 0; v < kVals / 2; ++v)
+                if (pair_ok(p, v)) {
+                    const int e = 2 * (threadIdx.x + v * blockDim.x);
+                    sq[e] = (T)compand(cs, xv[2 * v]);
+                    sq[e + 1] = (T)compand(cs, xv[2 * v + 1]);
                 }
+            __syncthreads();
+            for (int w = threadIdx.x; w < n; w += blockDim.x) {
+                double acc = 0.0, ep = 1.0;
+                if (w < Ls) {
+                    for (int q = 0; q < c.M; ++q) {
+                        const int t = w + q * Ls;
+                        if (t < p.Wb) acc = __dadd_rn(acc, __dmul_rn(ep, (double)sq[t]));
+                        ep = __dmul_rn(ep, eps);
+                    }
+                }
+                word<double>(Z, w) = acc;
             }
-            word<double>(Z, w) = acc;
-        }
+        };
+        const int esz = companded_bytes(p);
+        if (esz == 1) pack(reinterpret_cast<signed char*>(sqb));
+        else if (esz == 2) pack(reinterpret_cast<short*>(sqb));
+        else pack(reinterpret_cast<int*>(sqb));
     }
     __syncthreads();
     fft_smem<double2, false>(Z, mm, p.tw64, p.ntab, p.status);
@@ -296,10 +306,11 @@ size_t fft_smem_bytes(const Params& p) {
     for (int j = 0; j < p.ncand; ++j) asym |= p.cand[j].blk != APX_BLK_SYM;
     const size_t z32 = sizeof(float2) * padded_len(p.Wb / 2);
     // a symmetric candidate transforms W_block/2 real words (W_block/4 complex),
-    // an asymmetric one W_block real words plus the companded block as int32
+    // an asymmetric one W_block real words plus the companded block (the
+    // smaller the buffer, the more of the SM's unified memory stays L1 cache)
     size_t z64 = 0;
     if (p.ncand > 0) z64 = sizeof(double2) * padded_len(asym ? p.Wb / 2 : p.Wb / 4);
-    if (asym) z64 += sizeof(int) * (size_t)p.Wb;
+    if (asym) z64 += (size_t)companded_bytes(p) * (size_t)p.Wb;
     return z32 > z64 ? z32 : z64;
 }
 

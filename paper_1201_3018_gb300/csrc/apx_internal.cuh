@@ -194,6 +194,15 @@ __device__ inline unsigned feasible_mask(const Params& p, double s2s, float Ms, 
     return *slot;
 }
 
+// Bytes per companded sample the FFT core's asymmetric packing stages in
+// shared memory: |s~| <= S_q of every candidate (Eq. 2 rounds c x with
+// |c x| <= S_q), so one byte while every S_q <= 127, two up to 32767.
+__host__ __device__ inline int companded_bytes(const Params& p) {
+    int smax = 0;
+    for (int j = 0; j < p.ncand; ++j) smax = p.cand[j].S > smax ? p.cand[j].S : smax;
+    return smax <= 127 ? 1 : (smax <= 32767 ? 2 : 4);
+}
+
 // Eq. (2): c = Q / ||x||_inf (correctly rounded FP32) and x~ = rint(c x).
 __device__ __forceinline__ float compand_factor(int Q, float m) { return __fdiv_rn((float)Q, m); }
 __device__ __forceinline__ int compand(float c, float x) { return __float2int_rn(__fmul_rn(c, x)); }
