@@ -357,6 +357,13 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
     useful = 2.0 * F * out_len * N
     peak = float(pk.get("bf16_tflops", 1899.0))
 
+    def hbm_write(ms):
+        # the GEMM kernel's other bound: writing the F x (L+N-1) FP32 outputs
+        byts = 4.0 * F * out_len
+        return {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "bytes": byts,
+                "peak_source": "measured copy bandwidth" if pk.get("source") != "fallback" else "fallback"}
+
     # S_q = K_q = 16: every companded integer is exact in FP8 E4M3 (the paper's
     # 16-level setting), and the library runs the FP8 tensor-core path
     y8 = torch.empty(F, ldy, device=dev)
@@ -383,7 +390,8 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
            "roofline_tc_mma": {"bound": "tensor", "achieved": useful / (mma8 * 1e-3) / 1e12, "peak": 2 * peak,
                                "unit": "TFLOP/s", "frac": useful / (mma8 * 1e-3) / 1e12 / (2 * peak),
                                "peak_source": "measured cuBLAS bf16 x 2 (nominal FP8 : FP16 dense ratio)",
-                               "kernel_ms": mma8, "traffic": traffic_for("tc_mma_fp8")}}
+                               "kernel_ms": mma8, "traffic": traffic_for("tc_mma_fp8")},
+           "roofline_hbm_write": hbm_write(mma8)}
     return {"workload": "filterbank: 2^22 N(0,1) samples, 32 Hann-windowed-sinc band-pass kernels of 1024 taps "
                         "(log-spaced 50 Hz - 20 kHz at 44.1 kHz), S_q = K_q = 127, FP16 integers on the tensor cores",
             "outputs_per_step": F * out_len, "value": F * out_len / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
@@ -397,6 +405,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
                                 "unit": "TFLOP/s", "frac": useful / (mma_ms * 1e-3) / 1e12 / peak,
                                 "peak_source": "measured cuBLAS bf16 (FP16 runs at the same tensor rate)",
                                 "executed_over_useful": kpad / N, "traffic": traffic_for("tc_mma")},
+            "roofline_hbm_write": hbm_write(mma_ms),
             "blocks": nb, "outputs_per_block": T, "fp8_sq16": fp8}
 
 
@@ -673,7 +682,9 @@ def main():
     roof = {"kernel": dom, "avg_launch_us": avg_ms * 1e3}
     packed_blocks = int(sum(hist[1:4]))
     if dom == "fft":
-        flops = sum(fft_flops(Wb) if m == apx.BLK_FULL else 0.0 for m in st["mode"])
+        # the blocks' transforms plus the kernel spectrum (one real FFT of W_block
+        # points), which this single call's launch computes too
+        flops = sum(fft_flops(Wb) if m == apx.BLK_FULL else 0.0 for m in st["mode"]) + 2.5 * Wb * math.log2(Wb)
         fp64 = sum(fft_flops(Wb // 2 if m == apx.BLK_SYM else Wb) for m in st["mode"] if m in (1, 2, 3))
         if fp64 > flops:
             roof.update(bound="alu", achieved=fp64 / (avg_ms * 1e-3) / 1e12, peak=pk["fp64_tflops"],
