@@ -660,7 +660,9 @@ def main():
         tuner = tune.Tuner(ctx)
         want = set(args.extras.split(","))
         if "batched" in want:
-            extras["batched"] = bench_batched(ctx, tuner, dev, args.steps, flush, stream)
+            # a batch's blocks all run together: choose by throughput, timing the
+            # candidates on long signals (2^20 samples) rather than short ones
+            extras["batched"] = bench_batched(ctx, tune.Tuner(ctx, L=1 << 20), dev, args.steps, flush, stream)
         if "filterbank" in want:
             extras["filterbank"] = bench_filterbank(ctx, tuner, dev, args.steps, flush, stream, peaks())
         if "paper" in want:

@@ -7,6 +7,13 @@ time and frequency domains at W_block = 3N + 1, generalised here to any
 W_block); it ranks the candidates, and the best few are then timed on the GPU
 through the C ABI with CUDA events.  Results are cached per key in memory and,
 if a path is given, in a JSON file.
+
+The candidates are timed as single calls on a signal of L samples, so L sets
+what is optimised: short signals (2^18, the default) the latency of one
+request, as a server wants; long ones (2^20) the throughput of many blocks in
+flight, as a batched launch wants.  On the batched workload (256 signals of
+2^14 - 2^20 samples) the choices made at 2^20 ran 1.7x faster than those made
+at 2^18 (W_block 4096 - 8192 instead of 512 - 4096, and no direct core).
 """
 from __future__ import annotations
 
