@@ -1,0 +1,112 @@
+"""The FFT core's one-launch form (a single call with at least 64 blocks: the
+kernel preparation runs in ticketed CTAs of the block kernel's own launch)
+against its three-launch form (preparation launches ahead of the block
+kernel, which batched calls always use): the same bits, one launch instead of
+three, and the ticket counter staying in step across interleaved calls."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1201_3018_gb300 import apx
+import oracle as O
+from paper_1201_3018_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FUSE_MIN_BLOCKS = 64  # the library's threshold for the one-launch form
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = apx.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _length_for_blocks(P, N, Wb, mode):
+    """Smallest L whose block plan has exactly P blocks."""
+    lo, hi = 1, 1 << 26
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if apx.plan_blocks(mid, N, Wb, mode)[0] >= P:
+            hi = mid
+        else:
+            lo = mid + 1
+    assert apx.plan_blocks(lo, N, Wb, mode)[0] == P
+    return lo
+
+
+def _single(ctx, s, k, Wb, mode, snr):
+    r = torch.empty(s.numel() + k.numel() - 1, device="cuda")
+    n0 = ctx.launch_count()
+    if (mode & 0xF00) == apx.PACK_NONE:
+        ctx.apx_conv_full(s, k, Wb, mode, r)
+    else:
+        ctx.apx_conv(s, k, Wb, mode, snr, r)
+    assert ctx.apx_sync() == 0
+    return r.cpu().numpy(), ctx.launch_count() - n0
+
+
+def _batch_of_one(ctx, s, k, Wb, mode, snr):
+    r = torch.empty(s.numel() + k.numel() - 1, device="cuda")
+    ctx.apx_conv_batch(ctx.make_requests([dict(s=s, k=k, r=r, mode=mode, W_block=Wb, snr_db=snr)]))
+    assert ctx.apx_sync() == 0
+    return r.cpu().numpy()
+
+
+CASES = [
+    # (blocks, N, W_block, op | pack, target dB)
+    (FUSE_MIN_BLOCKS - 1, 1024, 4096, apx.OP_XCORR | apx.PACK_AUTO, 45.0),
+    (FUSE_MIN_BLOCKS, 1024, 4096, apx.OP_XCORR | apx.PACK_AUTO, 45.0),
+    (300, 4096, 8192, apx.OP_XCORR | apx.PACK_AUTO, 45.0),
+    (300, 4096, 8192, apx.OP_CONV | apx.PACK_NONE, 0.0),
+    (200, 255, 2048, apx.OP_CONV | apx.PACK_AUTO, 12.0),     # blocks pick packings
+    (100, 65, 1024, apx.OP_CONV | apx.PACK_ASYM2, 0.0),
+    (80, 3000, 16384, apx.OP_XCORR | apx.PACK_AUTO, 30.0),
+]
+
+
+@pytest.mark.parametrize("P,N,Wb,bits,snr", CASES)
+def test_one_launch_equals_three_launch_form(ctx, P, N, Wb, bits, snr):
+    mode = bits | apx.CORE_FFT
+    L = _length_for_blocks(P, N, Wb, mode)
+    s = _dev(wl.random_signal(wl.SEED_BASE + 900 + P, L, "laplace", 0.1))
+    k = _dev(wl.random_signal(wl.SEED_BASE + 950 + N, N, "uniform"))
+    got, launches = _single(ctx, s, k, Wb, mode, snr)
+    assert launches == (1 if P >= FUSE_MIN_BLOCKS else 3)
+    ref = _batch_of_one(ctx, s, k, Wb, mode, snr)
+    assert np.array_equal(got, ref)
+    # and sampled outputs against Eq. (1) in FP64 (full precision blocks within FP32 rounding;
+    # packed ones within the target)
+    sh, kh = s.cpu().numpy(), k.cpu().numpy()
+    if bits & 0xF == apx.OP_XCORR:
+        kh = kh[::-1].copy()
+    idx = np.linspace(0, L + N - 2, 400).astype(np.int64)
+    exact = O.conv_ref_at(sh, kh, idx)
+    err = np.linalg.norm(got[idx] - exact) / np.linalg.norm(exact)
+    bound = 1e-5 if (bits & 0xF00) == apx.PACK_NONE else 10 ** (-max(snr, 12.0) / 20) * 3
+    assert err <= bound, err
+
+
+def test_tickets_stay_in_step_across_interleaved_calls(ctx):
+    """One-launch calls between three-launch calls, batched calls and calls of
+    another W_block: every repeat gives the first result's bits."""
+    N, Wb, mode = 4096, 8192, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    L = _length_for_blocks(150, N, Wb, mode)
+    s = _dev(wl.random_signal(wl.SEED_BASE + 990, L, "laplace", 0.1))
+    k = _dev(wl.random_signal(wl.SEED_BASE + 991, N, "uniform"))
+    small_s = _dev(wl.random_signal(wl.SEED_BASE + 992, 20000, "laplace", 0.1))
+    small_k = _dev(wl.random_signal(wl.SEED_BASE + 993, 300, "uniform"))
+    first, n = _single(ctx, s, k, Wb, mode, 45.0)
+    assert n == 1
+    for rep in range(4):
+        _single(ctx, small_s, small_k, 2048, apx.OP_CONV | apx.CORE_FFT | apx.PACK_AUTO, 30.0)
+        _batch_of_one(ctx, small_s, small_k, 4096, apx.OP_CONV | apx.CORE_FFT | apx.PACK_NONE, 0.0)
+        _single(ctx, s, k, 16384, mode, 45.0)  # another W_block, also one launch
+        again, n = _single(ctx, s, k, Wb, mode, 45.0)
+        assert n == 1
+        assert np.array_equal(again, first), rep
