@@ -133,11 +133,14 @@ int apx_conv_fixed(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, i
 int apx_conv_full(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N,
                   int32_t W_block, uint32_t mode, float* r_out, void* stream);
 
-/* End-to-end variant for callers holding HOST data: copies s_in (host, L) and
- * k (host, N) to the device, runs apx_conv (S_q = K_q = 0) or apx_conv_fixed,
- * and copies r_out (host, L+N-1) back, all on `stream`, then synchronises it.
- * Host buffers should be pinned for full copy speed.  Device staging buffers
- * come from the context workspace.  Returns the apx_sync() status. */
+/* End-to-end variant for callers holding HOST data: s_in (host, L), k (host,
+ * N) in, r_out (host, L+N-1) out, apx_conv (S_q = K_q = 0) or apx_conv_fixed
+ * on `stream`, which is then synchronised.  When all three buffers are
+ * page-locked and addressable by the device (cudaHostAlloc or registered),
+ * the kernels read and write them in place over the host link, overlapping
+ * the transfers with the computation; otherwise s_in and k are copied to
+ * device staging buffers from the context workspace and r_out is copied back.
+ * The results are the same either way.  Returns the apx_sync() status. */
 int apx_conv_host(apx_ctx* ctx, const float* s_in_host, int64_t L, const float* k_host, int32_t N,
                   int32_t W_block, uint32_t mode, double snr_target_db, int32_t S_q, int32_t K_q,
                   float* r_out_host, void* stream);
