@@ -206,14 +206,15 @@ typedef struct {
 int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream);
 
 /* The same from HOST buffers: s_in, k and r_out of every request are host
- * pointers (pinned memory for asynchronous copies; pageable memory makes the
- * copies synchronous).  Enqueues on `stream` one host-to-device copy per input,
- * the batched launches on the context's device copies, and one device-to-host
- * copy per output; the outputs are valid once the stream has reached that
- * point, and the host buffers must stay valid until then.  The device copies
- * live in the context (grown on demand, budget-checked) and are reused by the
- * next call on any stream.  Errors: as apx_conv_batch (nothing is enqueued
- * for an invalid batch). */
+ * pointers.  A request whose three buffers are page-locked and addressable by
+ * the device runs on them in place (the kernels read and write them over the
+ * host link).  For the others `stream` gets one host-to-device copy per input
+ * into device copies and one device-to-host copy per output after the batched
+ * launches (pageable memory makes those copies synchronous).  The outputs are
+ * valid once the stream has reached the end of the call, and the host buffers
+ * must stay valid until then.  The device copies live in the context (grown on
+ * demand, budget-checked) and are reused by the next call on any stream.
+ * Errors: as apx_conv_batch (nothing is enqueued for an invalid batch). */
 int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream);
 
 /* A batch captured once into a CUDA graph and replayed: apx_graph_create plans

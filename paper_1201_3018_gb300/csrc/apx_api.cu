@@ -934,13 +934,28 @@ extern "C" int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, 
 extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream) {
     if (!ctx || n < 0 || (n > 0 && !reqs)) return APX_ERR_ARG;
     Range range("apx_conv_batch_host");
-    // device copies of every request's signal, kernel and output, 256-byte aligned
+    DeviceGuard dg(ctx->device);
+    // A request whose three buffers are page-locked and addressable by the device
+    // runs on them in place (as apx_conv_host); the others get device copies of
+    // their signal, kernel and output, 256-byte aligned, in the context workspace.
+    std::vector<apx_request> dq(reqs, reqs + n);
+    std::vector<char> staged((size_t)n, 0);
     std::vector<size_t> off(3 * (size_t)n);
     size_t total = 0;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     for (int32_t i = 0; i < n; ++i) {
         const apx_request& q = reqs[i];
         if (!q.s_in || !q.k || !q.r_out || q.L < 1 || q.N < 1) return APX_ERR_ARG;
+        const void* sa = host_alias(q.s_in);
+        const void* ka = sa ? host_alias(q.k) : nullptr;
+        void* ra = ka ? host_alias(q.r_out) : nullptr;
+        if (ra) {
+            dq[i].s_in = (const float*)sa;
+            dq[i].k = (const float*)ka;
+            dq[i].r_out = (float*)ra;
+            continue;
+        }
+        staged[i] = 1;
         off[3 * i] = total;
         total += al(sizeof(float) * (size_t)q.L);
         off[3 * i + 1] = total;
@@ -948,12 +963,11 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
         off[3 * i + 2] = total;
         total += al(sizeof(float) * (size_t)(q.L + q.N - 1));
     }
-    DeviceGuard dg(ctx->device);
-    int rc = ensure(ctx, ctx->bhost, total > 0 ? total : 256);
+    int rc = total > 0 ? ensure(ctx, ctx->bhost, total) : 0;
     if (rc) return rc;
     unsigned char* base = (unsigned char*)ctx->bhost.p;
-    std::vector<apx_request> dq(reqs, reqs + n);
     for (int32_t i = 0; i < n; ++i) {
+        if (!staged[i]) continue;
         dq[i].s_in = (const float*)(base + off[3 * i]);
         dq[i].k = (const float*)(base + off[3 * i + 1]);
         dq[i].r_out = (float*)(base + off[3 * i + 2]);
@@ -964,6 +978,7 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        if (!staged[i]) continue;
         e = cudaMemcpyAsync((void*)dq[i].s_in, reqs[i].s_in, sizeof(float) * (size_t)reqs[i].L,
                             cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
@@ -973,9 +988,11 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
     if (e != cudaSuccess) return cuda_status(e);
     rc = batch_run(ctx, bp, n, st);
     if (rc) return rc;
-    for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        if (!staged[i]) continue;
         e = cudaMemcpyAsync(reqs[i].r_out, dq[i].r_out, sizeof(float) * (size_t)(reqs[i].L + reqs[i].N - 1),
                             cudaMemcpyDeviceToHost, st);
+    }
     return cuda_status(e);
 }
 
