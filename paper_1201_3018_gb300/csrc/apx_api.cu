@@ -43,8 +43,16 @@ void set_flag_ptrs(Params& p, unsigned* flags) {
     p.ticket = reinterpret_cast<unsigned long long*>(flags + 8);
     p.jobready = flags + 10;
 }
-bool use_fused(const Params& p) {
-    return p.fft && p.P >= kFuseMinBlocks && prep_jobs_count(p.Wb, fft_threads(p.Wb)) <= kMaxJobs;
+// Not while the stream is being captured into a graph: the launch's ticket
+// base is fixed at capture, so replays would find the counter moved on.
+bool use_fused(const Params& p, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone && p.fft && p.P >= kFuseMinBlocks &&
+           prep_jobs_count(p.Wb, fft_threads(p.Wb)) <= kMaxJobs;
 }
 
 struct apx_ctx {
@@ -466,7 +474,7 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
 
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
     set_flag_ptrs(p, (unsigned*)ctx->flags.p);
-    p.fused = use_fused(p);
+    p.fused = use_fused(p, stream);
     p.ticket_base = ctx->tickets;
     p.Hfull = (float2*)ctx->Hfull.p;
     p.ki = (KInfo*)ctx->ki.p;
@@ -1227,7 +1235,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)(base + kSOffHc + j * kSHcBytes);
     const size_t smem = fft_smem_bytes(p);
     if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
-    p.fused = use_fused(p);
+    p.fused = use_fused(p, st);
     if (p.fused) {
         std::lock_guard<std::mutex> lk(g_static_mu);
         p.ticket_base = g_static[dev].tickets;

@@ -110,3 +110,33 @@ def test_tickets_stay_in_step_across_interleaved_calls(ctx):
         again, n = _single(ctx, s, k, Wb, mode, 45.0)
         assert n == 1
         assert np.array_equal(again, first), rep
+
+
+def test_captured_call_replays(ctx):
+    """A single call captured into a CUDA graph (stream capture) takes the
+    three-launch form, whose launches replay: each replay recomputes from the
+    signal's current contents."""
+    N, Wb, mode = 4096, 8192, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    L = _length_for_blocks(150, N, Wb, mode)
+    s = _dev(wl.random_signal(wl.SEED_BASE + 994, L, "laplace", 0.1))
+    k = _dev(wl.random_signal(wl.SEED_BASE + 995, N, "uniform"))
+    r = torch.empty(L + N - 1, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.apx_conv(s, k, Wb, mode, 45.0, r, stream=side)  # workspace allocated before capture
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        n0 = ctx.launch_count()
+        with torch.cuda.graph(g, stream=side):
+            ctx.apx_conv(s, k, Wb, mode, 45.0, r, stream=side)
+        assert ctx.launch_count() - n0 == 3
+    torch.cuda.current_stream().wait_stream(side)
+    for rep in range(2):
+        s.copy_(_dev(wl.random_signal(wl.SEED_BASE + 996 + rep, L, "laplace", 0.1)))
+        g.replay()
+        torch.cuda.synchronize()
+        got = r.cpu().numpy()
+        want, n = _single(ctx, s, k, Wb, mode, 45.0)
+        assert n == 1
+        assert np.array_equal(got, want), rep
