@@ -818,10 +818,6 @@ int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, i
                   uint32_t mode, double snr_target_db, int32_t S_q, int32_t K_q, float* r_h, void* stream) {
     if (!ctx || !s_h || !k_h || !r_h || L < 1 || N < 1) return APX_ERR_ARG;
     DeviceGuard dg(ctx->device);
-    int rc = ensure(ctx, ctx->hs, sizeof(float) * (size_t)L);
-    if (!rc) rc = ensure(ctx, ctx->hk, sizeof(float) * (size_t)N);
-    if (!rc) rc = ensure(ctx, ctx->hr, sizeof(float) * (size_t)(L + N - 1));
-    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t pack = mode & 0xF00u;
     const int sel = pack == APX_PACK_NONE ? 2 : ((S_q > 0 && K_q > 0 && pack != APX_PACK_AUTO) ? 1 : 0);
@@ -832,10 +828,16 @@ int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, i
     const float* s_a = (const float*)host_alias(s_h);
     const float* k_a = (const float*)host_alias(k_h);
     float* r_a = (float*)host_alias(r_h);
+    int rc;
     if (s_a && k_a && r_a) {
         rc = run(ctx, s_a, L, k_a, N, W_block, mode, sel, snr_target_db, S_q, K_q, r_a, nullptr, nullptr, st);
         return rc ? rc : apx_sync(ctx, stream);
     }
+    // otherwise through device staging buffers
+    rc = ensure(ctx, ctx->hs, sizeof(float) * (size_t)L);
+    if (!rc) rc = ensure(ctx, ctx->hk, sizeof(float) * (size_t)N);
+    if (!rc) rc = ensure(ctx, ctx->hr, sizeof(float) * (size_t)(L + N - 1));
+    if (rc) return rc;
     // the signal copy overlaps the kernel copy and the spectrum preparation
     cudaError_t e = copy_stream_begin(ctx, st);
     if (e == cudaSuccess)
