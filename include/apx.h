@@ -270,7 +270,7 @@ int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_ba
  * whose allocator owns the GPU, code that runs while another library holds the
  * device's memory pool.  It takes no context and calls no cudaMalloc, cudaFree
  * or other allocating routine: all of its scratch (twiddle tables, kernel
- * spectra, kernel statistics, claim words) lives in one fixed device array of
+ * spectra, kernel statistics, claim, ready and ticket words) lives in one fixed device array of
  * about 490 KB that every GPU loading the library keeps until the process
  * exits.
  *   s_in, k, r_out : device pointers as for apx_conv (L, N and L+N-1 floats)
@@ -281,7 +281,8 @@ int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_ba
  * FP32 outputs within rounding).  Non-finite input yields NaN outputs for the
  * affected blocks; there is no status word to read back.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and fills the twiddle tables; a call with a W_block
+ * (cudaGetSymbolAddress), clears its flag words and fills the twiddle tables on
+ * `stream`; a call with a W_block
  * different from the previous one on that device refills them on `stream`.
  * Make the first call before any stream capture.  Every call shares the array:
  * calls that overlap on the GPU (different streams, or several host threads)
