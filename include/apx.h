@@ -178,6 +178,14 @@ int apx_profile_read(apx_ctx* ctx, double* ms, int64_t* n);
  * faults or hangs.  Errors: APX_ERR_ARG. */
 int apx_test_stall_next(apx_ctx* ctx);
 
+/* Test hook for the one-launch FFT core's ticket check (no counterpart in the
+ * paper).  Moves the context's count of CTA tickets handed out by n without
+ * launching anything, as a bookkeeping fault would.  The next one-launch call
+ * finds its tickets out of range in every CTA, touches no output, and apx_sync
+ * returns APX_ERR_CHECK; apx_sync then reads the device counter back, so the
+ * call after that is correct again.  Errors: APX_ERR_ARG. */
+int apx_test_skew_tickets(apx_ctx* ctx, int64_t n);
+
 /* Static string naming a status code. */
 const char* apx_strerror(int status);
 

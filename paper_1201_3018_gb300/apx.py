@@ -67,6 +67,7 @@ SIGNATURES = {
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "apx_conv_batch_host": (C.c_int, [_vp, _vp, _i32, _vp]),
     "apx_test_stall_next": (C.c_int, [_vp]),
+    "apx_test_skew_tickets": (C.c_int, [_vp, _i64]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
 }
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
@@ -276,6 +277,10 @@ class Context:
     def test_stall_next(self):
         """Failure-path test hook (apx_test_stall_next)."""
         return _check("apx_test_stall_next", lib().apx_test_stall_next(self._h))
+
+    def test_skew_tickets(self, n):
+        """Failure-path test hook (apx_test_skew_tickets)."""
+        return _check("apx_test_skew_tickets", lib().apx_test_skew_tickets(self._h, int(n)))
 
     def apx_conv_batch_host(self, reqs, stream=None):
         """reqs: a numpy array of REQUEST_DTYPE (or a ctypes array of Request)

@@ -796,6 +796,13 @@ int apx_sync(apx_ctx* ctx, void* stream) {
     cudaError_t e = cudaMemcpyAsync(&h, ctx->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && h) e = cudaMemsetAsync(ctx->flags.p, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess && (h & 4u)) {
+        // a failed check may be a ticket count out of step: take the device's
+        unsigned long long t = 0;
+        e = cudaMemcpyAsync(&t, (unsigned*)ctx->flags.p + 8, sizeof t, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) ctx->tickets = t;
+    }
     if (e == cudaSuccess && h) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     if (h & 4u) return APX_ERR_CHECK;
@@ -1004,6 +1011,12 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
                             cudaMemcpyDeviceToHost, st);
     }
     return cuda_status(e);
+}
+
+extern "C" int apx_test_skew_tickets(apx_ctx* ctx, int64_t n) {
+    if (!ctx) return APX_ERR_ARG;
+    ctx->tickets += (unsigned long long)n;
+    return APX_OK;
 }
 
 extern "C" int apx_test_stall_next(apx_ctx* ctx) {

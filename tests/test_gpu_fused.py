@@ -140,3 +140,26 @@ def test_captured_call_replays(ctx):
         want, n = _single(ctx, s, k, Wb, mode, 45.0)
         assert n == 1
         assert np.array_equal(got, want), rep
+
+
+def test_ticket_fault_is_reported_and_recovered(ctx):
+    """A ticket count out of step (host-injected): every CTA of the next
+    one-launch call finds its ticket out of range and touches nothing,
+    apx_sync reports APX_ERR_CHECK and resynchronises, and the following call
+    is correct."""
+    N, Wb, mode = 1024, 4096, apx.OP_CONV | apx.CORE_FFT | apx.PACK_AUTO
+    L = _length_for_blocks(100, N, Wb, mode)
+    s = _dev(wl.random_signal(wl.SEED_BASE + 997, L, "laplace", 0.1))
+    k = _dev(wl.random_signal(wl.SEED_BASE + 998, N, "uniform"))
+    want, _ = _single(ctx, s, k, Wb, mode, 30.0)
+    for skew in (1 << 20, -(1 << 20)):  # every ticket below 0 or past the grid
+        ctx.test_skew_tickets(skew)
+        r = torch.full((L + N - 1,), float("nan"), device="cuda")
+        ctx.apx_conv(s, k, Wb, mode, 30.0, r)
+        with pytest.raises(apx.ApxError) as e:
+            ctx.apx_sync()
+        assert e.value.status == apx.APX_ERR_CHECK
+        assert torch.isnan(r).all()
+        again, n = _single(ctx, s, k, Wb, mode, 30.0)
+        assert n == 1
+        assert np.array_equal(again, want)
