@@ -419,8 +419,10 @@ def bench_paper_comparison(ctx, dev, flush, stream):
         full, FP32 full.
       e1: the Section IV.A throughput-test shape, L = 8192 * 2^10 U[-128,128],
         N = 800, direct core, fixed S_q = K_q = 16 (symmetric, asymmetric M=3)
-        and 256 (asymmetric M=2) where the exactness bound admits them, per
-        W_block; SNR against the FP64 full-precision output."""
+        and 256 (asymmetric M=2) where the exactness bound admits them, and
+        the symmetric setting through the paper-literal form (which runs
+        beyond that bound), per W_block; SNR against the FP64 full-precision
+        output."""
     import torch
     from paper_1201_3018_gb300 import apx
     out = {}
@@ -490,7 +492,8 @@ def bench_paper_comparison(ctx, dev, flush, stream):
         t32 = timed(lambda: ctx.apx_conv_full(s, k, Wb, apx.CORE_DIRECT | apx.PACK_NONE, r, stream=stream))
         rows.append({"W_block": Wb, "method": "full_fp32", "ms": t32, "value": n_out / (t32 * 1e-3) / 1e9})
         rows.append({"W_block": Wb, "method": "full_fp64", "ms": t64, "value": n_out / (t64 * 1e-3) / 1e9})
-        for method, pack, Q in (("sym", apx.PACK_SYM, 16), ("asym3", apx.PACK_ASYM3, 16), ("asym2", apx.PACK_ASYM2, 256)):
+        for method, pack, Q in (("sym", apx.PACK_SYM, 16), ("sym_paper_literal", apx.PACK_SYM | apx.LITERAL, 16),
+                                ("asym3", apx.PACK_ASYM3, 16), ("asym2", apx.PACK_ASYM2, 256)):
             row = {"W_block": Wb, "method": method, "Sq": Q, "Kq": Q}
             try:
                 t = timed(lambda: ctx.apx_conv_fixed(s, k, Wb, apx.CORE_DIRECT | pack, Q, Q, r, stream=stream))

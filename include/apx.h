@@ -65,6 +65,17 @@ extern "C" {
                                     full-precision convolution in FP64 (the
                                     paper's full-precision baseline runs in FP64),
                                     rounded once to FP32 on output              */
+#define APX_LITERAL      0x2000u /* with APX_PACK_SYM, the direct core and a fixed
+                                    quantiser (apx_conv_fixed): the paper's own
+                                    eps = (2 R_max)^-1 (Eq. 6) and Eqs. (11)-(15)
+                                    in FP64 with u_sys = 3.1193e-11 (Section IV)
+                                    instead of the exact power-of-two form.
+                                    Rounding can move a digit (the paper measures
+                                    the result by SNR); R_max = N' S_q K_q up to
+                                    2^31, beyond the exact form's bound.  The
+                                    packed block convolution runs without fused
+                                    multiply-adds, as the equations are written.
+                                    Single calls only (batched calls reject it). */
 
 /* ---- per-block modes reported in apx_block_stats.mode ----------------- */
 #define APX_BLK_FULL      0

@@ -559,18 +559,33 @@ typedef struct {
     int32_t nk;       /* packed kernel taps */
     double l1;        /* ||kbar||_1 (exact integer) */
     int32_t log2n;
+    int literal;      /* OR_LITERAL: eps = (2 R_max)^-1, FP64 unpacking with u_sys */
 } mode_t_;
 
 static int prep_mode(mode_t_* md, int blk, int32_t S, int32_t K, const float* kr, int32_t N,
-                     int32_t Nodd, float Mk, int32_t Wblock) {
+                     int32_t Nodd, float Mk, int32_t Wblock, int literal) {
     md->blk = blk; md->S = S; md->K = K; md->M = blk_M(blk);
+    md->literal = literal;
     md->Rmax = (int64_t)Nodd * S * K;                                 /* Eq. (3) */
     md->b = or_bits(md->Rmax);                                        /* Eq. (6), reading c3 */
     md->ck = or_compand_factor(K, Mk);                                /* Eq. (2) */
     int32_t* kq = calloc((size_t)Nodd + 1, sizeof(int32_t));
     if (!kq) return OR_ERR_ARG;
     or_compand(kr, N, md->ck, kq);                                    /* k~[N..N'] = 0 */
-    if (blk == OR_BLK_SYM) {
+    if (blk == OR_BLK_SYM && literal) {
+        /* Eq. (5) with the paper's eps^-1 = 2 R_max (pair order as reading c2):
+         * kbar[n] = k~[2n+1] + eps^-1 k~[2n], an exact integer in FP64 */
+        md->nk = (Nodd + 1) / 2;
+        md->kpk = malloc(sizeof(double) * (size_t)md->nk);
+        if (md->kpk) {
+            double einv = 2.0 * (double)md->Rmax;
+            for (int32_t n = 0; n < md->nk; ++n) {
+                double ko = (2 * n + 1 < Nodd) ? (double)kq[2 * n + 1] : 0.0;
+                md->kpk[n] = ko + einv * (double)kq[2 * n];
+            }
+        }
+        md->l1 = 0.0;
+    } else if (blk == OR_BLK_SYM) {
         md->nk = (Nodd + 1) / 2;
         md->kpk = malloc(sizeof(double) * (size_t)md->nk);
         or_pack_sym_kernel(kq, Nodd, md->b, md->kpk);                 /* Eq. (5), c2 */
@@ -612,7 +627,17 @@ static int run_packed_block(const mode_t_* md, const or_plan_t* p, int64_t i, co
         if (!(ferr < 0.25)) return 0;
     }
     int32_t Wstart = (!fft && i == 0) ? 0 : (Nodd - 1) / 2;          /* Eq. (10) */
-    if (md->blk == OR_BLK_SYM) {
+    if (md->literal) {
+        /* the paper's own form: eps of Eq. (6), Eq. (4) and Eq. (9) in FP64,
+         * Eqs. (11)-(15) in FP64 with u_sys; rounding may move a digit */
+        int32_t nbar = Wb / 2;
+        double eps_l = 1.0 / (2.0 * (double)md->Rmax);
+        for (int32_t m = 0; m < nbar; ++m) sbar[m] = (double)q[2 * m] + eps_l * (double)q[2 * m + 1];
+        or_conv_f64(sbar, nbar, md->kpk, md->nk, rbar, nbar);
+        double* rqd = rbar + nbar;                                    /* spare room after rbar */
+        or_unpack_sym_fp64(rbar, nbar, Wstart, (double)md->Rmax, eps_l, OR_U_SYS, rqd);
+        for (int32_t j = 0; j < 2 * nbar; ++j) rq_blk[j] = (int64_t)rqd[j];
+    } else if (md->blk == OR_BLK_SYM) {
         int32_t nbar = Wb / 2;
         or_pack_sym_signal(q, Wb, md->b, sbar);                       /* Eq. (4) */
         or_conv_f64(sbar, nbar, md->kpk, md->nk, rbar, nbar);         /* Eq. (9) */
@@ -638,6 +663,9 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     if (op > OR_OP_XCORR || (core != OR_CORE_DIRECT && core != OR_CORE_FFT) || pack > OR_PACK_ASYM3)
         return OR_ERR_ARG;
     int fft = core == OR_CORE_FFT;
+    /* the paper-literal form: symmetric packing, direct core, fixed quantiser */
+    int literal = (mode & OR_LITERAL) != 0;
+    if (literal && (fft || pack != OR_PACK_SYM)) return OR_ERR_ARG;
     or_plan_t p;
     int rc = or_plan(L, N, Wblock, fft, &p);
     if (rc) return rc;
@@ -660,14 +688,15 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
             for (int j = 0; j < 3; ++j) {
                 int32_t Q = fft ? or_qmax_fft(order[j], Nodd, Wb) : or_qmax_direct(order[j], Nodd);
                 if (Q < 1) continue;
-                if (prep_mode(&modes[nmodes], order[j], Q, Q, kr, N, Nodd, Mk, Wb)) { rc = OR_ERR_ARG; break; }
+                if (prep_mode(&modes[nmodes], order[j], Q, Q, kr, N, Nodd, Mk, Wb, 0)) { rc = OR_ERR_ARG; break; }
                 ++nmodes;
             }
         } else if (pack != OR_PACK_NONE) {
             int blk = pack == OR_PACK_SYM ? OR_BLK_SYM : (pack == OR_PACK_ASYM2 ? OR_BLK_ASYM2 : OR_BLK_ASYM3);
             if (Sq_fixed < 1 || Kq_fixed < 1 || Sq_fixed > (1 << 20) || Kq_fixed > (1 << 20)) rc = OR_ERR_ARG;
-            else if (!or_exact_ok(blk, Nodd, Sq_fixed, Kq_fixed)) rc = OR_ERR_RANGE;
-            else if (prep_mode(&modes[0], blk, Sq_fixed, Kq_fixed, kr, N, Nodd, Mk, Wb)) rc = OR_ERR_ARG;
+            else if (literal && (int64_t)Nodd * Sq_fixed * Kq_fixed > ((int64_t)1 << 31)) rc = OR_ERR_RANGE;
+            else if (!literal && !or_exact_ok(blk, Nodd, Sq_fixed, Kq_fixed)) rc = OR_ERR_RANGE;
+            else if (prep_mode(&modes[0], blk, Sq_fixed, Kq_fixed, kr, N, Nodd, Mk, Wb, literal)) rc = OR_ERR_ARG;
             else nmodes = 1;
         }
     }

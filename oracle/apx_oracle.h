@@ -36,6 +36,11 @@ extern "C" {
 #define OR_PACK_ASYM2   0x300u
 #define OR_PACK_ASYM3   0x400u
 #define OR_PACK_MASK    0xF00u
+/* with OR_PACK_SYM on the direct core and a fixed quantiser: the paper's own
+ * packing coefficient eps = (2 R_max)^-1 (Eq. 6) and Eqs. (11)-(15) in FP64
+ * with u_sys (Section IV) instead of the exact power-of-two form */
+#define OR_LITERAL      0x2000u
+#define OR_U_SYS        3.1193e-11  /* Section IV, from the machine-precision measurement the paper cites */
 
 /* per-block mode codes (what a block actually ran) */
 #define OR_BLK_FULL  0

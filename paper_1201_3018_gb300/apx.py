@@ -25,6 +25,7 @@ OP_CONV, OP_XCORR = 0x000, 0x001
 CORE_DIRECT, CORE_FFT, CORE_AUTO = 0x000, 0x010, 0x020
 PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
 FULL_FP64 = 0x1000
+LITERAL = 0x2000
 BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
 
 # apx_request as a numpy record (64 bytes, natural C alignment)

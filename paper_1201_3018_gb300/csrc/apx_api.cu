@@ -216,9 +216,11 @@ struct Plan {
 int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
     if (L < 1 || N < 1) return APX_ERR_ARG;
     if ((mode & 0xFu) > APX_OP_XCORR || ((mode >> 4) & 0xFu) > 1u || ((mode >> 8) & 0xFu) > 4u ||
-        (mode & ~(0xFFFu | APX_FULL_FP64)))
+        (mode & ~(0xFFFu | APX_FULL_FP64 | APX_LITERAL)))
         return APX_ERR_ARG;
     if ((mode & APX_FULL_FP64) && ((mode & 0xF00u) != APX_PACK_NONE || (mode & 0xF0u) != APX_CORE_DIRECT))
+        return APX_ERR_ARG;
+    if ((mode & APX_LITERAL) && ((mode & 0xF00u) != APX_PACK_SYM || (mode & 0xF0u) != APX_CORE_DIRECT))
         return APX_ERR_ARG;
     int fft = (mode & 0xF0u) == APX_CORE_FFT;
     int Nodd = (N % 2) ? N : N + 1;
@@ -404,8 +406,14 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     } else if (sel_kind == 1) {
         int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
         if (S < 1 || K < 1 || S > (1 << 20) || K > (1 << 20)) return APX_ERR_ARG;
-        if (!exact_ok(blk, pl.Nodd, S, K)) return APX_ERR_RANGE;
-        p.cand[nc++] = make_cand(blk, S, K, pl.Nodd, Wb);
+        const bool literal = (mode & APX_LITERAL) != 0;
+        if (literal ? (long long)pl.Nodd * S * K > (1LL << 31) : !exact_ok(blk, pl.Nodd, S, K)) return APX_ERR_RANGE;
+        Cand c = make_cand(blk, S, K, pl.Nodd, Wb);
+        if (literal) {  // Eq. (6) as printed
+            c.literal = 1;
+            c.eps_l = 1.0 / (2.0 * (double)c.Rmax);
+        }
+        p.cand[nc++] = c;
     }
 
     // Shared memory of the block kernel for this candidate set.
@@ -568,6 +576,7 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
         if (q.N < 1) return APX_ERR_ARG;
         const int Nodd = (q.N % 2) ? q.N : q.N + 1;
         uint32_t mode = q.mode;
+        if (mode & APX_LITERAL) return APX_ERR_ARG;  // the paper-literal form: single calls only
         uint32_t core = mode & 0xF0u;
         if (core == APX_CORE_AUTO) core = default_core_fft(Nodd) ? APX_CORE_FFT : APX_CORE_DIRECT;
         mode = (mode & ~0xF0u) | core;

@@ -249,6 +249,34 @@ __device__ __forceinline__ long long unpack_sym(const Cand& c, int j, int wstart
     return sinv + se - 2 * c.Rmax;
 }
 
+// The paper's own form (APX_LITERAL): eps = (2 R_max)^-1 (Eq. 6) and Eqs.
+// (11)-(15) in FP64 on the packed outputs rbar, with R_safe = R_max (eps + 1 +
+// eps^-1) + u_sys eps^-1 and u_sys = 3.1193e-11 (Section IV).  Every operation
+// is one correctly rounded FP64 step in the order the equations give them
+// (no contraction), so the result is a function of rbar alone; rounding can
+// move a digit, which is what the paper's SNR measurements include.
+constexpr double kUsys = 3.1193e-11;
+__device__ __forceinline__ long long unpack_sym_literal(const Cand& c, int j, int wstart, const double* rbar) {
+    const int m = j >> 1;
+    const double R = (double)c.Rmax, eps = c.eps_l, einv = __ddiv_rn(1.0, eps);
+    const double Rsafe = __dadd_rn(__dmul_rn(R, __dadd_rn(__dadd_rn(eps, 1.0), einv)), __dmul_rn(kUsys, einv));
+    const double u = __dadd_rn(rbar[m], Rsafe);                                  // (11)
+    const double sinv = floor(__dmul_rn(eps, u));                                 // (13)
+    if (j & 1) return (long long)floor(__dsub_rn(__dsub_rn(floor(u), __dmul_rn(einv, sinv)), R));  // (15)
+    double se = R;                                                                // (12)
+    if (m != wstart) {
+        const double up = __dadd_rn(rbar[m - 1], Rsafe);
+        se = __dmul_rn(einv, __dsub_rn(up, floor(up)));
+    }
+    return (long long)floor(__dsub_rn(__dadd_rn(sinv, se), __dmul_rn(2.0, R)));   // (14)
+}
+// Eq. (5) with the paper's eps^-1 = 2 R_max (pair order as in kbar_int): an
+// exact integer in FP64.
+__device__ __forceinline__ double kbar_literal(const Params& p, const Cand& c, float ck, int n) {
+    if (n >= c.nk) return 0.0;
+    return __dadd_rn((double)kq(p, ck, 2 * n + 1), __dmul_rn(__dmul_rn(2.0, (double)c.Rmax), (double)kq(p, ck, 2 * n)));
+}
+
 // Asymmetric unpacking: digit q of T[i] offset by R_max, overlap-added over the
 // M segments: r~[j] = sum_q c_q[j - q Ls], with packed outputs i < nr.
 template <typename F>

@@ -60,9 +60,36 @@ __device__ __forceinline__ void conv_f64(const double* sig, const double* taps, 
     }
 }
 
+// The same sums as separate correctly rounded products and additions, in the
+// same order (the paper-literal form: the oracle's arithmetic step for step).
+template <int R>
+__device__ __forceinline__ void conv_f64_nofma(const double* sig, const double* taps, int nkp, int j0,
+                                               double (&acc)[R]) {
+    double w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc[r] = 0.0; w[r] = sig[j0 + r]; }
+    for (int n = 0; n < nkp; n += R) {
+        double t[R];
+#pragma unroll
+        for (int v = 0; v < R; v += 2) {
+            double2 q = *reinterpret_cast<const double2*>(taps + n + v);
+            t[v] = q.x; t[v + 1] = q.y;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = __dadd_rn(acc[r], __dmul_rn(w[(r - u + R) % R], t[u]));
+            w[R - 1 - u] = sig[j0 - n - u - 1];
+        }
+    }
+}
+
 __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
-template <bool BATCH>
+// LIT: the paper-literal symmetric form (APX_LITERAL, single calls only) in
+// an instantiation of its own, so that the other kernels are compiled as if
+// it did not exist.
+template <bool BATCH, bool LIT>
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
@@ -144,12 +171,13 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     const Cand& c = p.cand[ci];
     const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
     const float ck = compand_factor(c.K, ks.Mk);
-    const double eps = ldexp(1.0, -c.b);
+    const double eps = LIT ? c.eps_l : ldexp(1.0, -c.b);
     double* sb = reinterpret_cast<double*>(smem + dl.offS) + dl.padS;
     double* tb = reinterpret_cast<double*>(smem + dl.offT);
     double* kb = reinterpret_cast<double*>(smem + dl.offKb);
     const int nkp = round_up(c.nk, kRd);
-    for (int n = threadIdx.x; n < nkp; n += blockDim.x) kb[n] = (double)kbar_int(p, c, ck, n);  // Eq. (5) / k~
+    for (int n = threadIdx.x; n < nkp; n += blockDim.x)  // Eq. (5) / k~
+        kb[n] = LIT ? kbar_literal(p, c, ck, n) : (double)kbar_int(p, c, ck, n);
     int nsb, Ls = 0;
     if (c.blk == APX_BLK_SYM) {
         nsb = p.Wb / 2;
@@ -187,7 +215,8 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
         const int j0 = olo + ch * kRd;
         double acc[kRd];
-        conv_f64<kRd>(sb, kb, nkp, j0, acc);
+        if (LIT) conv_f64_nofma<kRd>(sb, kb, nkp, j0, acc);
+        else conv_f64<kRd>(sb, kb, nkp, j0, acc);
 #pragma unroll
         for (int r = 0; r < kRd; ++r)
             if (j0 + r < ohi) tb[j0 + r] = acc[r];
@@ -202,7 +231,9 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
         if (o < 0 || o >= p.out_len) continue;
-        long long rt = c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat) : unpack_asym(c, j, Ls, nr, Tat);
+        long long rt = LIT                      ? unpack_sym_literal(c, j, g.wstart, tb)
+                       : c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat)
+                                              : unpack_asym(c, j, Ls, nr, Tat);
         p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
         if (p.rq) p.rq[o] = (int)rt;
     }
@@ -210,30 +241,32 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
-template <bool BATCH>
+template <bool BATCH, bool LIT>
 static cudaError_t direct_attrs() {
     static int attr_dev = -1;
     int dev;
     cudaGetDevice(&dev);
     if (attr_dev == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_direct<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_direct<BATCH, LIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess) attr_dev = dev;
     return e;
 }
 
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
-    cudaError_t e = direct_attrs<false>();
+    const bool lit = p.ncand == 1 && p.cand[0].literal;
+    cudaError_t e = lit ? direct_attrs<false, true>() : direct_attrs<false, false>();
     if (e != cudaSuccess) return e;
     if (p.P <= 0) return cudaSuccess;
     const BatchTab none = {nullptr, nullptr, 0};
-    return launch_k(k_direct<false>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
+    if (lit) return launch_k(k_direct<false, true>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
+    return launch_k(k_direct<false, false>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
 }
 
 cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {
-    cudaError_t e = direct_attrs<true>();
+    cudaError_t e = direct_attrs<true, false>();
     if (e != cudaSuccess) return e;
     if (ctas <= 0) return cudaSuccess;
-    return launch_k(k_direct<true>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
+    return launch_k(k_direct<true, false>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
 }
 
 }  // namespace apx

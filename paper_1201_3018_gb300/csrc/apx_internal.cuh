@@ -38,6 +38,8 @@ struct Cand {
     int log2n;        // FFT core: log2 of the real transform length
     double fftc;      // FFT core: (3 phi + 16 u) for log2n (error-bound constant)
     double2* H;       // FFT core: kernel spectrum FFT_n(kbar) / (4m), m+1 entries (built on demand)
+    int literal;      // APX_LITERAL: eps = eps_l = (2 R_max)^-1, FP64 unpacking with u_sys
+    double eps_l;
 };
 
 // Kernel statistics published by the FFT core's spectrum launch.

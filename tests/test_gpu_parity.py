@@ -364,3 +364,43 @@ def test_host_entry_equals_device_path_large(ctx, core, L, N, Wb, mode_bits, snr
             ctx.apx_conv(dev(s), dev(k), Wb, mode, snr, r)
         assert ctx.apx_sync() == 0
         np.testing.assert_array_equal(out.numpy(), r.cpu().numpy())
+
+
+@pytest.mark.parametrize("L,N,Q,Wb,op,dist", [
+    (20000, 65, 8, 1024, apx.OP_CONV, "uniform"),        # small range: the exact form's digits
+    (1 << 16, 800, 16, 8192, apx.OP_CONV, "u128"),       # Section IV.A's symmetric setting, beyond the exact bound
+    (30000, 257, 16, 2048, apx.OP_XCORR, "laplace"),
+])
+def test_paper_literal_form_matches_oracle(ctx, L, N, Q, Wb, op, dist):
+    """APX_LITERAL (Eq. 6 eps, FP64 Eqs. 11-15 with u_sys, packed convolution
+    without fused multiply-adds) on the direct core: the same integers as the
+    oracle's literal form, bit for bit, digits moved by rounding included."""
+    g = np.random.default_rng(L + N + Q)
+    if dist == "u128":
+        s, k = g.uniform(-128, 128, L).astype(np.float32), g.uniform(-128, 128, N).astype(np.float32)
+    else:
+        s, k = wl.random_signal(L + 5, L, dist, 0.1), wl.random_signal(N + 6, N, "uniform")
+    mode = op | apx.CORE_DIRECT | apx.PACK_SYM | apx.LITERAL
+    check(*run_both(ctx, s, k, Wb, mode, Sq=Q, Kq=Q), s, k, mode, Wb)
+
+
+def test_paper_literal_form_rejections(ctx):
+    s, k = dev(np.ones(5000, np.float32)), dev(np.ones(65, np.float32))
+    for mode in (apx.CORE_FFT | apx.PACK_SYM | apx.LITERAL, apx.CORE_DIRECT | apx.PACK_ASYM2 | apx.LITERAL,
+                 apx.CORE_DIRECT | apx.PACK_AUTO | apx.LITERAL):
+        with pytest.raises(apx.ApxError) as e:
+            ctx.conv(s, k, 1024, mode, Sq=8, Kq=8)
+        assert e.value.status == apx.APX_ERR_ARG
+    with pytest.raises(apx.ApxError) as e:  # R_max = 65 * 2^20 * 2^20 > 2^31
+        ctx.conv(s, k, 1024, apx.CORE_DIRECT | apx.PACK_SYM | apx.LITERAL, Sq=1 << 20, Kq=1 << 20)
+    assert e.value.status == apx.APX_ERR_RANGE
+
+
+def test_paper_literal_form_not_batched(ctx):
+    s, k = dev(np.ones(5000, np.float32)), dev(np.ones(65, np.float32))
+    r = torch.empty(5064, device="cuda")
+    reqs = ctx.make_requests([dict(s=s, k=k, r=r, mode=apx.CORE_DIRECT | apx.PACK_SYM | apx.LITERAL, W_block=1024,
+                                   Sq=8, Kq=8)])
+    with pytest.raises(apx.ApxError) as e:
+        ctx.apx_conv_batch(reqs)
+    assert e.value.status == apx.APX_ERR_ARG

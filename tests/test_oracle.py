@@ -225,6 +225,42 @@ def test_sym_paper_literal_fp64_form():
     assert np.mean(rq == ref) > 0.9
 
 
+@pytest.mark.parametrize("N,Q", [(65, 8), (257, 16), (9, 40)])
+def test_literal_pipeline_equals_exact_form_on_small_ranges(N, Q):
+    """The paper-literal symmetric form (Eq. 6 eps, FP64 Eqs. 11-15 with
+    u_sys) through the whole pipeline gives the exact form's integers where
+    the range is small enough for FP64 to keep the three digits apart."""
+    g = np.random.default_rng(N + Q)
+    s = g.uniform(-1, 1, 20000).astype(np.float32)
+    k = g.uniform(-1, 1, N).astype(np.float32)
+    _, qa, _, rca = O.apx_conv(s, k, 1024, O.CORE_DIRECT | O.PACK_SYM, Sq=Q, Kq=Q)
+    _, qb, _, rcb = O.apx_conv(s, k, 1024, O.CORE_DIRECT | O.PACK_SYM | O.LITERAL, Sq=Q, Kq=Q)
+    assert rca == rcb == 0
+    assert np.array_equal(qa, qb)
+
+
+def test_literal_pipeline_at_the_papers_symmetric_setting():
+    """Section IV.A's symmetric setting (N = 800, S_q = K_q = 16, inputs
+    U[-128, 128]) is beyond the exact form's bound (R_max = 205056 > 131071),
+    so only the literal form runs it: rounding moves digits of the side
+    outputs, but the SNR is that of the companding alone (the exact asym2 form
+    at the same S_q, K_q) and matches the Table 1 estimate printed for it."""
+    g = np.random.default_rng(44)
+    s = g.uniform(-128, 128, 1 << 16).astype(np.float32)
+    k = g.uniform(-128, 128, 800).astype(np.float32)
+    ref = O.conv_ref(s, k)
+    _, _, _, rc = O.apx_conv(s, k, 8192, O.CORE_DIRECT | O.PACK_SYM, Sq=16, Kq=16)
+    assert rc == O.ERR_RANGE
+    r, q, _, rc = O.apx_conv(s, k, 8192, O.CORE_DIRECT | O.PACK_SYM | O.LITERAL, Sq=16, Kq=16)
+    assert rc == 0
+    ra, qa, _, rca = O.apx_conv(s, k, 8192, O.CORE_DIRECT | O.PACK_ASYM2, Sq=16, Kq=16)
+    assert rca == 0
+    snr = lambda x: 10 * math.log10(np.sum(ref ** 2) / np.sum((x.astype(np.float64) - ref) ** 2))
+    assert abs(snr(r) - snr(ra)) < 0.05
+    assert abs(snr(r) - GOLD["snr_model_db"]["Sq16"]) < 0.3
+    assert np.mean(q != qa) > 0.1  # the rounding did move digits: this is not the exact form
+
+
 @pytest.mark.parametrize("M", [2, 3])
 @pytest.mark.parametrize("nodd,n", [(1, 8), (3, 31), (65, 1024), (257, 700), (801, 1000)])
 def test_asym_pack_unpack_reconstructs_integer_conv(M, nodd, n):
