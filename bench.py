@@ -651,7 +651,22 @@ def main():
     t_e2e_ms = time_steps(step_e2e, args.steps, flush, stream)
     barrier()
 
-    t_ms, t_full_ms, t_e2e_ms = max_over_ranks([t_ms, t_full_ms, t_e2e_ms], dist, dev)
+    # the same template prepared once and kept resident (template matching against many
+    # signals): one block-kernel launch per call, no per-call kernel preparation
+    kp = ctx.prepare_kernel(k, Wb, mode, stream=stream)
+
+    def step_prepared():
+        ctx.apx_conv_prepared(kp, s, TARGET_DB, r, stream=stream)
+
+    for _ in range(3):
+        step_prepared()
+    barrier()
+    t_prep_ms = time_steps(step_prepared, args.steps, flush, stream)
+    barrier()
+    ctx.apx_sync(stream)
+    kp.close()
+
+    t_ms, t_full_ms, t_e2e_ms, t_prep_ms = max_over_ranks([t_ms, t_full_ms, t_e2e_ms, t_prep_ms], dist, dev)
     per_step = t_ms / args.steps
     value = whole_job_gsamples(out_len, world, per_step)
     full_value = whole_job_gsamples(out_len, world, t_full_ms / args.steps)
@@ -712,6 +727,10 @@ def main():
         "config": dict(config_dict(case), parallelism="replicas" if world > 1 else "single"),
         "full_precision": {"value": full_value, "unit": UNIT, "ms_per_step": t_full_ms / args.steps},
         "speedup_vs_full_precision": value / full_value,
+        "prepared_kernel": {"value": whole_job_gsamples(out_len, world, t_prep_ms / args.steps), "unit": UNIT,
+                            "ms_per_step": t_prep_ms / args.steps,
+                            "note": "the template prepared once (apx_kernel_create) and reused by every step; "
+                                    "the headline value prepares it in every call"},
         "block_modes": {"full": hist[0], "sym": hist[1], "asym2": hist[2], "asym3": hist[3], "zero": hist[4],
                         "nonfinite": hist[5]},
         "snr_vs_full_db": snr_vs_full,

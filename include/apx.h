@@ -282,6 +282,31 @@ int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_ba
                    int32_t S_q, int32_t K_q, float* y_out, int64_t ldy, int32_t* yq_out, float* block_cs,
                    void* stream);
 
+/* ---- prepared kernels (resident across calls) ----------------------------
+ * Section IV prepares the kernel once per request; a caller that convolves
+ * many signals with the same kernel (template matching against a stream of
+ * inputs, a filter applied block after block) can prepare it once instead.
+ * apx_kernel_create copies the N taps into the handle's own device memory and
+ * computes there the kernel statistics, the exact packed-kernel norms and the
+ * FP32 spectrum (FFT core); the FP64 packed spectra are built by the first
+ * call whose blocks select each packing and kept.  Everything stays resident
+ * until apx_kernel_destroy (the handle's memory is its own, outside the
+ * context budget; the caller's tap buffer may be reused once `stream` has
+ * passed the creation).
+ *   mode : op | APX_CORE_FFT | APX_PACK_AUTO or APX_PACK_NONE
+ * apx_conv_prepared then runs one call: the same as apx_conv (APX_PACK_AUTO,
+ * per-block selection under snr_target_db) or apx_conv_full (APX_PACK_NONE)
+ * with this kernel, as one launch of the block kernel, with the same results
+ * bit for bit.  Calls with one handle on different streams may overlap (the
+ * on-demand spectra are built once either way); the handle must outlive them.
+ * Errors: APX_ERR_ARG (other cores or packings), as apx_conv otherwise. */
+typedef struct apx_kernel apx_kernel;
+int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_t W_block, uint32_t mode, void* stream,
+                      apx_kernel** out);
+int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float* s_in, int64_t L, double snr_target_db,
+                      float* r_out, int32_t* rq_out, apx_block_stats* stats, void* stream);
+void apx_kernel_destroy(apx_kernel* kp);
+
 /* ---- allocation-free FFT core ---------------------------------------------
  * The paper has no counterpart: this is a deployment variant of apx_conv with
  * the FFT core for callers that may not allocate device memory once they are

@@ -65,6 +65,9 @@ SIGNATURES = {
     "apx_graph_launch": (C.c_int, [_vp, _vp]),
     "apx_graph_launch_count": (_i64, [_vp]),
     "apx_graph_destroy": (None, [_vp]),
+    "apx_kernel_create": (C.c_int, [_vp, _vp, _i32, _i32, _u32, _vp, C.POINTER(C.c_void_p)]),
+    "apx_conv_prepared": (C.c_int, [_vp, _vp, _vp, _i64, C.c_double, _vp, _vp, _vp, _vp]),
+    "apx_kernel_destroy": (None, [_vp]),
     "apx_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "apx_conv_batch_host": (C.c_int, [_vp, _vp, _i32, _vp]),
     "apx_test_stall_next": (C.c_int, [_vp]),
@@ -157,6 +160,24 @@ class Graph:
     def close(self):
         if getattr(self, "_h", None):
             lib().apx_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PreparedKernel:
+    """A kernel prepared once and kept resident (apx_kernel)."""
+
+    def __init__(self, h, N, W_block, mode):
+        self._h, self.N, self.W_block, self.mode = h, N, W_block, mode
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apx_kernel_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -288,6 +309,20 @@ class Context:
         whose pointers are host addresses."""
         ptr = reqs.ctypes.data if isinstance(reqs, np.ndarray) else C.cast(reqs, C.c_void_p).value
         return _check("apx_conv_batch_host", lib().apx_conv_batch_host(self._h, ptr, len(reqs), _stream(stream)))
+
+    def prepare_kernel(self, k, W_block, mode, stream=None):
+        """apx_kernel_create: returns a PreparedKernel (FFT core, PACK_AUTO or
+        PACK_NONE)."""
+        _dev_f32(k, "k")
+        h = C.c_void_p()
+        _check("apx_kernel_create", lib().apx_kernel_create(self._h, _ptr(k), k.numel(), W_block, mode,
+                                                             _stream(stream), C.byref(h)))
+        return PreparedKernel(h, k.numel(), W_block, mode)
+
+    def apx_conv_prepared(self, kp, s, snr_db, r, rq=None, stats=None, stream=None):
+        _dev_f32(s, "s_in"); _dev_f32(r, "r_out")
+        return _check("apx_conv_prepared", lib().apx_conv_prepared(self._h, kp._h, _ptr(s), s.numel(), float(snr_db),
+                                                                   _ptr(r), _ptr(rq), _ptr(stats), _stream(stream)))
 
     def graph(self, reqs, stream=None):
         """Capture the batch once; returns a Graph (launch() replays it)."""

@@ -1073,6 +1073,136 @@ extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const 
     return cuda_status(e);
 }
 
+// ------------------------------------------------------------------ prepared kernels
+// A kernel's preparation kept resident: its own device arena holds the
+// claim/ready words of its packed spectra, a copy of the taps, the kernel
+// statistics, the FP32 spectrum with its decimated sub-spectra, and the packed
+// spectra.  The epoch is fixed, so a packed spectrum built by one call is
+// ready for every later one.
+struct apx_kernel {
+    int device = 0;
+    int32_t N = 0, W_block = 0;
+    uint32_t mode = 0;
+    void* arena = nullptr;
+    float* taps = nullptr;
+    Params prep;  // the kernel half of the parameters (pointers into the arena)
+};
+
+extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_t W_block, uint32_t mode,
+                                 void* stream, apx_kernel** out) {
+    if (!ctx || !k || !out || N < 1) return APX_ERR_ARG;
+    *out = nullptr;
+    const uint32_t pack = mode & 0xF00u;
+    if ((mode & 0xF0u) != APX_CORE_FFT || (pack != APX_PACK_AUTO && pack != APX_PACK_NONE) || (mode & ~0xFFFu))
+        return APX_ERR_ARG;
+    // the candidate set depends on N, W_block and the mode only: plan a one-sample call
+    Params p;
+    size_t smem = 0;
+    int rc = make_params(k, 1, k, N, W_block, mode, pack == APX_PACK_NONE ? 2 : 0, 0.0, 0, 0, (float*)k, nullptr,
+                         nullptr, &p, &smem);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+    if (!rc) rc = ensure_twiddles(ctx, W_block, (cudaStream_t)stream);
+    if (rc) return rc;
+    const size_t m1 = (size_t)W_block / 2 + 1;
+    const size_t off_taps = 256, off_ki = off_taps + al256b(sizeof(float) * (size_t)N);
+    const size_t off_h = off_ki + al256b(sizeof(KInfo)), off_y = off_h + al256b(sizeof(float2) * (m1 + 1));
+    const size_t off_c = off_y + al256b(sizeof(float2) * (size_t)W_block);
+    const size_t bytes = off_c + (size_t)p.ncand * al256b(sizeof(double2) * m1);
+    apx_kernel* kp = new apx_kernel();
+    kp->device = ctx->device;
+    kp->N = N;
+    kp->W_block = W_block;
+    kp->mode = mode;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&kp->arena, bytes);
+    if (e != cudaSuccess) { kp->arena = nullptr; delete kp; return cuda_status(e); }
+    unsigned char* a = (unsigned char*)kp->arena;
+    kp->taps = (float*)(a + off_taps);
+    e = cudaMemsetAsync(a, 0, 256, st);  // claim and ready words
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kp->taps, k, sizeof(float) * (size_t)N, cudaMemcpyDeviceToDevice, st);
+    p.s = kp->taps;
+    p.k = kp->taps;
+    p.r = (float*)kp->taps;
+    p.status = (unsigned*)ctx->flags.p;
+    p.claim = (unsigned*)a;
+    p.ready = (unsigned*)a + kMaxCand;
+    p.epoch = 1;
+    p.ki = (KInfo*)(a + off_ki);
+    p.Hfull = (float2*)(a + off_h);
+    p.Ysub = (float2*)(a + off_y);
+    for (int j = 0; j < p.ncand; ++j) p.cand[j].H = (double2*)(a + off_c + (size_t)j * al256b(sizeof(double2) * m1));
+    p.tw64 = (const double2*)ctx->tw64.p;
+    p.tw32 = (const float2*)ctx->tw32.p;
+    p.ntab = ctx->tw_wb;
+    p.autosel = 0;  // the norms of every candidate: the target is chosen per call
+    if (e == cudaSuccess) {
+        Trace t(ctx, st, APX_PHASE_SPECTRA);
+        e = launch_spec(p, st);
+        if (e == cudaSuccess) e = launch_spec_combine(p, st);
+        ctx->launches += 2;
+    }
+    if (e != cudaSuccess) {
+        cudaFree(kp->arena);
+        delete kp;
+        return cuda_status(e);
+    }
+    kp->prep = p;
+    *out = kp;
+    return APX_OK;
+}
+
+extern "C" int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float* s_in, int64_t L,
+                                 double snr_target_db, float* r_out, int32_t* rq_out, apx_block_stats* stats,
+                                 void* stream) {
+    if (!ctx || !kp || !s_in || !r_out) return APX_ERR_ARG;
+    if (kp->device != ctx->device) return APX_ERR_ARG;
+    Range range("apx_conv_prepared");
+    const int sel = (kp->mode & 0xF00u) == APX_PACK_NONE ? 2 : 0;
+    Params p;
+    size_t smem = 0;
+    int rc = make_params(s_in, L, kp->taps, kp->N, kp->W_block, kp->mode, sel, snr_target_db, 0, 0, r_out, rq_out,
+                         stats, &p, &smem);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
+    if (!rc) rc = ensure_twiddles(ctx, kp->W_block, st);
+    if (rc) return rc;
+    const Params& q = kp->prep;
+    for (int j = 0; j < p.ncand; ++j) p.cand[j].H = q.cand[j].H;
+    p.status = (unsigned*)ctx->flags.p;
+    p.claim = q.claim;
+    p.ready = q.ready;
+    p.epoch = q.epoch;
+    p.ki = q.ki;
+    p.Hfull = q.Hfull;
+    p.Ysub = q.Ysub;
+    p.tw64 = (const double2*)ctx->tw64.p;
+    p.tw32 = (const float2*)ctx->tw32.p;
+    p.ntab = ctx->tw_wb;
+    p.fused = 0;
+    if (!device_pointers_set(p)) return APX_ERR_CUDA;
+    cudaError_t e;
+    {
+        Trace t(ctx, st, APX_PHASE_FFT);
+        e = launch_fft(p, smem, st, false);  // the preparation is resident: not a dependent launch
+        ctx->launches += 1;
+    }
+    return cuda_status(e);
+}
+
+extern "C" void apx_kernel_destroy(apx_kernel* kp) {
+    if (!kp) return;
+    {
+        DeviceGuard dg(kp->device);
+        cudaDeviceSynchronize();
+        if (kp->arena) cudaFree(kp->arena);
+    }
+    delete kp;
+}
+
 extern "C" int apx_graph_create(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream, apx_graph** out) {
     if (!ctx || !out) return APX_ERR_ARG;
     *out = nullptr;

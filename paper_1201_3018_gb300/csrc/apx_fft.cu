@@ -327,14 +327,16 @@ static cudaError_t fft_attrs() {
     return e;
 }
 
-cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st) {
+// pdl: the programmatic dependent of the preparation launches just before it;
+// false when the kernel's preparation is already resident (a prepared kernel).
+cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st, bool pdl) {
     if (p.P <= 0) return cudaSuccess;
     cudaError_t e = fft_attrs<false>();
     if (e != cudaSuccess) return e;
     const BatchTab none = {nullptr, nullptr, 0};
     if (p.Wb / fft_threads(p.Wb) > 16)
-        return launch_k(k_fft<32, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
-    return launch_k(k_fft<16, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, true, p, none);
+        return launch_k(k_fft<32, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, pdl, p, none);
+    return launch_k(k_fft<16, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, pdl, p, none);
 }
 
 // Fused single call: nj preparation CTAs ahead of the P block CTAs in one

@@ -45,7 +45,7 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 cudaError_t launch_spec(const Params& p, cudaStream_t st);
 cudaError_t launch_spec_combine(const Params& p, cudaStream_t st);
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st);
-cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st);
+cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st, bool pdl = true);
 cudaError_t launch_fft_fused(const Params& p, size_t smem, cudaStream_t st);
 unsigned fused_grid(const Params& p);
 size_t fft_smem_bytes(const Params& p);
