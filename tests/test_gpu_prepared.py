@@ -76,3 +76,41 @@ def test_prepared_kernel_targets_and_rejections(ctx):
         with pytest.raises(apx.ApxError) as e:
             ctx.prepare_kernel(k, Wb, bad)
         assert e.value.status == apx.APX_ERR_ARG
+
+
+@pytest.mark.parametrize("taps", ["nan", "zero", "one"])
+def test_prepared_kernel_degenerate_kernels(ctx, taps):
+    """A non-finite, an all-zero and a one-tap kernel: the prepared call gives
+    what the per-call preparation gives, status included."""
+    N = 1 if taps == "one" else 300
+    k = _dev(wl.random_signal(wl.SEED_BASE + 640, N, "uniform"))
+    if taps == "nan":
+        k[N // 2] = float("nan")
+    elif taps == "zero":
+        k.zero_()
+    s = _dev(wl.random_signal(wl.SEED_BASE + 641, 150000, "laplace", 0.1))
+    mode = apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    Wb = 1024
+    status = []
+    outs = []
+    kp = ctx.prepare_kernel(k, Wb, mode)
+    try:
+        for prepared in (True, False):
+            r = torch.empty(s.numel() + N - 1, device="cuda")
+            if prepared:
+                ctx.apx_conv_prepared(kp, s, 30.0, r)
+            else:
+                ctx.apx_conv(s, k, Wb, mode, 30.0, r)
+            try:
+                status.append(ctx.apx_sync())
+            except apx.ApxError as e:
+                status.append(e.status)
+            outs.append(r.cpu().numpy())
+    finally:
+        kp.close()
+    assert status[0] == status[1]
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    if taps == "nan":
+        assert status[0] == apx.APX_ERR_NONFINITE and np.isnan(outs[0]).all()
+    if taps == "zero":
+        assert status[0] == apx.APX_OK and not outs[0].any()
