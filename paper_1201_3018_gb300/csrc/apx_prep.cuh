@@ -63,13 +63,14 @@ __device__ inline void spec_stats(const Params& p, Shared& sh) {
     double l1s[kMaxCand] = {0.0, 0.0, 0.0};
     const bool ok = !ks.bad && ks.Mk > 0.f;
     // Under per-block selection a candidate whose model SNR misses the target even for the
-    // best window (second moment = squared maximum; the model depends on the window only
-    // through that ratio) is never chosen: skip its norm (1 % margin for rounding).  Lane c
-    // of warp 0 checks candidate c (one FP64 chain for all of them).
+    // best window is never chosen: skip its norm.  The model grows with the window's ratio
+    // sigma^2 / ||s||_inf^2 <= 1, so the best window has ratio 1; the check is made 1 % below
+    // the target, so that rounding can only keep a norm that is not needed, never drop one
+    // that is.  Lane c of warp 0 checks candidate c (one FP64 chain for all of them).
     if (threadIdx.x < 32) {
         const int c = threadIdx.x;
         const bool reach = c < p.ncand && (!p.autosel || snr_feasible(1.0, 1.f, ks.sig2k, ks.Mk, p.cand[c].S,
-                                                                      p.cand[c].K, __dmul_rn(p.thr, 1.01)));
+                                                                      p.cand[c].K, __dmul_rn(p.thr, 0.99)));
         const unsigned m = __ballot_sync(0xffffffffu, reach);
         if (c == 0) sh.redi[0] = (int)m;
     }

@@ -404,3 +404,24 @@ def test_paper_literal_form_not_batched(ctx):
     with pytest.raises(apx.ApxError) as e:
         ctx.apx_conv_batch(reqs)
     assert e.value.status == apx.APX_ERR_ARG
+
+
+@pytest.mark.parametrize("core,Wb", [(apx.CORE_FFT, 2048), (apx.CORE_FFT, 8192)])
+def test_target_just_below_the_best_case_model_snr(ctx, core, Wb):
+    """Blocks of constant magnitude (every sample +-1: sigma^2 = ||s||_inf^2,
+    the window for which the Section IV.D model is largest) with the target a
+    hair below the best-case model SNR of the first candidate: those blocks
+    pass its model check, so its exact norm must be there for the FFT error
+    bound, which then rejects it (the block is at full scale); per-block
+    decisions, bounds and integers as the oracle's."""
+    g = np.random.default_rng(Wb)
+    N = 255
+    k = g.uniform(-1, 1, N).astype(np.float32)
+    s = np.where(g.random(60000) < 0.5, -1.0, 1.0).astype(np.float32)
+    Mk, s2k = O.maxabs(k), O.second_moment(k)
+    Q = O.qmax_fft(O.BLK_SYM, N, Wb)
+    assert Q >= 1
+    best_db = O.snr_model_db(1.0, 1.0, s2k, Mk, Q, Q)
+    for target in (best_db - 0.02, best_db - 0.001):
+        mode = apx.OP_CONV | core | apx.PACK_AUTO
+        check(*run_both(ctx, s, k, Wb, mode, snr=target), s, k, mode, Wb)
