@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(512) k_fft(const Params p0, const BatchTab bt)
             const double eps = ldexp(1.0, -cd.b);
             const double grow = cd.blk == APX_BLK_SYM ? __dadd_rn(1.0, eps) : __dadd_rn(1.0, __dmul_rn(2.0, eps));
             const double l2 = __dmul_rn(__dsqrt_rn(__ll2double_rn(ss)), grow);
-            sh.bcast[1] = ldexp(__dmul_rn(__dmul_rn(cd.fftc, __ldcg(&p.ki->l1[c])), l2), cd.sc);
+            // a nonzero kernel has ||kbar||_1 >= 1 (its largest tap companded to +-K_q);
+            // 0 means the preparation skipped this candidate: never admit it on that
+            const double l1 = __ldcg(&p.ki->l1[c]);
+            sh.bcast[1] = l1 > 0.0 ? ldexp(__dmul_rn(__dmul_rn(cd.fftc, l1), l2), cd.sc) : 1.0;
         }
         __syncthreads();
         const double E = sh.bcast[1];
