@@ -1086,7 +1086,17 @@ struct apx_kernel {
     void* arena = nullptr;
     float* taps = nullptr;
     Params prep;  // the kernel half of the parameters (pointers into the arena)
+    KInfo stats;  // a host copy of the kernel statistics
 };
+
+// Section IV.D model check on the host, for a candidate-level decision with a
+// margin far above any rounding difference from the device's evaluation.
+static bool snr_feasible_host(double s2s, double Ms, double s2k, double Mk, int S, int K, double thr) {
+    const double S2 = (double)S * S, K2 = (double)K * K, Ms2 = Ms * Ms, Mk2 = Mk * Mk;
+    const double num = 144.0 * (s2s * s2k) * (S2 * K2);
+    const double den = 12.0 * (s2s * S2 * Mk2 + s2k * K2 * Ms2) + Ms2 * Mk2;
+    return num >= thr * den;
+}
 
 extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_t W_block, uint32_t mode,
                                  void* stream, apx_kernel** out) {
@@ -1143,6 +1153,9 @@ extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_
         if (e == cudaSuccess) e = launch_spec_combine(p, st);
         ctx->launches += 2;
     }
+    // the statistics on the host too (creation is a setup step: it waits for them)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kp->stats, p.ki, sizeof(KInfo), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(kp->arena);
         delete kp;
@@ -1165,6 +1178,21 @@ extern "C" int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float
     int rc = make_params(s_in, L, kp->taps, kp->N, kp->W_block, kp->mode, sel, snr_target_db, 0, 0, r_out, rq_out,
                          stats, &p, &smem);
     if (rc) return rc;
+    // With the kernel's statistics known on the host, a target that no packing can reach
+    // even for the best window (model SNR at sigma^2 = ||s||_inf^2, checked 1 % below the
+    // target) leaves every block in full precision: drop the candidates, and with them the
+    // FP64 buffers from the block kernel's shared memory.  The same results: those
+    // candidates fail every block's model check.
+    if (sel == 0 && !kp->stats.bad && kp->stats.Mk > 0.f) {
+        bool any = false;
+        for (int j = 0; j < p.ncand; ++j)
+            any |= snr_feasible_host(1.0, 1.0, kp->stats.sig2k, kp->stats.Mk, p.cand[j].S, p.cand[j].K,
+                                     p.thr * 0.99);
+        if (!any) {
+            p.ncand = 0;
+            smem = fft_smem_bytes(p);
+        }
+    }
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
