@@ -438,8 +438,9 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
 }
 
 // A call from host buffers: the signal's host-to-device copy runs on a copy
-// stream while the caller's stream copies the kernel and (FFT core) prepares
-// its spectrum; the block kernel then waits for the signal copy.
+// stream while the caller's stream copies the kernel and (three-launch FFT
+// core) prepares its spectrum; the block kernel then waits for the signal copy
+// (a one-launch call waits before its first CTA).
 cudaError_t copy_stream_begin(apx_ctx* ctx, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (!ctx->hp_in) e = cudaStreamCreateWithFlags(&ctx->hp_in, cudaStreamNonBlocking);
@@ -854,7 +855,7 @@ int apx_conv_host(apx_ctx* ctx, const float* s_h, int64_t L, const float* k_h, i
     if (!rc) rc = ensure(ctx, ctx->hk, sizeof(float) * (size_t)N);
     if (!rc) rc = ensure(ctx, ctx->hr, sizeof(float) * (size_t)(L + N - 1));
     if (rc) return rc;
-    // the signal copy overlaps the kernel copy and the spectrum preparation
+    // the signal copy overlaps the kernel copy (and a three-launch call's spectrum preparation)
     cudaError_t e = copy_stream_begin(ctx, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->hs.p, s_h, sizeof(float) * (size_t)L, cudaMemcpyHostToDevice, ctx->hp_in);
