@@ -114,3 +114,22 @@ def test_prepared_kernel_degenerate_kernels(ctx, taps):
         assert status[0] == apx.APX_ERR_NONFINITE and np.isnan(outs[0]).all()
     if taps == "zero":
         assert status[0] == apx.APX_OK and not outs[0].any()
+
+
+@pytest.mark.parametrize("L", [1, 100, 5000, 65537])
+def test_prepared_kernel_short_signals(ctx, L):
+    """Signals shorter than the kernel and than one block (the FFT core's head
+    blocks and partial last blocks) through a prepared kernel."""
+    N, Wb = 4096, 16384
+    mode = apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    k = _dev(wl.random_signal(wl.SEED_BASE + 650, N, "uniform"))
+    kp = ctx.prepare_kernel(k, Wb, mode)
+    try:
+        s = _dev(wl.random_signal(wl.SEED_BASE + 651 + L, L, "laplace", 0.1))
+        got = torch.empty(L + N - 1, device="cuda")
+        ctx.apx_conv_prepared(kp, s, 30.0, got)
+        ref, _, _ = ctx.conv(s, k, Wb, mode, snr_db=30.0)
+        assert ctx.apx_sync() == 0
+        assert torch.equal(got, ref)
+    finally:
+        kp.close()
