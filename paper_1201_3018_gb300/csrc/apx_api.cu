@@ -715,8 +715,6 @@ int stage_upload(apx_ctx* c, const void* src1, size_t n1, void* dst1, const void
     }
     if (c->hstage_bytes < need) {
         if (c->hstage) cudaFreeHost(c->hstage);
-        if (c->hp_in) cudaStreamDestroy(c->hp_in);
-        for (cudaEvent_t e : c->hp_ev) cudaEventDestroy(e);
         c->hstage = nullptr;
         c->hstage_bytes = 0;
         if (cudaMallocHost(&c->hstage, need) != cudaSuccess) { c->hstage = nullptr; return APX_ERR_OOM; }

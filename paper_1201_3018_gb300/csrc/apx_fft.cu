@@ -367,4 +367,10 @@ cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, si
     return launch_k(k_fft<16, true>, dim3((unsigned)ctas), dim3(fft_threads(any.Wb)), smem, st, true, any, bt);
 }
 
+// A batched launch's static shared memory (the block scratch, the request's
+// parameters and two flags) has to fit beside the dynamic cap: a larger Params
+// or Shared makes setting that cap fail.
+static_assert(sizeof(Shared) + sizeof(Params) + 2 * sizeof(int) <= 227 * 1024 - kMaxSmem,
+              "k_fft's static shared memory exceeds the room the dynamic cap leaves");
+
 }  // namespace apx
