@@ -427,7 +427,7 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
             if (drop < 0) drop = nc - 1;
             for (int j = drop; j + 1 < nc; ++j) p.cand[j] = p.cand[j + 1];
             --nc;
-            smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl);
+            smem = direct_layout(p.cand, nc, Wb, pl.Nodd, &p.dl, p.full64 != 0);
         }
         if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
     }
@@ -623,6 +623,7 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
         G.start_comb.push_back(0);
         for (int r : G.reqs) {
             const Params& p = bp->prm[r];
+            if (p.P > 0x7fffffffLL - a) return APX_ERR_ARG;  // one launch's grid: fewer than 2^31 blocks
             a += (int)p.P;
             G.start_blk.push_back(a);
             if (G.fft) {

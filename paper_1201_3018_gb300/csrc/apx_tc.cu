@@ -706,11 +706,16 @@ static cudaError_t launch_prep_e(const TcGeom& g, const float* s, int64_t L, con
                                  void* seg, void* bt, float* cs_tab, float* inv_tab, float* cs_out, unsigned* status,
                                  cudaStream_t st) {
     const size_t wsm = sizeof(float) * (size_t)((g.T + g.N - 1 + kRun - 1) / kRun * kRun);
-    static size_t wsm_set = 48 * 1024;
-    if (wsm > wsm_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_quant<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
-        if (e != cudaSuccess) return e;
-        wsm_set = kTcSmemCap;
+    static int wsm_dev = -1;  // the device whose copy of the kernel has the raised cap
+    if (wsm > 48 * 1024) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (wsm_dev != dev) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_tc_quant<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
+            if (e != cudaSuccess) return e;
+            wsm_dev = dev;
+        }
     }
     k_tc_quant<E><<<(unsigned)g.nb, 256, wsm, st>>>(s, L, g, Sq, (E*)seg, cs_tab, cs_out, status);
     k_tc_kern<E><<<dim3((unsigned)(g.ngroups * g.G), (unsigned)(g.P / 8)), 256, sizeof(E) * (size_t)(g.N + 128), st>>>(
@@ -743,21 +748,20 @@ cudaError_t launch_tc_mma(const TcGeom& g, const void* seg, const void* bt, cons
         *encode_failed = true;
         return cudaErrorInvalidValue;
     }
-    static bool attr = false;
-    if (!attr) {
+    // function attributes and the SM count belong to a device: redo them when it changes
+    static int attr_dev = -1;
+    static int sms = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
         cudaError_t e = cudaSuccess;
         void (*ks[4])(CUtensorMap, CUtensorMap, CUtensorMap, TcGeom, const float*, float*, int32_t*, unsigned*) = {
             k_tc_mma<true, false>, k_tc_mma<false, false>, k_tc_mma<true, true>, k_tc_mma<false, true>};
         for (int i = 0; i < 4 && e == cudaSuccess; ++i)
             e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemCap);
         if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        attr_dev = dev;
     }
     const int64_t nsets = g.nb * g.ngroups;
     const unsigned grid = (unsigned)(nsets < sms ? nsets : sms);
