@@ -366,12 +366,33 @@ bool device_pointers_set(const Params& p) {
     return true;
 }
 
+// Table 1 model check on the host (the device's inequality, without its
+// operation-by-operation rounding; callers leave a margin).
+bool snr_feasible_host(double s2s, double Ms, double s2k, double Mk, int S, int K, double thr) {
+    const double S2 = (double)S * S, K2 = (double)K * K, Ms2 = Ms * Ms, Mk2 = Mk * Mk;
+    const double num = 144.0 * (s2s * s2k) * (S2 * K2);
+    const double den = 12.0 * (s2s * S2 * Mk2 + s2k * K2 * Ms2) + Ms2 * Mk2;
+    return num >= thr * den;
+}
+
+// The model grows with sigma_s^2 / ||s||_inf^2 and sigma_k^2 / ||k||_inf^2,
+// both at most 1: a candidate below the target there (checked 1 % below it,
+// far beyond the device's rounding) fails every block's check for every
+// kernel.  Such candidates are left out (the others keep their order), so the
+// block kernel holds no buffers for them; the same decisions, bit for bit.
+int prune_unreachable(Cand* c, int nc, double thr) {
+    int m = 0;
+    for (int j = 0; j < nc; ++j)
+        if (snr_feasible_host(1.0, 1.0, 1.0, 1.0, c[j].S, c[j].K, thr * 0.99)) c[m++] = c[j];
+    return m;
+}
+
 // Host half of a call: validate, plan (Section III, Eq. 17), choose the
 // packing candidates and the block kernel's shared memory.  Pointers to the
 // workspace are filled in by the caller.
 int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
                 int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
-                apx_block_stats* st, Params* out, size_t* smem_out) {
+                apx_block_stats* st, Params* out, size_t* smem_out, bool prune = true) {
     if (!s || !k || !r) return APX_ERR_ARG;
     Plan pl;
     int rc = plan(L, N, Wb, mode, &pl);
@@ -403,6 +424,7 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
             int Q = pl.fft ? qmax_fft(order[j], pl.Nodd, Wb) : qmax_direct(order[j], pl.Nodd);
             if (Q >= 1) p.cand[nc++] = make_cand(order[j], Q, Q, pl.Nodd, Wb);
         }
+        if (prune) nc = prune_unreachable(p.cand, nc, p.thr);
     } else if (sel_kind == 1) {
         int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
         if (S < 1 || K < 1 || S > (1 << 20) || K > (1 << 20)) return APX_ERR_ARG;
@@ -1089,15 +1111,6 @@ struct apx_kernel {
     KInfo stats;  // a host copy of the kernel statistics
 };
 
-// Section IV.D model check on the host, for a candidate-level decision with a
-// margin far above any rounding difference from the device's evaluation.
-static bool snr_feasible_host(double s2s, double Ms, double s2k, double Mk, int S, int K, double thr) {
-    const double S2 = (double)S * S, K2 = (double)K * K, Ms2 = Ms * Ms, Mk2 = Mk * Mk;
-    const double num = 144.0 * (s2s * s2k) * (S2 * K2);
-    const double den = 12.0 * (s2s * S2 * Mk2 + s2k * K2 * Ms2) + Ms2 * Mk2;
-    return num >= thr * den;
-}
-
 extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_t W_block, uint32_t mode,
                                  void* stream, apx_kernel** out) {
     if (!ctx || !k || !out || N < 1) return APX_ERR_ARG;
@@ -1108,8 +1121,9 @@ extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_
     // the candidate set depends on N, W_block and the mode only: plan a one-sample call
     Params p;
     size_t smem = 0;
+    // every candidate: the resident norms and spectra are indexed by candidate position
     int rc = make_params(k, 1, k, N, W_block, mode, pack == APX_PACK_NONE ? 2 : 0, 0.0, 0, 0, (float*)k, nullptr,
-                         nullptr, &p, &smem);
+                         nullptr, &p, &smem, false);
     if (rc) return rc;
     DeviceGuard dg(ctx->device);
     rc = ensure(ctx, ctx->flags, kFlagWords * sizeof(unsigned));
@@ -1176,7 +1190,7 @@ extern "C" int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float
     Params p;
     size_t smem = 0;
     int rc = make_params(s_in, L, kp->taps, kp->N, kp->W_block, kp->mode, sel, snr_target_db, 0, 0, r_out, rq_out,
-                         stats, &p, &smem);
+                         stats, &p, &smem, false);  // candidate positions as at creation
     if (rc) return rc;
     // With the kernel's statistics known on the host, a target that no packing can reach
     // even for the best window (model SNR at sigma^2 = ||s||_inf^2, checked 1 % below the
@@ -1386,6 +1400,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     Params p;
     memset(&p, 0, sizeof p);
     const uint32_t pack = mode & 0xF00u;
+    p.thr = pow(10.0, snr_target_db / 10.0);
     int nc = 0;
     if (pack == APX_PACK_AUTO) {
         const int order[3] = {APX_BLK_SYM, APX_BLK_ASYM3, APX_BLK_ASYM2};
@@ -1393,6 +1408,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
             int Q = qmax_fft(order[j], pl.Nodd, W_block);
             if (Q >= 1) p.cand[nc++] = make_cand(order[j], Q, Q, pl.Nodd, W_block);
         }
+        nc = prune_unreachable(p.cand, nc, p.thr);
     } else if (pack != APX_PACK_NONE) {
         int blk = pack == APX_PACK_SYM ? APX_BLK_SYM : (pack == APX_PACK_ASYM2 ? APX_BLK_ASYM2 : APX_BLK_ASYM3);
         int Q = qmax_fft(blk, pl.Nodd, W_block);
@@ -1401,7 +1417,6 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     }
     p.ncand = nc;
     p.autosel = pack == APX_PACK_AUTO;
-    p.thr = pow(10.0, snr_target_db / 10.0);
     p.s = s_in; p.L = L; p.k = k; p.N = N; p.Nodd = pl.Nodd; p.Wb = W_block; p.W = pl.W; p.head = pl.head;
     p.fft = 1; p.xcorr = (mode & 0xFu) == APX_OP_XCORR;
     p.P = pl.P; p.out_len = L + N - 1;

@@ -425,3 +425,28 @@ def test_target_just_below_the_best_case_model_snr(ctx, core, Wb):
     for target in (best_db - 0.02, best_db - 0.001):
         mode = apx.OP_CONV | core | apx.PACK_AUTO
         check(*run_both(ctx, s, k, Wb, mode, snr=target), s, k, mode, Wb)
+
+
+@pytest.mark.parametrize("core,Wb", [(apx.CORE_DIRECT, 1024), (apx.CORE_FFT, 2048)])
+def test_candidates_at_the_model_maximum(ctx, core, Wb):
+    """Signal and kernel of +-1 values: both ratios sigma^2 / ||.||_inf^2 are 1,
+    where the Section IV.D model is largest, so a candidate is unreachable for
+    every block exactly when the target exceeds its model there -- the rule by
+    which the plan leaves candidates out.  Targets a hair below, a hair above
+    and well above each candidate's maximum: per-block decisions, integers and
+    outputs as the oracle's, which evaluates every candidate."""
+    g = np.random.default_rng(Wb + 7)
+    N = 65
+    k = np.where(g.random(N) < 0.5, -1.0, 1.0).astype(np.float32)
+    s = np.where(g.random(40000) < 0.5, -1.0, 1.0).astype(np.float32)
+    qfun = O.qmax_fft if core == apx.CORE_FFT else (lambda blk, n, w: O.qmax_direct(blk, n))
+    tops = set()
+    for blk in (O.BLK_SYM, O.BLK_ASYM3, O.BLK_ASYM2):
+        Q = qfun(blk, N, Wb)
+        if Q >= 1:
+            tops.add(round(O.snr_model_db(1.0, 1.0, 1.0, 1.0, Q, Q), 6))
+    assert tops
+    mode = apx.OP_CONV | core | apx.PACK_AUTO
+    for top in sorted(tops):
+        for target in (top - 0.001, top + 0.001, top + 1.0):
+            check(*run_both(ctx, s, k, Wb, mode, snr=target), s, k, mode, Wb)
