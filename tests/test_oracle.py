@@ -315,6 +315,25 @@ def _printed_table1_db(s2s, Ms, s2k, Mk, S, K):
     return 10 * math.log10(num / den)
 
 
+def test_snr_model_is_largest_at_unit_ratios():
+    """The model rises with each ratio sigma^2 / ||.||_inf^2 (Section IV.D;
+    both are at most 1 for any block and kernel), so its value at ratios 1 bounds
+    every block's: the plan leaves out a candidate whose model misses the target
+    there.  Checked on a grid of ratios and companding ranges, with windows and
+    kernels of any scale."""
+    g = np.random.default_rng(11)
+    for S, K in [(1, 1), (10, 10), (16, 200), (191, 191), (2047, 3), (65535, 65535)]:
+        top = O.snr_model_lin(1.0, 1.0, 1.0, 1.0, S, K)
+        for _ in range(200):
+            Ms, Mk = 10.0 ** g.uniform(-3, 3), 10.0 ** g.uniform(-3, 3)
+            a, b = g.uniform(1e-6, 1.0, 2)
+            v = O.snr_model_lin(a * Ms * Ms, Ms, b * Mk * Mk, Mk, S, K)
+            assert v <= top * (1 + 1e-12)
+            # and it grows with each ratio
+            assert O.snr_model_lin(min(1.0, 1.5 * a) * Ms * Ms, Ms, b * Mk * Mk, Mk, S, K) >= v * (1 - 1e-12)
+            assert O.snr_model_lin(a * Ms * Ms, Ms, min(1.0, 1.5 * b) * Mk * Mk, Mk, S, K) >= v * (1 - 1e-12)
+
+
 def test_snr_model_matches_measured_noise_delta2_over_12():
     """Eq. (18) with uniform quantisation noise Delta^2/12: the measured noise
     power of companded convolution matches the model within a few percent for
