@@ -567,6 +567,7 @@ struct BatchPlan {
     std::vector<size_t> smem;
     struct Group {
         int fft, Wb;
+        int packed;  // whether its requests keep packing candidates (their buffers set the shared memory)
         std::vector<int> reqs;
         size_t smem = 0;
         std::vector<int> start_blk, start_spec, start_comb;  // CTA offsets, nreq + 1 each
@@ -612,16 +613,21 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
                              nullptr, &bp->prm[r], &bp->smem[r]);
         if (rc) return rc;
     }
-    // group by core and W_block
+    // group by core and W_block, and apart the requests without packing candidates
+    // (full precision, or no candidate can reach the target): a group launches with the
+    // largest shared memory of its requests, and the candidates' FP64 buffers would
+    // take L1 cache from the others
     for (int r = 0; r < n; ++r) {
         const Params& p = bp->prm[r];
+        const int packed = p.ncand > 0;
         int g = -1;
         for (size_t j = 0; j < bp->groups.size(); ++j)
-            if (bp->groups[j].fft == p.fft && bp->groups[j].Wb == p.Wb) g = (int)j;
+            if (bp->groups[j].fft == p.fft && bp->groups[j].Wb == p.Wb && bp->groups[j].packed == packed) g = (int)j;
         if (g < 0) {
             bp->groups.emplace_back();
             bp->groups.back().fft = p.fft;
             bp->groups.back().Wb = p.Wb;
+            bp->groups.back().packed = packed;
             g = (int)bp->groups.size() - 1;
         }
         bp->groups[g].reqs.push_back(r);
