@@ -116,6 +116,25 @@ void apx_destroy(apx_ctx* ctx);
  * Errors: APX_ERR_ARG, APX_ERR_WBLOCK. */
 int apx_plan_blocks(int64_t L, int32_t N, int32_t W_block, uint32_t mode, int64_t* P, int32_t* W);
 
+/* Host-only: the packing candidates that apx_conv (or apx_conv_host,
+ * apx_conv_batch) with this mode and target gives its blocks, in the order a
+ * block tries them (Table 1: symmetric, asymmetric M = 3, asymmetric M = 2).
+ * With APX_PACK_AUTO every packing at the largest S_q = K_q its bound admits
+ * (exactness, reading c5; the direct and FFT cores differ), less those whose
+ * Section IV.D model misses the target even at ratios sigma^2 / ||.||_inf^2 = 1
+ * for block and kernel (checked 1 % below the target): no block could pick
+ * them.  Direct core only: a packing whose shared-memory layout (FP64 packed
+ * window, outputs and taps beside the FP32 window) does not fit one CTA at
+ * this N and W_block is not offered either (the asymmetric ones first; e.g.
+ * N = 4096 at W_block = 8192), so its blocks take the next candidate or full
+ * precision where the oracle of the method would pack them.  A single packing
+ * bit gives that packing alone, APX_PACK_NONE none.
+ * Writes up to 3 entries: blk[i] (APX_BLK_*), q[i] = S_q = K_q, b[i] (eps =
+ * 2^-b); any output pointer may be NULL.  Returns the count (0 to 3), or
+ * APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE as apx_conv would. */
+int apx_plan_candidates(int64_t L, int32_t N, int32_t W_block, uint32_t mode, double snr_target_db, int32_t* blk,
+                        int32_t* q, int32_t* b);
+
 /* Approximate convolution / cross-correlation under a per-block SNR target
  * (pack bits APX_PACK_AUTO; Section IV.D), or with a forced packing whose
  * S_q = K_q is the largest the packing's exactness bound admits.

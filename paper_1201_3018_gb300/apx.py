@@ -51,6 +51,8 @@ SIGNATURES = {
     "apx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _sz]),
     "apx_destroy": (None, [_vp]),
     "apx_plan_blocks": (C.c_int, [_i64, _i32, _i32, _u32, C.POINTER(_i64), C.POINTER(_i32)]),
+    "apx_plan_candidates": (C.c_int, [_i64, _i32, _i32, _u32, _d, C.POINTER(_i32), C.POINTER(_i32),
+                                      C.POINTER(_i32)]),
     "apx_conv": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _d, _vp, _vp, _vp, _vp]),
     "apx_conv_fixed": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "apx_conv_full": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _u32, _vp, _vp]),
@@ -125,6 +127,16 @@ def plan_blocks(L: int, N: int, W_block: int, mode: int = 0):
     P, W = _i64(), _i32()
     _check("apx_plan_blocks", lib().apx_plan_blocks(L, N, W_block, mode, C.byref(P), C.byref(W)))
     return P.value, W.value
+
+
+def plan_candidates(L: int, N: int, W_block: int, mode: int, snr_db: float = 0.0):
+    """The packing candidates a call with this mode and target gives its blocks,
+    in the order they are tried: a list of (APX_BLK_*, S_q = K_q, b)."""
+    blk, q, b = (_i32 * 3)(), (_i32 * 3)(), (_i32 * 3)()
+    n = lib().apx_plan_candidates(L, N, W_block, mode, float(snr_db), blk, q, b)
+    if n < 0:
+        raise ApxError("apx_plan_candidates", n)
+    return [(blk[j], q[j], b[j]) for j in range(n)]
 
 
 def _ptr(t):

@@ -806,6 +806,24 @@ int apx_plan_blocks(int64_t L, int32_t N, int32_t W_block, uint32_t mode, int64_
     return APX_OK;
 }
 
+int apx_plan_candidates(int64_t L, int32_t N, int32_t W_block, uint32_t mode, double snr_target_db, int32_t* blk,
+                        int32_t* q, int32_t* b) {
+    // the plan of a call reads no sample: any non-null addresses do
+    static float none;
+    Params p;
+    size_t smem = 0;
+    const int sel = (mode & 0xF00u) == APX_PACK_NONE ? 2 : 0;
+    int rc = make_params(&none, L, &none, N, W_block, mode, sel, snr_target_db, 0, 0, &none, nullptr, nullptr, &p,
+                         &smem);
+    if (rc) return rc;
+    for (int j = 0; j < p.ncand; ++j) {
+        if (blk) blk[j] = p.cand[j].blk;
+        if (q) q[j] = p.cand[j].S;
+        if (b) b[j] = p.cand[j].b;
+    }
+    return p.ncand;
+}
+
 int apx_conv(apx_ctx* ctx, const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block,
              uint32_t mode, double snr_target_db, float* r_out, int32_t* rq_out, apx_block_stats* stats,
              void* stream) {
