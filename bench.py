@@ -156,9 +156,10 @@ def peaks():
     if os.path.exists(PEAKS_FILE):
         try:
             pk = dict(json.load(open(PEAKS_FILE)))
-            pk["source"] = "measured"
-        except (OSError, ValueError):
-            pass
+            pk["source"] = "measured" if "hbm_gbs" in pk else "fallback"
+            pk.setdefault("hbm_gbs", 6800.0)
+        except (OSError, ValueError, TypeError):
+            pk = {"hbm_gbs": 6800.0, "source": "fallback"}
     clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     pk["fp32_tflops"] = SMS * FP32_LANES * 2 * clk / 1e12
     pk["fp64_tflops"] = SMS * FP64_PER_SM_CLK * clk / 1e12
