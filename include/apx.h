@@ -6,11 +6,11 @@
  *
  * The problem (Section II, Eq. 1): r_out[m] = sum_{n<N} s_in[m-n] k[n] for
  * m in [0, L+N-1).  Overlap-save splits s_in into P blocks of W_block samples
- * (Section III).  Per block the middle layer companded the block (Eq. 2),
+ * (Section III).  Per block the middle layer compands the block (Eq. 2),
  * packs pairs or triples of small integers into one FP64 word (symmetric
  * packing, Eqs. 4-5; asymmetric packing, Eq. 7), convolves the packed words
- * with a direct or FFT core (Eqs. 8-9), unpacks (Eqs. 11-15), inverse-companded
- * (Eq. 16) and places the block's W outputs (Eq. 17).  Under an SNR target the
+ * with a direct or FFT core (Eqs. 8-9), unpacks (Eqs. 11-15), inverts the
+ * companding (Eq. 16) and places the block's W outputs (Eq. 17).  Under an SNR target the
  * packing and companding range are chosen per block from the block's marginal
  * statistics (Table 1 model, Section IV.D); when no packing meets the target
  * the block runs in full precision (FP32).
@@ -222,9 +222,11 @@ const char* apx_strerror(int status);
 /* ---- batched calls ---------------------------------------------------------
  * Many independent signals in one call (Section II: overlap-save blocks are
  * independent, so the blocks of all requests share each launch).  Requests are
- * grouped by core and W_block; each group is one launch of the direct kernel
- * or three of the FFT core (spectrum, combine, block kernel).  Each request's
- * result equals that of the corresponding single call. */
+ * grouped by core, W_block and whether any packing candidate remains for them
+ * (apx_plan_candidates: the candidates' FP64 buffers set a group's shared
+ * memory); each group is one launch of the direct kernel or three of the FFT
+ * core (spectrum, combine, block kernel).  Each request's result equals that
+ * of the corresponding single call. */
 typedef struct {
     const float* s_in;      /* device, L samples                                  */
     int64_t L;
