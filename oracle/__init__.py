@@ -88,6 +88,7 @@ def _declare(L):
         "or_snr_model_lin": (d, [d, f, d, f, i32, i32]),
         "or_snr_model_db": (d, [d, f, d, f, i32, i32]),
         "or_snr_feasible": (C.c_int, [d, f, d, f, i32, i32, d]),
+        "or_snr_margin_db": (d, [i32]),
         "or_fft_err_digits": (d, [C.c_int, i32, d, d, i32]),
         "or_compand_factor": (f, [i32, f]),
         "or_compand": (None, [vp, i64, f, vp]),
@@ -220,6 +221,11 @@ def snr_model_lin(sig2_s, Ms, sig2_k, Mk, S, K):
 
 def snr_feasible(sig2_s, Ms, sig2_k, Mk, S, K, thr_lin):
     return bool(lib().or_snr_feasible(sig2_s, Ms, sig2_k, Mk, S, K, thr_lin))
+
+
+def snr_margin_db(W):
+    """dB by which the Section IV.D model must clear the target (W outputs per block)."""
+    return lib().or_snr_margin_db(W)
 
 
 def fft_err_digits(blk, log2n, l1_kbar, l2_sbar, b):

@@ -103,6 +103,8 @@ int32_t or_qmax_fft(int blkmode, int32_t Nodd, int32_t Wblock);
 double  or_snr_model_lin(double sig2_s, float Ms, double sig2_k, float Mk, int32_t Sq, int32_t Kq);
 double  or_snr_model_db(double sig2_s, float Ms, double sig2_k, float Mk, int32_t Sq, int32_t Kq);
 int     or_snr_feasible(double sig2_s, float Ms, double sig2_k, float Mk, int32_t Sq, int32_t Kq, double thr_lin);
+/* margin in dB by which the model must clear the target (W = outputs kept per block) */
+double  or_snr_margin_db(int32_t W);
 double  or_fft_err_digits(int blkmode, int32_t log2n, double l1_kbar, double l2_sbar, int32_t b);
 
 /* ---- a5/a6: compand and pack --------------------------------------------- */

@@ -68,7 +68,7 @@ def test_candidates_match_oracle(libapx, fft, N, Wb, snr):
     mode = (libapx.CORE_FFT if fft else libapx.CORE_DIRECT) | libapx.PACK_AUTO
     got = libapx.plan_candidates(100000, N, Wb, mode, snr)
     nodd = N if N % 2 else N + 1
-    thr = 10.0 ** (snr / 10.0)
+    thr = 10.0 ** ((snr + O.snr_margin_db(Wb - nodd - 1)) / 10.0)  # Section IV.D minimum and margin
     want = []
     for blk in (O.BLK_SYM, O.BLK_ASYM3, O.BLK_ASYM2):
         Q = O.qmax_fft(blk, nodd, Wb) if fft else O.qmax_direct(blk, nodd)

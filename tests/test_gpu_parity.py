@@ -125,15 +125,27 @@ def test_auto_selection(ctx, core, target, L, N, Wb, op):
     r, rq, st, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=target)
     pm, fm = check(r, rq, st, ro, rqo, so, s, k, mode, Wb)
     packed = np.isin(st["mode"], PACKED)
-    assert np.all(st["snr_pred_db"][packed] >= target)
+    p = O.plan(len(s), len(k), Wb, core == apx.CORE_FFT)
+    # the model clears the minimum by the Section IV.D margin
+    assert np.all(st["snr_pred_db"][packed] >= target + O.snr_margin_db(p.W) - 1e-9)
     if pm.any():
         kk = k[::-1] if op == apx.OP_XCORR else k
+        ref_all = O.conv_ref(s, kk.copy())
         idx = np.nonzero(pm)[0]
-        ref = O.conv_ref_at(s, kk, idx)
+        ref = ref_all[idx]
         snr_gpu = 10 * math.log10(np.sum(ref ** 2) / np.sum((r[idx] - ref) ** 2))
         snr_or = 10 * math.log10(np.sum(ref ** 2) / np.sum((ro[idx] - ref) ** 2))
         assert abs(snr_gpu - snr_or) < 0.1
-        assert snr_gpu >= target - 1.0
+        assert snr_gpu >= target
+        # and in every packed block (Section IV.D: a lower limit per block)
+        for i in np.nonzero(packed)[0]:
+            st0 = O.block_start(p, int(i))
+            lo, hi = O.block_out_range(p, int(i))
+            g = np.arange(st0 + lo, st0 + hi)
+            g = g[(g >= 0) & (g < len(r))]
+            num, den = np.sum(ref_all[g] ** 2), np.sum((r[g] - ref_all[g]) ** 2)
+            if num > 0 and den > 0:
+                assert 10 * math.log10(num / den) >= target, (i, st["snr_pred_db"][i])
 
 
 def test_zero_blocks_and_zero_kernel(ctx):
@@ -421,7 +433,8 @@ def test_target_just_below_the_best_case_model_snr(ctx, core, Wb):
     Mk, s2k = O.maxabs(k), O.second_moment(k)
     Q = O.qmax_fft(O.BLK_SYM, N, Wb)
     assert Q >= 1
-    best_db = O.snr_model_db(1.0, 1.0, s2k, Mk, Q, Q)
+    # the model must clear the target by the Section IV.D margin
+    best_db = O.snr_model_db(1.0, 1.0, s2k, Mk, Q, Q) - O.snr_margin_db(Wb - N - 1)
     for target in (best_db - 0.02, best_db - 0.001):
         mode = apx.OP_CONV | core | apx.PACK_AUTO
         check(*run_both(ctx, s, k, Wb, mode, snr=target), s, k, mode, Wb)
@@ -444,7 +457,8 @@ def test_candidates_at_the_model_maximum(ctx, core, Wb):
     for blk in (O.BLK_SYM, O.BLK_ASYM3, O.BLK_ASYM2):
         Q = qfun(blk, N, Wb)
         if Q >= 1:
-            tops.add(round(O.snr_model_db(1.0, 1.0, 1.0, 1.0, Q, Q), 6))
+            # the highest target the candidate can serve: its model maximum less the margin
+            tops.add(round(O.snr_model_db(1.0, 1.0, 1.0, 1.0, Q, Q) - O.snr_margin_db(Wb - N - 1), 6))
     assert tops
     mode = apx.OP_CONV | core | apx.PACK_AUTO
     for top in sorted(tops):
