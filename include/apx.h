@@ -119,16 +119,17 @@ int apx_plan_blocks(int64_t L, int32_t N, int32_t W_block, uint32_t mode, int64_
 /* Host-only: the packing candidates that apx_conv (or apx_conv_host,
  * apx_conv_batch) with this mode and target gives its blocks, in the order a
  * block tries them (Table 1: symmetric, asymmetric M = 3, asymmetric M = 2).
- * With APX_PACK_AUTO every packing at the largest S_q = K_q its bound admits
- * (exactness, reading c5; the direct and FFT cores differ), less those whose
- * Section IV.D model misses the target even at ratios sigma^2 / ||.||_inf^2 = 1
- * for block and kernel (checked 1 % below the target): no block could pick
- * them.  Direct core only: a packing whose shared-memory layout (FP64 packed
- * window, outputs and taps beside the FP32 window) does not fit one CTA at
- * this N and W_block is not offered either (the asymmetric ones first; e.g.
- * N = 4096 at W_block = 8192), so its blocks take the next candidate or full
- * precision where the oracle of the method would pack them.  A single packing
- * bit gives that packing alone, APX_PACK_NONE none.
+ * With APX_PACK_AUTO every packing at the largest S_q = K_q = Q for which the
+ * FP64 packed convolution stays exact (every packed word, product and partial
+ * sum an integer multiple of the finest digit 2^-b below 2^53; the FFT core
+ * also keeps its a-priori rounding-error bound below a quarter digit), less
+ * those whose Section IV.D model misses the target plus its margin even at
+ * ratios sigma^2 / ||.||_inf^2 = 1 for block and kernel (checked 1 % below):
+ * no block could pick them.  The margin is 0.5 + 48 / sqrt(W) dB, W =
+ * W_block - N' - 1 the outputs kept per block: the model gives the SNR a
+ * block can expect, and a packing is admitted only where every block's
+ * measured SNR stays at or above the target.  A single packing bit gives that
+ * packing alone, APX_PACK_NONE none.
  * Writes up to 3 entries: blk[i] (APX_BLK_*), q[i] = S_q = K_q, b[i] (eps =
  * 2^-b); any output pointer may be NULL.  Returns the count (0 to 3), or
  * APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE as apx_conv would. */
@@ -237,6 +238,8 @@ typedef struct {
     uint32_t mode;          /* op | core (APX_CORE_AUTO allowed) | pack           */
     double snr_target_db;   /* APX_PACK_AUTO: per-block target (Section IV.D)     */
     int32_t S_q, K_q;       /* > 0 with SYM / ASYM2 / ASYM3: fixed quantiser      */
+    int32_t* rq_out;        /* device or NULL: L+N-1 integer-domain outputs, as apx_conv's rq_out */
+    apx_block_stats* stats; /* device or NULL: one record per block, as apx_conv's stats */
 } apx_request;
 
 /* Enqueue all requests on `stream`.  Errors: any single-call error of a request
@@ -246,7 +249,7 @@ typedef struct {
 int apx_conv_batch(apx_ctx* ctx, const apx_request* reqs, int32_t n, void* stream);
 
 /* The same from HOST buffers: s_in, k and r_out of every request are host
- * pointers.  A request whose three buffers are page-locked and addressable by
+ * pointers (rq_out and stats must be NULL: APX_ERR_ARG otherwise).  A request whose three buffers are page-locked and addressable by
  * the device runs on them in place (the kernels read and write them over the
  * host link).  For the others `stream` gets one host-to-device copy per input
  * into device copies and one device-to-host copy per output after the batched
@@ -303,6 +306,12 @@ int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const float* k_ba
                    int32_t S_q, int32_t K_q, float* y_out, int64_t ldy, int32_t* yq_out, float* block_cs,
                    void* stream);
 
+/* Host-only: the block geometry apx_filterbank uses for these sizes and
+ * companding ranges: *T outputs per block (T = 128 P, the phases P per row as
+ * above) and *nb blocks, ceil((L+N-1) / T).  Either pointer may be NULL.
+ * Errors: APX_ERR_ARG (sizes beyond the limits above), APX_ERR_RANGE. */
+int apx_filterbank_blocks(int64_t L, int32_t F, int32_t N, int32_t S_q, int32_t K_q, int32_t* T, int64_t* nb);
+
 /* ---- prepared kernels (resident across calls) ----------------------------
  * Section IV prepares the kernel once per request; a caller that convolves
  * many signals with the same kernel (template matching against a stream of
@@ -342,16 +351,25 @@ void apx_kernel_destroy(apx_kernel* kp);
  *   mode           : op | APX_CORE_FFT | pack bits (APX_PACK_AUTO uses
  *                    snr_target_db); the direct core is rejected (APX_ERR_ARG)
  *   W_block        : a power of two up to 8192; larger -> APX_ERR_WBLOCK
- * Results equal apx_conv's for the same arguments (integer domain exactly,
- * FP32 outputs within rounding).  Non-finite input yields NaN outputs for the
- * affected blocks; there is no status word to read back.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), clears its flag words and fills the twiddle tables on
- * `stream`; a call with a W_block
- * different from the previous one on that device refills them on `stream`.
- * Make the first call before any stream capture.  Every call shares the array:
- * calls that overlap on the GPU (different streams, or several host threads)
- * race and must be serialised by the caller. */
+ * Results equal apx_conv's for the same arguments: the same per-block
+ * decisions, and outputs of packed blocks bit for bit (the same integers
+ * times the same FP32 factor); outputs of full-precision blocks within FP32
+ * rounding (this entry point builds its twiddle tables on the device with
+ * sincospi, apx_conv on the host in long double, and the two can differ in the
+ * last bit).  Non-finite input yields NaN outputs for the affected blocks;
+ * there is no status word to read back (the array's status bits are set as in
+ * apx_conv but nothing reads or clears them, which affects no later call).
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first call on a device also clears the array's
+ * flag words and fills its twiddle tables (once, for every W_block up to the
+ * maximum), enqueued on `stream`: make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) while the process runs is not
+ * supported by this entry point.  Every call shares the array and leaves its
+ * contents for the next: calls that overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.
+ * Errors: APX_ERR_ARG (null pointer, not the FFT core, mode bits the FFT core
+ * rejects such as APX_FULL_FP64 or APX_LITERAL), APX_ERR_WBLOCK, APX_ERR_RANGE,
+ * APX_ERR_CUDA. */
 int apx_conv_fft_static(const float* s_in, int64_t L, const float* k, int32_t N, int32_t W_block, uint32_t mode,
                         double snr_target_db, float* r_out, void* stream);
 

@@ -142,7 +142,7 @@ def conv_ref(s, k):
 
 
 def xcorr_ref(s, t):
-    """Cross-correlation by its definition (reading c9), index l + N - 1."""
+    """Cross-correlation by its definition, sum_n s[n + l] t[n], stored at index l + N - 1."""
     s, t = _f64(s), _f64(t)
     r = np.empty(len(s) + len(t) - 1, np.float64)
     lib().or_xcorr_ref(_p(s), len(s), _p(t), len(t), _p(r))

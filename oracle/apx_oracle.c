@@ -10,8 +10,8 @@
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.  No fused
  * multiply-add anywhere: every product and sum is a separate IEEE operation.
  *
- * Readings taken where the paper is silent or garbled (c1..c11) are stated at
- * the code they govern.
+ * Where the paper is silent or garbled, the reading taken is stated at the
+ * code it governs.
  */
 #include "apx_oracle.h"
 
@@ -40,7 +40,8 @@ void or_conv_ref(const double* s, int64_t L, const double* k, int32_t N, double*
     }
 }
 
-/* Cross-correlation (reading c9; the paper only names Matlab xcorr):
+/* Cross-correlation (the paper only names Matlab's xcorr; read as the plain
+ * definition below, equal to conv(s, reverse(t))):
  *   x[l] = sum_n s[n + l] t[n],  l in [-(N-1), L-1],  stored at index l + N - 1.
  * Written from the definition, not through a reversed convolution, so that it
  * pins the reversal the pipeline uses. */
@@ -82,7 +83,8 @@ void or_conv_int(const int64_t* s, int64_t L, const int64_t* k, int32_t N, int64
 }
 
 /* ======================================================================== */
-/* a1: block plan (Section III, Eqs. (10) and (17)); reading c1               */
+/* a1: block plan (Section III, Eqs. (10) and (17)): W_block = W + N' + 1, block
+ * w >= 1 starts at wW - 2 (Eq. 17 solved for the origin)                    */
 /* ======================================================================== */
 
 /* Section III: N odd (an even kernel gets one zero tap), W even, and
@@ -144,7 +146,7 @@ float or_maxabs(const float* x, int64_t n) {
 
 /* Second moment of the marginal (Section IV.D: sigma^2 is the second moment of
  * the fitted marginal; here the sample second moment of the window).
- * Reading c10: evaluated in 24-bit fixed point relative to ||x||_inf so that
+ * Evaluated in 24-bit fixed point relative to ||x||_inf so that
  * the sum is an exact integer, independent of summation order:
  *   q_i = trunc(x_i * 2^sh), ||x||_inf * 2^sh in [2^23, 2^24),
  *   sigma^2 = (sum q_i^2) * 2^(-2 sh) / n.                                   */
@@ -163,10 +165,10 @@ double or_second_moment(const float* x, int64_t n, float maxabs) {
 }
 
 /* ======================================================================== */
-/* a4: exactness bounds (reading c5) and the per-block selector (c10)        */
+/* a4: exactness bounds and the per-block selector (Section IV.D)            */
 /* ======================================================================== */
 
-/* Reading c3: eps = 2^-b with the smallest b such that 2^b >= 2 R_max + 1, so
+/* Eq. (6) with a power of two: eps = 2^-b with the smallest b such that 2^b >= 2 R_max + 1, so
  * every offset digit R_max + c, c in [-R_max, R_max], fits in b bits (the
  * paper's Eq. (6) eps = 1/(2 R_max) rounded down to a power of two). */
 int32_t or_bits(int64_t Rmax) {
@@ -175,7 +177,7 @@ int32_t or_bits(int64_t Rmax) {
     return b;
 }
 
-/* Reading c5 (replaces Table 1's "Companding range" row for power-of-two eps):
+/* Exactness bound (replaces Table 1's "Companding range" row for power-of-two eps):
  * every packed word, product and partial sum of the FP64 block convolution is
  * an integer multiple of the finest digit; it is exact and order-independent
  * when the scaled magnitude bound stays within 2^53.
@@ -202,7 +204,7 @@ int or_exact_ok(int blkmode, int32_t Nodd, int32_t Sq, int32_t Kq) {
 }
 
 /* Section IV.D: "the maximum S_q and K_q that allow for this packing".  With
- * S_q = K_q = Q as in every experiment of the paper (reading c10), the largest
+ * S_q = K_q = Q as in every experiment of the paper, the largest
  * Q in [1, 2^20] that passes the exactness bound; 0 when none does. */
 int32_t or_qmax_direct(int blkmode, int32_t Nodd) {
     if (!or_exact_ok(blkmode, Nodd, 1, 1)) return 0;
@@ -215,7 +217,7 @@ int32_t or_qmax_direct(int blkmode, int32_t Nodd) {
     return lo;
 }
 
-/* Reading c7: error bound of an FFT block convolution in units of the finest
+/* FFT core (the paper is silent on its rounding): error bound of an FFT block convolution in units of the finest
  * packed digit.  Radix-2 structured FFT with twiddle error mu (Higham,
  * Accuracy and Stability of Numerical Algorithms, Thm 24.2):
  *   phi = Lg eta / (1 - Lg eta),  eta = mu + gamma_4 (sqrt 2 + mu),
@@ -243,7 +245,7 @@ static int32_t ilog2_i(int64_t n) { int32_t l = 0; while (((int64_t)1 << l) < n)
 /* Length of the real block signal transformed by the FFT core for a mode:
  * symmetric packs W_block samples into W_block/2 words; asymmetric packing
  * convolves segments of ceil(W_block/M) words whose full linear convolution
- * fits a transform of W_block points (reading c6). */
+ * fits a transform of W_block points (the asymmetric layout of Eq. (7)). */
 static int32_t fft_log2n(int blkmode, int32_t Wblock) {
     return blkmode == OR_BLK_SYM ? ilog2_i(Wblock / 2) : ilog2_i(Wblock);
 }
@@ -320,11 +322,12 @@ int or_snr_feasible(double sig2_s, float Ms, double sig2_k, float Mk, int32_t Sq
 /* a5/a6: companding (Eq. 2) and packing (Eqs. 4, 5, 7)                      */
 /* ======================================================================== */
 
-/* Eq. (2): c = Q / ||x||_inf.  Reading c8: one correctly rounded FP32 divide
+/* Eq. (2): c = Q / ||x||_inf, one correctly rounded FP32 divide
  * (the inputs are FP32; the decision is taken in FP32 on every side). */
 float or_compand_factor(int32_t Q, float maxabs) { return (float)Q / maxabs; }
 
-/* Eq. (2): x~ = [[c x]], round half to even on the FP32 product (reading c8). */
+/* Eq. (2): x~ = [[c x]], round half to even on the FP32 product (the paper does
+ * not name its rounding). */
 void or_compand(const float* x, int64_t n, float c, int32_t* q) {
     for (int64_t i = 0; i < n; ++i) {
         float p = c * x[i];
@@ -338,7 +341,8 @@ void or_pack_sym_signal(const int32_t* sq, int32_t n, int32_t b, double* sbar) {
     for (int32_t m = 0; m < n / 2; ++m) sbar[m] = (double)sq[2 * m] + eps * (double)sq[2 * m + 1];
 }
 
-/* Eq. (5) with reading c2: the kernel pair is swapped relative to the print,
+/* Eq. (5) with the kernel pair swapped relative to the print (as printed, Eqs.
+ * (12)-(15) do not reconstruct s~*k~),
  *   kbar[n] = k~[2n+1] + eps^-1 k~[2n],  n in [0, (N'+1)/2),  k~[N'] = 0,
  * which makes the eps^0 term of Eq. (9) the odd output r~[2m+1] and the
  * eps^-1 / eps terms the two halves of r~[2m], as Eqs. (14)-(15) require. */
@@ -360,7 +364,7 @@ void or_pack_sym_kernel_printed(const int32_t* kq, int32_t Nodd, int32_t b, doub
     }
 }
 
-/* Eq. (7), reading c6: segments of Ls = ceil(n/M) samples,
+/* Eq. (7) (its stride is garbled in the print): segments of Ls = ceil(n/M) samples,
  *   sbar[m] = sum_{q<M} eps^q s~[m + q Ls],  zero past the block end. */
 void or_pack_asym_signal(const int32_t* sq, int32_t n, int32_t M, int32_t b, double* sbar) {
     int32_t Ls = (n + M - 1) / M;
@@ -450,7 +454,7 @@ int or_conv_f64_fft(const double* a, int64_t na, const double* k, int64_t nk, do
 
 /* Packed output scaled to the finest digit: T = rbar 2^sc, an exact integer
  * whenever the exactness bound holds (rounded to nearest for the FFT core,
- * reading c7, whose error bound is below 1/4 digit). */
+ * whose error bound is kept below 1/4 digit). */
 static int scaled_int(double rbar, int32_t sc, int round_nearest, int64_t* T) {
     double t = ldexp(rbar, sc);
     if (round_nearest) t = nearbyint(t);
@@ -459,7 +463,7 @@ static int scaled_int(double rbar, int32_t sc, int round_nearest, int64_t* T) {
     return OR_OK;
 }
 
-/* Eqs. (11)-(15), exact mode (reading c4: u_sys = 0, eps = 2^-b), evaluated
+/* Eqs. (11)-(15), exact mode (u_sys = 0, eps = 2^-b), evaluated
  * on u scaled by 2^b, which is an integer:
  *   (11) u[m] = rbar[m] + R_safe,  R_safe = R_max (eps + 1 + eps^-1)
  *   (12) side_eps    = R_max for m = W_start, else eps^-1 (u[m-1] - floor u[m-1])
@@ -489,7 +493,7 @@ int or_unpack_sym(const double* rbar, int32_t nbar, int32_t Wstart, int64_t Rmax
     return OR_OK;
 }
 
-/* Reading c4, second form: balanced base-2^b digits of T = rbar 2^b,
+/* Exact mode, second form: balanced base-2^b digits of T = rbar 2^b,
  * T = A 2^{2b} + B 2^b + C, r~[2m+1] = B, r~[2m] = A[m] + C[m-1].  Must agree
  * with or_unpack_sym wherever both are exact (tested). */
 int or_unpack_sym_digits(const double* rbar, int32_t nbar, int32_t Wstart, int32_t b, int64_t* rq) {
@@ -530,7 +534,7 @@ void or_unpack_sym_fp64(const double* rbar, int32_t nbar, int32_t Wstart, double
 }
 
 /* Asymmetric unpacking: "M successive iterations" (Section III.C, citing [8]).
- * Reading c6: offset every digit by R_max, u = rbar + R_max sum_q eps^q, then
+ * Offset every digit by R_max, u = rbar + R_max sum_q eps^q, then
  * for q = 0..M-1 take the integer part at the scale of digit q and keep the
  * remainder; c_q = digit - R_max.  Segment results overlap-add:
  *   r~[j] = sum_q c_q[j - q Ls],  j in [0, nout). */
@@ -578,13 +582,13 @@ static int prep_mode(mode_t_* md, int blk, int32_t S, int32_t K, const float* kr
     md->blk = blk; md->S = S; md->K = K; md->M = blk_M(blk);
     md->literal = literal;
     md->Rmax = (int64_t)Nodd * S * K;                                 /* Eq. (3) */
-    md->b = or_bits(md->Rmax);                                        /* Eq. (6), reading c3 */
+    md->b = or_bits(md->Rmax);                                        /* Eq. (6), eps = 2^-b */
     md->ck = or_compand_factor(K, Mk);                                /* Eq. (2) */
     int32_t* kq = calloc((size_t)Nodd + 1, sizeof(int32_t));
     if (!kq) return OR_ERR_ARG;
     or_compand(kr, N, md->ck, kq);                                    /* k~[N..N'] = 0 */
     if (blk == OR_BLK_SYM && literal) {
-        /* Eq. (5) with the paper's eps^-1 = 2 R_max (pair order as reading c2):
+        /* Eq. (5) with the paper's eps^-1 = 2 R_max (the swapped pair order above):
          * kbar[n] = k~[2n+1] + eps^-1 k~[2n], an exact integer in FP64 */
         md->nk = (Nodd + 1) / 2;
         md->kpk = malloc(sizeof(double) * (size_t)md->nk);
@@ -682,7 +686,7 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     if (rc) return rc;
     int32_t Nodd = p.Nodd, Wb = Wblock;
 
-    /* Section II / reading c9: xcorr(s, t) = conv(s, reverse(t)). */
+    /* Section II: xcorr(s, t) = conv(s, reverse(t)). */
     float* kr = calloc((size_t)Nodd, sizeof(float));
     if (!kr) return OR_ERR_ARG;
     for (int32_t n = 0; n < N; ++n) kr[n] = op == OR_OP_XCORR ? k[N - 1 - n] : k[n];

@@ -28,10 +28,12 @@ FULL_FP64 = 0x1000
 LITERAL = 0x2000
 BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
 
-# apx_request as a numpy record (64 bytes, natural C alignment)
-REQUEST_DTYPE = np.dtype({"names": ["s_in", "L", "k", "N", "r_out", "W_block", "mode", "snr_target_db", "S_q", "K_q"],
-                          "formats": ["<u8", "<i8", "<u8", "<i4", "<u8", "<i4", "<u4", "<f8", "<i4", "<i4"],
-                          "offsets": [0, 8, 16, 24, 32, 40, 44, 48, 56, 60], "itemsize": 64})
+# apx_request as a numpy record (80 bytes, natural C alignment)
+REQUEST_DTYPE = np.dtype({"names": ["s_in", "L", "k", "N", "r_out", "W_block", "mode", "snr_target_db", "S_q", "K_q",
+                                    "rq_out", "stats"],
+                          "formats": ["<u8", "<i8", "<u8", "<i4", "<u8", "<i4", "<u4", "<f8", "<i4", "<i4", "<u8",
+                                      "<u8"],
+                          "offsets": [0, 8, 16, 24, 32, 40, 44, 48, 56, 60, 64, 72], "itemsize": 80})
 STATS_DTYPE = np.dtype([("mode", "<i4"), ("Sq", "<i4"), ("Kq", "<i4"), ("b", "<i4"), ("cs", "<f4"),
                         ("maxabs", "<f4"), ("sigma2", "<f8"), ("snr_pred_db", "<f8"), ("fft_err", "<f8")])
 assert STATS_DTYPE.itemsize == 48
@@ -40,10 +42,10 @@ class Request(C.Structure):
     """apx_request of include/apx.h."""
     _fields_ = [("s_in", C.c_void_p), ("L", C.c_int64), ("k", C.c_void_p), ("N", C.c_int32),
                 ("r_out", C.c_void_p), ("W_block", C.c_int32), ("mode", C.c_uint32), ("snr_target_db", C.c_double),
-                ("S_q", C.c_int32), ("K_q", C.c_int32)]
+                ("S_q", C.c_int32), ("K_q", C.c_int32), ("rq_out", C.c_void_p), ("stats", C.c_void_p)]
 
 
-assert C.sizeof(Request) == 64
+assert C.sizeof(Request) == 80
 
 # (restype, argtypes) of every entry point in include/apx.h
 _vp, _i32, _i64, _u32, _d, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double, C.c_size_t
@@ -75,17 +77,17 @@ SIGNATURES = {
     "apx_test_stall_next": (C.c_int, [_vp]),
     "apx_test_skew_tickets": (C.c_int, [_vp, _i64]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
+    "apx_filterbank_blocks": (C.c_int, [_i64, _i32, _i32, _i32, _i32, C.POINTER(_i32), C.POINTER(_i64)]),
 }
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
 
 
 def filterbank_blocks(L, F, N, Sq=127, Kq=127):
-    """(outputs per block T, number of blocks) of apx_filterbank (FP8 operands
-    when S_q, K_q <= 16: 128 phases per row for two or more kernels)."""
-    fp8 = Sq <= 16 and Kq <= 16
-    P = 256 if F == 1 else (128 if (F == 2 or fp8) else 64)
-    T = 128 * P
-    return T, (L + N - 1 + T - 1) // T
+    """(outputs per block T, number of blocks) of apx_filterbank, as the library
+    chooses them (apx_filterbank_blocks)."""
+    T, nb = _i32(), _i64()
+    _check("apx_filterbank_blocks", lib().apx_filterbank_blocks(L, F, N, Sq, Kq, C.byref(T), C.byref(nb)))
+    return T.value, nb.value
 
 
 class ApxError(RuntimeError):
@@ -157,6 +159,26 @@ def _dev_f32(t, name):
     return t
 
 
+def _check_call(s, k, r, device, rq=None, stats=None, W_block=None, mode=0):
+    """Sizes and devices of a call's tensors: r (and rq) hold L+N-1 outputs,
+    stats one record per block, and every tensor is on `device` (the device the
+    library launches on), so that a wrong tensor is a Python error rather than
+    an out-of-bounds or cross-device access on the GPU."""
+    import torch
+    out = s.numel() + k.numel() - 1
+    if r.numel() < out:
+        raise ValueError("r_out holds %d floats, the call writes L+N-1 = %d" % (r.numel(), out))
+    if rq is not None and not (rq.is_cuda and rq.dtype == torch.int32 and rq.is_contiguous() and rq.numel() >= out):
+        raise ValueError("rq_out must be a contiguous int32 CUDA tensor of at least L+N-1 = %d entries" % out)
+    if stats is not None:
+        P, _ = plan_blocks(s.numel(), k.numel(), W_block, mode)
+        if not (stats.is_cuda and stats.is_contiguous() and stats.numel() * stats.element_size() >= P * STATS_DTYPE.itemsize):
+            raise ValueError("stats must be a contiguous CUDA tensor of at least %d bytes" % (P * STATS_DTYPE.itemsize))
+    for name, t in (("s_in", s), ("k", k), ("r_out", r), ("rq_out", rq), ("stats", stats)):
+        if t is not None and t.device.index != device:
+            raise ValueError("%s is on cuda:%s, the call runs on cuda:%d" % (name, t.device.index, device))
+
+
 class Graph:
     """A captured batch (apx_graph)."""
 
@@ -202,7 +224,9 @@ class PreparedKernel:
 def apx_conv_fft_static(s, k, W_block, mode, snr_db, r, stream=None):
     """Allocation-free FFT-core call (no context): s, k, r are CUDA float32
     tensors on the current device."""
+    import torch
     _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+    _check_call(s, k, r, torch.cuda.current_device())  # the entry point's scratch belongs to the current device
     return _check("apx_conv_fft_static", lib().apx_conv_fft_static(_ptr(s), s.numel(), _ptr(k), k.numel(), W_block,
                                                                    mode, float(snr_db), _ptr(r), _stream(stream)))
 
@@ -247,17 +271,20 @@ class Context:
     # ---------------------------------------------------------------- raw entry points
     def apx_conv(self, s, k, W_block, mode, snr_db, r, rq=None, stats=None, stream=None):
         _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        _check_call(s, k, r, self.device, rq, stats, W_block, mode)
         return _check("apx_conv", lib().apx_conv(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(), W_block, mode,
                                                  float(snr_db), _ptr(r), _ptr(rq), _ptr(stats), _stream(stream)))
 
     def apx_conv_fixed(self, s, k, W_block, mode, Sq, Kq, r, rq=None, stats=None, stream=None):
         _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        _check_call(s, k, r, self.device, rq, stats, W_block, mode)
         return _check("apx_conv_fixed", lib().apx_conv_fixed(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(),
                                                              W_block, mode, Sq, Kq, _ptr(r), _ptr(rq),
                                                              _ptr(stats), _stream(stream)))
 
     def apx_conv_full(self, s, k, W_block, mode, r, stream=None):
         _dev_f32(s, "s_in"); _dev_f32(k, "k"); _dev_f32(r, "r_out")
+        _check_call(s, k, r, self.device)
         return _check("apx_conv_full", lib().apx_conv_full(self._h, _ptr(s), s.numel(), _ptr(k), k.numel(),
                                                            W_block, mode, _ptr(r), _stream(stream)))
 
@@ -293,7 +320,9 @@ class Context:
     @staticmethod
     def make_requests(items):
         """items: dicts with s, k, r (CUDA float32 tensors), mode, and optional
-        W_block, snr_db, Sq, Kq.  Returns a ctypes array of Request."""
+        W_block, snr_db, Sq, Kq, rq (int32 CUDA tensor, L+N-1) and stats (CUDA
+        tensor of one apx_block_stats record per block).  Returns a ctypes
+        array of Request."""
         arr = (Request * len(items))()
         for q, it in zip(arr, items):
             s, k, r = it["s"], it["k"], it["r"]
@@ -303,6 +332,12 @@ class Context:
             q.mode = int(it.get("mode", 0))
             q.snr_target_db = float(it.get("snr_db", 0.0))
             q.S_q, q.K_q = int(it.get("Sq", 0)), int(it.get("Kq", 0))
+            rq, st = it.get("rq"), it.get("stats")
+            if rq is not None and not (rq.is_cuda and rq.dtype == __import__("torch").int32 and rq.is_contiguous()
+                                       and rq.numel() >= s.numel() + k.numel() - 1):
+                raise ValueError("rq must be a contiguous int32 CUDA tensor of L+N-1 entries")
+            q.rq_out = None if rq is None else rq.data_ptr()
+            q.stats = None if st is None else st.data_ptr()
         return arr
 
     def apx_conv_batch(self, reqs, stream=None):

@@ -1,8 +1,8 @@
 // apx_api.cu -- host side of libapx: the C ABI declared in include/apx.h.
 //
 // Per call: validate, plan the blocks (Section III, Eq. 17), choose the packing
-// candidates (largest S_q = K_q within each packing's exactness bound, reading
-// c5; Section IV.D), then enqueue the kernel preparation and the block kernels
+// candidates (largest S_q = K_q for which the FP64 packed convolution stays
+// exact; Section IV.D), then enqueue the kernel preparation and the block kernels
 // on the caller's stream.  Nothing here touches sample data on the host.
 #include <nvtx3/nvToolsExt.h>
 #include <math.h>
@@ -114,7 +114,9 @@ void release(apx_ctx* c, DevBuf& b) {
 }
 
 // ------------------------------------------------------------------ host arithmetic of the selector
-// eps = 2^-b, smallest b with 2^b >= 2 R_max + 1 (reading c3).
+// eps = 2^-b, smallest b with 2^b >= 2 R_max + 1 (the paper's eps = (2 R_max)^-1,
+// Eq. 6, rounded to a power of two so that every packed value is an exact multiple
+// of the finest digit).
 int bits_for(long long Rmax) {
     int b = 0;
     while (b < 62 && (1ll << b) < 2 * Rmax + 1) ++b;
@@ -123,7 +125,9 @@ int bits_for(long long Rmax) {
 
 typedef unsigned __int128 u128;
 
-// Reading c5: exactness of the FP64 packed convolution (scaled magnitude <= 2^53).
+// Exactness of the FP64 packed convolution with eps = 2^-b: every packed word,
+// product and partial sum, scaled by the finest digit, stays <= 2^53 (this
+// replaces Table 1's companding-range row for a power-of-two eps).
 bool exact_ok(int blk, int Nodd, int S, int K) {
     if (Nodd < 1 || S < 1 || K < 1) return false;
     u128 SK = (u128)(unsigned)S * (unsigned)K;
@@ -155,7 +159,8 @@ int qmax_direct(int blk, int Nodd) {
     return lo;
 }
 
-// Reading c7: (3 phi + 16 u) with phi = Lg eta / (1 - Lg eta), eta = mu + gamma_4 (sqrt 2 + mu),
+// FFT-core error bound constant (the FFT round-off must stay below a quarter of
+// the finest digit so that rounding recovers the digits): (3 phi + 16 u) with phi = Lg eta / (1 - Lg eta), eta = mu + gamma_4 (sqrt 2 + mu),
 // mu = 4u, Lg = log2(n) + 2 (Higham, Thm 24.2, for radix-2 structured FFTs).
 double fft_const(int log2n) {
     const double u = ldexp(1.0, -53);
@@ -240,46 +245,49 @@ int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
 
 int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
-// Direct core shared-memory layout for the candidate set: window (zero front
-// pad), FP32 taps, and for packed blocks the packed signal, the packed outputs
-// and the packed taps.
+// Direct core shared-memory layout for the candidate set.  Full precision:
+// the FP32 window behind a zero pad of N' samples, then one chunk of FP32
+// taps.  Packed blocks: the packed signal in a region of its own; the packed
+// outputs and one chunk of packed taps overlay the FP32 window (packing is the
+// last step to read it).  Taps are staged a chunk at a time (kDirectTapChunk*),
+// so every packing fits one CTA up to the largest W_block at any kernel length.
 size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl, bool full64 = false) {
+    auto al16 = [](size_t b) { return (b + 15) / 16 * 16; };
     dl->padF = round_up(Nodd, 8);
-    size_t off = (size_t)4 * (dl->padF + Wb + 8);
-    dl->offK = (int)((off + 15) / 16 * 16);
-    off = (size_t)dl->offK + (size_t)4 * round_up(Nodd, 8);
-    int padS = 0, body = 0, nT = 0, nkb = 0;
-    if (full64) {  // the window and the taps as FP64
-        padS = nkb = round_up(Nodd, 4);
-        body = Wb + 4;
-        dl->offS = (int)((off + 15) / 16 * 16);
-        dl->padS = padS;
-        dl->nS = padS + body;
-        dl->offT = (int)(((size_t)dl->offS + (size_t)8 * dl->nS + 15) / 16 * 16);
+    dl->offK = (int)al16((size_t)4 * (dl->padF + Wb + 8));
+    const int kcf = round_up(Nodd, 8) < kDirectTapChunkF ? round_up(Nodd, 8) : kDirectTapChunkF;
+    const size_t full_end = (size_t)dl->offK + (size_t)4 * kcf;
+    if (full64) {  // the window and every tap as FP64, behind the FP32 region
+        const int nkb = round_up(Nodd, 4);
+        dl->offS = (int)al16(full_end);
+        dl->padS = nkb;
+        dl->nS = nkb + Wb + 4;
+        dl->offT = (int)al16((size_t)dl->offS + (size_t)8 * dl->nS);
         dl->offKb = dl->offT;
         return (size_t)dl->offKb + (size_t)8 * nkb;
     }
+    int body = 0, nT = 0, kcd = 0;
     for (int i = 0; i < nc; ++i) {
-        int nkp = round_up(c[i].nk, 4);
-        if (nkp > padS) padS = nkp;
-        if (nkp > nkb) nkb = nkp;
+        const int nkp = round_up(c[i].nk, 4);
+        const int kc = nkp < kDirectTapChunkD ? nkp : kDirectTapChunkD;
+        if (kc > kcd) kcd = kc;
         if (c[i].blk == APX_BLK_SYM) {
-            body = body > Wb / 2 + 4 ? body : Wb / 2 + 4;
+            body = body > Wb / 2 ? body : Wb / 2;
             nT = nT > Wb / 2 ? nT : Wb / 2;
         } else {
-            int Ls = (Wb + c[i].M - 1) / c[i].M;
-            int bb = Ls + Nodd + 4;
-            body = body > bb ? body : bb;
-            int t = Ls + Nodd - 1 < Wb ? Ls + Nodd - 1 : Wb;
+            const int Ls = (Wb + c[i].M - 1) / c[i].M;
+            body = body > Ls ? body : Ls;
+            const int t = Ls + Nodd - 1 < Wb ? Ls + Nodd - 1 : Wb;
             nT = nT > t ? nT : t;
         }
     }
-    dl->offS = (int)((off + 15) / 16 * 16);
-    dl->padS = padS;
-    dl->nS = nc ? padS + body : 0;
-    dl->offT = (int)(((size_t)dl->offS + (size_t)8 * dl->nS + 15) / 16 * 16);
-    dl->offKb = (int)(((size_t)dl->offT + (size_t)8 * nT + 15) / 16 * 16);
-    return (size_t)dl->offKb + (size_t)8 * nkb;
+    dl->padS = 0;
+    dl->nS = body;
+    dl->offT = 0;
+    dl->offKb = (int)al16((size_t)8 * nT);
+    const size_t over = (size_t)dl->offKb + (size_t)8 * kcd;
+    dl->offS = (int)al16(full_end > over ? full_end : over);
+    return nc ? (size_t)dl->offS + (size_t)8 * body : full_end;
 }
 
 // exp(-2 pi i t / Wb), t in [0, Wb), from long double arithmetic.  One table
@@ -537,10 +545,14 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
         p.epoch = ctx->epoch;
         if (ctx->stall_next) {  // claimed by no one who will build them: blocks that pick a packing time out
             ctx->stall_next = 0;
-            const unsigned ep[kMaxCand] = {p.epoch, p.epoch, p.epoch};
-            cudaError_t e0 = cudaMemcpyAsync(p.claim, ep, sizeof ep, cudaMemcpyHostToDevice, stream);
-            if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(stream);  // the host array goes out of scope
-            if (e0 != cudaSuccess) return cuda_status(e0);
+            if (p.fused) {
+                const unsigned ep[kMaxCand] = {p.epoch, p.epoch, p.epoch};
+                cudaError_t e0 = cudaMemcpyAsync(p.claim, ep, sizeof ep, cudaMemcpyHostToDevice, stream);
+                if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(stream);  // the host array goes out of scope
+                if (e0 != cudaSuccess) return cuda_status(e0);
+            } else {
+                p.claim_init = p.epoch;  // the spectrum launch claims them
+            }
         }
         e = cudaSuccess;
         if (!p.fused) {
@@ -620,8 +632,8 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
         int sel = 0;
         if (pack == APX_PACK_NONE) sel = 2;
         else if (pack != APX_PACK_AUTO && q.S_q > 0 && q.K_q > 0) sel = 1;
-        int rc = make_params(q.s_in, q.L, q.k, q.N, Wb, mode, sel, q.snr_target_db, q.S_q, q.K_q, q.r_out, nullptr,
-                             nullptr, &bp->prm[r], &bp->smem[r]);
+        int rc = make_params(q.s_in, q.L, q.k, q.N, Wb, mode, sel, q.snr_target_db, q.S_q, q.K_q, q.r_out, q.rq_out,
+                             q.stats, &bp->prm[r], &bp->smem[r]);
         if (rc) return rc;
     }
     // group by core and W_block, and apart the requests without packing candidates
@@ -1028,7 +1040,7 @@ extern "C" int apx_conv_batch_host(apx_ctx* ctx, const apx_request* reqs, int32_
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     for (int32_t i = 0; i < n; ++i) {
         const apx_request& q = reqs[i];
-        if (!q.s_in || !q.k || !q.r_out || q.L < 1 || q.N < 1) return APX_ERR_ARG;
+        if (!q.s_in || !q.k || !q.r_out || q.L < 1 || q.N < 1 || q.rq_out || q.stats) return APX_ERR_ARG;
         const void* sa = host_alias(q.s_in);
         const void* ka = sa ? host_alias(q.k) : nullptr;
         void* ra = ka ? host_alias(q.r_out) : nullptr;
@@ -1128,6 +1140,19 @@ extern "C" int apx_filterbank(apx_ctx* ctx, const float* s_in, int64_t L, const 
     if (enc_failed) return APX_ERR_CUDA;
     if (e == cudaSuccess) ctx->launches += 3;
     return cuda_status(e);
+}
+
+extern "C" int apx_filterbank_blocks(int64_t L, int32_t F, int32_t N, int32_t S_q, int32_t K_q, int32_t* T,
+                                     int64_t* nb) {
+    if (L < 1 || F < 1 || N < 1 || F > kTcMaxF || N > kTcMaxN) return APX_ERR_ARG;
+    if (S_q < 1 || K_q < 1 || S_q > kTcMaxQ || K_q > kTcMaxQ) return APX_ERR_RANGE;
+    if ((long long)N * S_q * K_q > kTcExactSum) return APX_ERR_RANGE;
+    TcGeom g;
+    const int esize = (S_q <= kTcMaxQ8 && K_q <= kTcMaxQ8) ? 1 : 2;  // as apx_filterbank chooses
+    if (!tc_geometry(L, F, N, esize, &g)) return APX_ERR_ARG;
+    if (T) *T = g.T;
+    if (nb) *nb = g.nb;
+    return APX_OK;
 }
 
 // ------------------------------------------------------------------ prepared kernels
@@ -1378,20 +1403,21 @@ static __device__ __align__(256) unsigned char g_apx_scratch[kStaticBytes];
 namespace {
 
 struct StaticDevice {
-    unsigned char* base = nullptr;  // device address of g_apx_scratch on this device
-    int tw_wb = 0;                  // W_block the twiddle tables hold
+    unsigned char* base = nullptr;  // device address of g_apx_scratch on this device (null: not set up)
     unsigned epoch = 0;             // call number (claims of on-demand spectra)
     unsigned long long tickets = 0; // CTA tickets handed out by fused launches
 };
 std::mutex g_static_mu;
 StaticDevice g_static[64];
 
-// exp(-2 pi i t / Wb) from sincospi of the exact ratio 2t/Wb.
-__global__ void k_twiddles(double2* t64, float2* t32, int Wb) {
+// exp(-2 pi i t / n) from sincospi of the exact ratio 2t/n, t < n = kStaticWbMax:
+// one table for every W_block up to the maximum (a transform of length Wb reads
+// every (n / Wb)-th entry, whose ratio 2 (t n / Wb) / n = 2t / Wb is exact).
+__global__ void k_twiddles(double2* t64, float2* t32, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Wb) return;
+    if (t >= n) return;
     double sn, cs;
-    sincospi(2.0 * (double)t / (double)Wb, &sn, &cs);
+    sincospi(2.0 * (double)t / (double)n, &sn, &cs);
     t64[t] = make_double2(cs, -sn);
     t32[t] = make_float2((float)cs, (float)-sn);
 }
@@ -1412,20 +1438,26 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
 
     unsigned char* base;
     unsigned epoch;
-    bool need_tw;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
         StaticDevice& sd = g_static[dev];
-        if (!sd.base) {  // first call on this device: the array's device address
-            void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_apx_scratch) != cudaSuccess || !ptr) return APX_ERR_CUDA;
-            // the flag words start from zero (the ticket counter matches `tickets`)
+        // The array's device address on this device (the host-side name is not one).
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_apx_scratch) != cudaSuccess || !ptr) return APX_ERR_CUDA;
+        if (sd.base != (unsigned char*)ptr) {
+            // first call on this device (or the module was loaded anew): the flag
+            // words start from zero (the ticket counter matches `tickets`), and the
+            // twiddle tables are filled once at the maximum length
             if (cudaMemsetAsync(ptr, 0, kSOffKInfo, st) != cudaSuccess) return APX_ERR_CUDA;
-            sd.base = (unsigned char*)ptr;
+            unsigned char* b = (unsigned char*)ptr;
+            k_twiddles<<<(kStaticWbMax + 255) / 256, 256, 0, st>>>((double2*)(b + kSOffTw64), (float2*)(b + kSOffTw32),
+                                                                  kStaticWbMax);
+            if (cudaGetLastError() != cudaSuccess) return APX_ERR_CUDA;
+            sd.base = b;
+            sd.epoch = 0;
+            sd.tickets = 0;
         }
         if (++sd.epoch == 0) sd.epoch = 1;
-        need_tw = sd.tw_wb != W_block;
-        sd.tw_wb = W_block;
         base = sd.base;
         epoch = sd.epoch;
     }
@@ -1463,7 +1495,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     p.Ysub = (float2*)(base + kSOffYsub);
     p.tw32 = (const float2*)(base + kSOffTw32);
     p.tw64 = (const double2*)(base + kSOffTw64);
-    p.ntab = W_block;
+    p.ntab = kStaticWbMax;
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)(base + kSOffHc + j * kSHcBytes);
     const size_t smem = fft_smem_bytes(p);
     if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
@@ -1475,12 +1507,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     }
 
     cudaError_t e = cudaSuccess;
-    if (need_tw) {
-        k_twiddles<<<(W_block + 255) / 256, 256, 0, st>>>((double2*)(base + kSOffTw64), (float2*)(base + kSOffTw32),
-                                                          W_block);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && !p.fused) e = launch_spec(p, st);
+    if (!p.fused) e = launch_spec(p, st);
     if (e == cudaSuccess && !p.fused) e = launch_spec_combine(p, st);
     if (e == cudaSuccess) e = p.fused ? launch_fft_fused(p, smem, st) : launch_fft(p, smem, st);
     if (e != cudaSuccess && p.fused) {  // not launched: its tickets were never taken

@@ -59,7 +59,8 @@ struct Shared {
     double bcast[4];
 };
 
-// Tap n of the convolution kernel: reversed for cross-correlation (reading c9),
+// Tap n of the convolution kernel: reversed for cross-correlation
+// (xcorr(s, t) = conv(s, reverse(t)); the paper only names Matlab's xcorr),
 // zero past N (the odd-length pad of Section III).
 __device__ __forceinline__ float ktap(const Params& p, int n) {
     return n < p.N ? __ldg(&p.k[p.xcorr ? p.N - 1 - n : n]) : 0.f;

@@ -15,19 +15,27 @@ namespace apx {
 constexpr int kRf = 8;  // FP32 outputs per thread (taps padded to a multiple of 8)
 constexpr int kRd = 4;  // FP64 outputs per thread (taps padded to a multiple of 4)
 
-// acc[r] = sum_{n < nkp} sig[j0 + r - n] taps[n] with signal and taps in shared
-// memory; sig is zero-padded by >= nkp in front.  Register ring: slot (t mod R)
+// Taps are staged in shared memory a chunk at a time, so that neither the
+// kernel length nor the block length limits which packings a CTA can run.
+// The chunked forms continue the sums the previous chunk left in acc, in the
+// same order as one pass over all taps would take.
+constexpr int kKcF = kDirectTapChunkF;  // FP32 taps per chunk (8 KB)
+constexpr int kKcD = kDirectTapChunkD;  // packed FP64 taps per chunk (8 KB)
+
+// acc[r] += sum_{n0 <= n < n1} sig[j0 + r - n] taps[n - n0], n1 - n0 a multiple
+// of R; sig is zero-padded by >= n1 in front.  Register ring: slot (t mod R)
 // holds sig[j0 + t - n].
 template <int R>
-__device__ __forceinline__ void conv_f32(const float* sig, const float* taps, int nkp, int j0, float (&acc)[R]) {
+__device__ __forceinline__ void conv_f32(const float* sig, const float* taps, int n0, int n1, int j0,
+                                         float (&acc)[R]) {
     float w[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { acc[r] = 0.f; w[r] = sig[j0 + r]; }
-    for (int n = 0; n < nkp; n += R) {
+    for (int r = 0; r < R; ++r) w[r] = sig[j0 + r - n0];
+    for (int n = n0; n < n1; n += R) {
         float t[R];
 #pragma unroll
         for (int v = 0; v < R; v += 4) {
-            float4 q = *reinterpret_cast<const float4*>(taps + n + v);
+            float4 q = *reinterpret_cast<const float4*>(taps + (n - n0) + v);
             t[v] = q.x; t[v + 1] = q.y; t[v + 2] = q.z; t[v + 3] = q.w;
         }
 #pragma unroll
@@ -39,8 +47,41 @@ __device__ __forceinline__ void conv_f32(const float* sig, const float* taps, in
     }
 }
 
+// The packed FP64 form over the nsig packed words, zero outside [0, nsig)
+// (the block's history and tail; a predicated read costs nothing beside an
+// FP64 multiply-add).  NOFMA: separate correctly rounded products and sums in
+// the same order (the paper-literal form, the oracle's arithmetic step for
+// step).
+template <int R, bool NOFMA>
+__device__ __forceinline__ void conv_f64(const double* sig, int nsig, const double* taps, int n0, int n1, int j0,
+                                         double (&acc)[R]) {
+    auto at = [&](int i) { return (unsigned)i < (unsigned)nsig ? sig[i] : 0.0; };
+    double w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = at(j0 + r - n0);
+    for (int n = n0; n < n1; n += R) {
+        double t[R];
+#pragma unroll
+        for (int v = 0; v < R; v += 2) {
+            double2 q = *reinterpret_cast<const double2*>(taps + (n - n0) + v);
+            t[v] = q.x; t[v + 1] = q.y;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                acc[r] = NOFMA ? __dadd_rn(acc[r], __dmul_rn(w[(r - u + R) % R], t[u]))
+                               : fma(w[(r - u + R) % R], t[u], acc[r]);
+            w[R - 1 - u] = at(j0 - n - u - 1);
+        }
+    }
+}
+
+// The FP64 full-precision form (APX_FULL_FP64): every tap resident, the
+// window zero-padded by >= nkp in front.
 template <int R>
-__device__ __forceinline__ void conv_f64(const double* sig, const double* taps, int nkp, int j0, double (&acc)[R]) {
+__device__ __forceinline__ void conv_f64_full(const double* sig, const double* taps, int nkp, int j0,
+                                              double (&acc)[R]) {
     double w[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc[r] = 0.0; w[r] = sig[j0 + r]; }
@@ -55,30 +96,6 @@ __device__ __forceinline__ void conv_f64(const double* sig, const double* taps, 
         for (int u = 0; u < R; ++u) {
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = fma(w[(r - u + R) % R], t[u], acc[r]);
-            w[R - 1 - u] = sig[j0 - n - u - 1];
-        }
-    }
-}
-
-// The same sums as separate correctly rounded products and additions, in the
-// same order (the paper-literal form: the oracle's arithmetic step for step).
-template <int R>
-__device__ __forceinline__ void conv_f64_nofma(const double* sig, const double* taps, int nkp, int j0,
-                                               double (&acc)[R]) {
-    double w[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { acc[r] = 0.0; w[r] = sig[j0 + r]; }
-    for (int n = 0; n < nkp; n += R) {
-        double t[R];
-#pragma unroll
-        for (int v = 0; v < R; v += 2) {
-            double2 q = *reinterpret_cast<const double2*>(taps + n + v);
-            t[v] = q.x; t[v + 1] = q.y;
-        }
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = __dadd_rn(acc[r], __dmul_rn(w[(r - u + R) % R], t[u]));
             w[R - 1 - u] = sig[j0 - n - u - 1];
         }
     }
@@ -128,7 +145,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         for (int ch = threadIdx.x; ch * kRd < nout; ch += blockDim.x) {
             const int j0 = g.lo + ch * kRd;
             double acc[kRd];
-            conv_f64<kRd>(sd, kd, nkp, j0, acc);
+            conv_f64_full<kRd>(sd, kd, nkp, j0, acc);
 #pragma unroll
             for (int r = 0; r < kRd; ++r) {
                 const int j = j0 + r;
@@ -143,24 +160,35 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         return;
     }
     if (ci < 0) {
-        // Full precision (FP32), Eq. (1) over the window, taps staged in shared memory.
+        // Full precision (FP32), Eq. (1) over the window, taps staged in
+        // shared memory a chunk at a time; a later chunk continues the sums
+        // the thread stored for its outputs.
         const int nkp = round_up(p.Nodd, kRf);
         float* kf = reinterpret_cast<float*>(smem + dl.offK);
-        for (int n = threadIdx.x; n < nkp; n += blockDim.x) kf[n] = ktap(p, n);
-        __syncthreads();
         const int nout = g.hi - g.lo;
-        for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
-            const int j0 = g.lo + ch * kRf;
-            if (!APX_IN_BOUNDS(j0 - nkp >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
-            float acc[kRf];
-            conv_f32<kRf>(xs, kf, nkp, j0, acc);
+        for (int n0 = 0; n0 < nkp; n0 += kKcF) {
+            const int n1 = min(nkp, n0 + kKcF);
+            if (n0 > 0) __syncthreads();  // every thread is done with the previous chunk
+            for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) kf[n - n0] = ktap(p, n);
+            __syncthreads();
+            for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
+                const int j0 = g.lo + ch * kRf;
+                if (!APX_IN_BOUNDS(j0 - n1 >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
+                float acc[kRf];
 #pragma unroll
-            for (int r = 0; r < kRf; ++r) {
-                const int j = j0 + r;
-                const long long o = g.start + j;
-                if (j < g.hi && o >= 0 && o < p.out_len) {
-                    p.r[o] = acc[r];
-                    if (p.rq) p.rq[o] = 0;
+                for (int r = 0; r < kRf; ++r) {
+                    const long long o = g.start + j0 + r;
+                    acc[r] = (n0 > 0 && j0 + r < g.hi && o >= 0 && o < p.out_len) ? p.r[o] : 0.f;
+                }
+                conv_f32<kRf>(xs, kf, n0, n1, j0, acc);
+#pragma unroll
+                for (int r = 0; r < kRf; ++r) {
+                    const int j = j0 + r;
+                    const long long o = g.start + j;
+                    if (j < g.hi && o >= 0 && o < p.out_len) {
+                        p.r[o] = acc[r];
+                        if (p.rq && n1 == nkp) p.rq[o] = 0;
+                    }
                 }
             }
         }
@@ -172,12 +200,12 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
     const float ck = compand_factor(c.K, ks.Mk);
     const double eps = LIT ? c.eps_l : ldexp(1.0, -c.b);
-    double* sb = reinterpret_cast<double*>(smem + dl.offS) + dl.padS;
+    // packed signal (its own region); packed outputs and the packed-tap chunk
+    // overlay the FP32 window, which packing is the last to read
+    double* sb = reinterpret_cast<double*>(smem + dl.offS);
     double* tb = reinterpret_cast<double*>(smem + dl.offT);
     double* kb = reinterpret_cast<double*>(smem + dl.offKb);
     const int nkp = round_up(c.nk, kRd);
-    for (int n = threadIdx.x; n < nkp; n += blockDim.x)  // Eq. (5) / k~
-        kb[n] = LIT ? kbar_literal(p, c, ck, n) : (double)kbar_int(p, c, ck, n);
     int nsb, Ls = 0;
     if (c.blk == APX_BLK_SYM) {
         nsb = p.Wb / 2;
@@ -199,11 +227,11 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
             sb[m] = acc;
         }
     }
-    for (int t = threadIdx.x; t < dl.padS; t += blockDim.x) sb[t - dl.padS] = 0.0;
-    for (int t = nsb + threadIdx.x; t < dl.nS - dl.padS; t += blockDim.x) sb[t] = 0.0;
-    __syncthreads();
+    __syncthreads();  // the FP32 window is free from here on
 
-    // Packed FP64 block convolution (Eq. 9 / Eq. 8): exact by the c5 bound.
+    // Packed FP64 block convolution (Eq. 9 / Eq. 8): exact, since S_q, K_q keep
+    // every scaled partial sum below 2^53,
+    // taps staged a chunk at a time, partial sums kept in the output buffer.
     int olo, ohi, nr = 0;
     if (c.blk == APX_BLK_SYM) {
         olo = g.wstart; ohi = g.hi / 2;
@@ -212,14 +240,23 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         olo = max(0, g.lo - (c.M - 1) * Ls);
         ohi = min(g.hi, nr);
     }
-    for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
-        const int j0 = olo + ch * kRd;
-        double acc[kRd];
-        if (LIT) conv_f64_nofma<kRd>(sb, kb, nkp, j0, acc);
-        else conv_f64<kRd>(sb, kb, nkp, j0, acc);
+    for (int n0 = 0; n0 < nkp; n0 += kKcD) {
+        const int n1 = min(nkp, n0 + kKcD);
+        if (n0 > 0) __syncthreads();  // every thread is done with the previous chunk
+        for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x)  // Eq. (5) / k~
+            kb[n - n0] = LIT ? kbar_literal(p, c, ck, n) : (double)kbar_int(p, c, ck, n);
+        __syncthreads();
+        for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
+            const int j0 = olo + ch * kRd;
+            double acc[kRd];
 #pragma unroll
-        for (int r = 0; r < kRd; ++r)
-            if (j0 + r < ohi) tb[j0 + r] = acc[r];
+            for (int r = 0; r < kRd; ++r) acc[r] = (n0 > 0 && j0 + r < ohi) ? tb[j0 + r] : 0.0;
+            if (LIT) conv_f64<kRd, true>(sb, nsb, kb, n0, n1, j0, acc);
+            else conv_f64<kRd, false>(sb, nsb, kb, n0, n1, j0, acc);
+#pragma unroll
+            for (int r = 0; r < kRd; ++r)
+                if (j0 + r < ohi) tb[j0 + r] = acc[r];
+        }
     }
     __syncthreads();
 

@@ -11,7 +11,8 @@
 //   2. starts the FP32 forward real FFT of the window (full precision is every
 //      block's fallback) before it waits for the preparation,
 //   3. runs the Section IV.D selection; for a packing candidate it companded
-//      the block and checks the FFT error bound (reading c7) with the exact
+//      the block and checks the FFT error bound (the round-off of the FP64
+//      transforms below a quarter of the finest digit) with the exact
 //      integer norms sum(s~^2) and ||kbar||_1, so rounding recovers the digits,
 //   4. full precision: multiplies by the spectrum and inverts; packed:
 //      companded and packs (Eqs. 2, 4, 7) into an FP64 complex buffer (two

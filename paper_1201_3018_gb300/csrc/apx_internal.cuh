@@ -86,6 +86,8 @@ struct Params {
     int autosel;          // 1: per-block selection under thr
     int full64;           // direct core, no packing: full precision in FP64
     int ncand;
+    unsigned claim_init;  // FFT core, three-launch single call: value k_spec writes to the claim words
+                          // (0; the call's epoch when a test stalls the builders)
     double thr;           // 10^(target/10)
     Cand cand[kMaxCand];
     DirectLayout dl;      // direct core

@@ -8,6 +8,10 @@
 namespace apx {
 
 constexpr int kDirectThreads = 256;
+// Direct core: taps staged in shared memory per chunk (FP32 taps for full
+// precision, packed FP64 taps for packed blocks).
+constexpr int kDirectTapChunkF = 2048;
+constexpr int kDirectTapChunkD = 1024;
 constexpr int kMaxSmem = 227 * 1024 - 1024;  // dynamic shared memory cap (static shared memory needs the rest)
 
 // FFT core block kernel: one thread per 16 complex points of the largest

@@ -3,7 +3,9 @@
 // launches ahead of the block kernel, for batched calls and for single calls
 // with few blocks (single calls with many blocks run the same pieces inside
 // the block kernel, see apx_prep.cuh):
-//   k_spec:   CTA r < R1 runs spec_subfft(r); CTA R1 runs spec_stats.
+//   k_spec:   CTA r < R1 runs spec_subfft(r); CTA R1 runs spec_stats; a
+//             single call's CTA 0 also resets the claim and ready words of
+//             its packed spectra.
 //   k_combine: spec_combine, one thread per frequency.
 // Each launch is the programmatic dependent of the one before it; the block
 // kernel waits for k_combine only where it multiplies by H.
@@ -19,6 +21,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const Ba
     pdl_trigger();
     const int cta = BATCH ? (int)batch_enter(bt, sp) : (int)blockIdx.x;
     const Params& p = BATCH ? sp : p0;
+    if (!BATCH && cta == 0 && threadIdx.x < kMaxCand) {
+        // A single call's packed spectra are built anew: a call captured into a
+        // graph replays with the same epoch, and its kernel taps may have
+        // changed since the last replay.  The block kernel claims them only
+        // after the combine launch, which waits for this one.
+        p0.claim[threadIdx.x] = p0.claim_init;
+        p0.ready[threadIdx.x] = 0u;
+    }
     if (cta == spec_r1(p.Wb)) spec_stats(p, sh);
     else spec_subfft(p, cta, reinterpret_cast<float2*>(smem));
 }

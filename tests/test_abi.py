@@ -58,11 +58,12 @@ def test_plan_matches_oracle(libapx, fft, L, N, Wb):
 
 
 @pytest.mark.parametrize("fft", [False, True])
-@pytest.mark.parametrize("N,Wb", [(7, 64), (64, 1024), (257, 2048), (1024, 4096), (4096, 8192), (300, 16384)])
+@pytest.mark.parametrize("N,Wb", [(7, 64), (64, 1024), (257, 2048), (1024, 4096), (4096, 8192), (300, 16384),
+                                  (8191, 16384), (4096, 16384), (16380, 16384), (1, 16384), (2047, 4096)])
 @pytest.mark.parametrize("snr", [0.0, 12.0, 20.0, 30.0, 45.0, 60.0, 90.0])
 def test_candidates_match_oracle(libapx, fft, N, Wb, snr):
     """The host half of the Section IV.D selection against the oracle's own
-    arithmetic: the largest S_q = K_q per packing (reading c5, and the FFT
+    arithmetic: the largest S_q = K_q per packing (exact FP64 packed sums, and the FFT
     bound's guide for the FFT core), eps = 2^-b, the Table 1 order, and the
     candidates left out because their model misses the target even at ratios 1."""
     mode = (libapx.CORE_FFT if fft else libapx.CORE_DIRECT) | libapx.PACK_AUTO
@@ -74,13 +75,7 @@ def test_candidates_match_oracle(libapx, fft, N, Wb, snr):
         Q = O.qmax_fft(blk, nodd, Wb) if fft else O.qmax_direct(blk, nodd)
         if Q >= 1 and O.snr_model_lin(1.0, 1.0, 1.0, 1.0, Q, Q) >= 0.99 * thr:
             want.append((blk, Q, O.bits(nodd * Q * Q)))
-    if fft or N * Wb < 4096 * 8192:
-        assert got == want
-    else:
-        # direct core at N = 4096, W_block = 8192: the asymmetric packings' shared-memory
-        # layout exceeds one CTA, so they are not offered (a documented library limit)
-        assert got == [c for c in want if c[0] == O.BLK_SYM]
-        assert len(want) >= len(got)
+    assert got == want
 
 
 def test_candidates_forced_and_none(libapx):
@@ -143,4 +138,21 @@ def test_request_record_matches_struct():
     from paper_1201_3018_gb300 import apx
     for name, _ in apx.Request._fields_:
         assert apx.REQUEST_DTYPE.fields[name][1] == getattr(apx.Request, name).offset, name
-    assert apx.REQUEST_DTYPE.itemsize == C.sizeof(apx.Request) == 64
+    assert apx.REQUEST_DTYPE.itemsize == C.sizeof(apx.Request) == 80
+
+
+@pytest.mark.parametrize("F,Q", [(1, 127), (2, 127), (3, 127), (32, 127), (1, 16), (2, 16), (32, 16)])
+def test_filterbank_blocks(libapx, F, Q):
+    """The filterbank's block geometry as the header states it: T = 128 P with
+    P = 256 (one kernel), 128 (two kernels, or FP8 operands when S_q, K_q <= 16)
+    or 64 phases per row, and ceil((L+N-1) / T) blocks."""
+    L, N = 100000, 1024
+    T, nb = libapx.filterbank_blocks(L, F, N, Q, Q)
+    P = 256 if F == 1 else (128 if (F == 2 or Q <= 16) else 64)
+    assert T == 128 * P and nb == -(-(L + N - 1) // T)
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.filterbank_blocks(L, 0, N, Q, Q)
+    assert e.value.status == libapx.APX_ERR_ARG
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.filterbank_blocks(L, F, N, 4096, Q)
+    assert e.value.status == libapx.APX_ERR_RANGE

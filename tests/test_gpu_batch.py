@@ -98,19 +98,29 @@ def test_batch_rejects_bad_request(ctx):
 def test_batched_uneven_graph_vs_oracle(ctx):
     """The 256-signal batched workload (lengths log-uniform in [2^14, 2^20],
     N in {256, 1024}, targets {30, 45, 60} dB) as one captured graph with the
-    autotuned geometry, as the benchmark launches it; 24 of the signals are
-    checked against the oracle: outputs of packed blocks within FP32
-    dequantisation rounding (the block decisions must agree for that), sampled
-    full-precision outputs within 1e-5 relative L2."""
+    autotuned geometry, as the benchmark launches it, every request returning
+    its per-block records and integer-domain outputs.  24 of the signals are
+    checked against the oracle: per-block decisions (mode, S_q, K_q, b, c_s)
+    and the integers r~ bit for bit, outputs of packed blocks within FP32
+    dequantisation rounding, sampled full-precision outputs within 1e-5
+    relative L2."""
     import oracle as O
     from paper_1201_3018_gb300 import tune
     case = wl.batched_uneven()
     tuner = tune.Tuner(ctx)
     items = tune.batch_items(case, tuner, torch.device("cuda", 0))
+    for it in items:
+        L, N = it["s"].numel(), it["k"].numel()
+        P, _ = apx.plan_blocks(L, N, it["W_block"], it["mode"])
+        it["rq"] = torch.zeros(L + N - 1, dtype=torch.int32, device="cuda")
+        it["stats"] = torch.zeros(P * apx.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     g = ctx.graph(ctx.make_requests(items))
     g.launch()
     torch.cuda.synchronize()
     g.close()
+    stats = [np.frombuffer(it["stats"].cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE) for it in items]
+    modes = np.concatenate([st["mode"] for st in stats])
+    assert np.all(np.isin(modes, (apx.BLK_FULL, apx.BLK_SYM, apx.BLK_ASYM2, apx.BLK_ASYM3, apx.BLK_ZERO)))
     rng = np.random.default_rng(4)
     for i in sorted(rng.choice(len(items), 24, replace=False)):
         it = items[i]
@@ -118,10 +128,16 @@ def test_batched_uneven_graph_vs_oracle(ctx):
         L, N = len(s), len(k)
         want = np.zeros(L + N - 1, np.uint8)
         want[rng.choice(L + N - 1, 512, replace=False)] = 1
-        ro, _, so, rc = O.apx_conv(s, k, it["W_block"], it["mode"], snr_db=it["snr_db"], nthreads=0,
-                                   want_int=False, want=want)
+        ro, rqo, so, rc = O.apx_conv(s, k, it["W_block"], it["mode"], snr_db=it["snr_db"], nthreads=0,
+                                     want_int=True, want=want)
         assert rc == 0
         so = O.stats_arrays(so)
+        st = stats[i]
+        np.testing.assert_array_equal(st["mode"], so["mode"])
+        for f in ("Sq", "Kq", "b"):
+            np.testing.assert_array_equal(st[f], so[f])
+        np.testing.assert_array_equal(st["cs"].view(np.uint32), so["cs"].astype(np.float32).view(np.uint32))
+        np.testing.assert_array_equal(it["rq"].cpu().numpy().astype(np.int64), rqo)
         fft = (it["mode"] & 0xF0) == apx.CORE_FFT
         p = O.plan(L, N, it["W_block"], fft)
         got = it["r"].cpu().numpy()
@@ -177,7 +193,7 @@ def test_batch_from_host_buffers_equals_device_batch(ctx):
             s, k, r = s.pin_memory(), k.pin_memory(), r.pin_memory()
         host.append((s, k, r))
         recs[j] = (s.data_ptr(), s.numel(), k.data_ptr(), k.numel(), r.data_ptr(), it["W_block"], it["mode"],
-                   it["snr_db"], 0, 0)
+                   it["snr_db"], 0, 0, 0, 0)
     ctx.apx_conv_batch_host(recs)
     torch.cuda.synchronize()
     assert ctx.apx_sync() == 0

@@ -142,6 +142,39 @@ def test_captured_call_replays(ctx):
         assert np.array_equal(got, want), rep
 
 
+def test_captured_packed_call_replays_with_new_kernel(ctx):
+    """A captured single call whose blocks pack: its packed kernel spectra are
+    built anew on every replay (the replays share the capture's call number),
+    so replays after the template's taps change equal fresh calls."""
+    N, Wb, mode = 255, 2048, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    L = _length_for_blocks(40, N, Wb, mode)
+    s = _dev(wl.random_signal(wl.SEED_BASE + 981, L, "laplace", 0.1))
+    k = _dev(wl.random_signal(wl.SEED_BASE + 982, N, "uniform"))
+    r = torch.empty(L + N - 1, device="cuda")
+    st = torch.empty(apx.plan_blocks(L, N, Wb, mode)[0] * apx.STATS_DTYPE.itemsize, dtype=torch.uint8,
+                     device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.apx_conv(s, k, Wb, mode, 12.0, r, stream=side)  # workspace allocated before capture
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            ctx.apx_conv(s, k, Wb, mode, 12.0, r, None, st, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    for rep in range(3):
+        k.copy_(_dev(wl.random_signal(wl.SEED_BASE + 983 + rep, N, "uniform")))
+        if rep == 2:
+            s.copy_(_dev(wl.random_signal(wl.SEED_BASE + 990, L, "laplace", 0.1)))
+        g.replay()
+        torch.cuda.synchronize()
+        got = r.cpu().numpy()
+        modes = np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)["mode"]
+        assert np.isin(modes, (apx.BLK_SYM, apx.BLK_ASYM2, apx.BLK_ASYM3)).any()
+        want, _ = _single(ctx, s, k, Wb, mode, 12.0)
+        assert np.array_equal(got, want), rep
+
+
 def test_ticket_fault_is_reported_and_recovered(ctx):
     """A ticket count out of step (host-injected): every CTA of the next
     one-launch call finds its ticket out of range and touches nothing,

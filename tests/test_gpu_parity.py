@@ -203,6 +203,23 @@ def test_max_wblock(ctx):
         check(*run_both(ctx, s, k, 16384, mode, snr=20.0, want=want), s, k, mode, 16384, want=want)
 
 
+@pytest.mark.parametrize("L,N,Wb,target", [(60000, 4096, 8192, 20.0), (50000, 8191, 16384, 12.0),
+                                            (40000, 2500, 8192, 30.0)])
+def test_direct_core_packs_long_kernels(ctx, L, N, Wb, target):
+    """Per-block selection on the direct core with long kernels at large
+    W_block: every packing the oracle offers fits one CTA (the taps stream
+    through shared memory a chunk at a time), so decisions, integers and
+    outputs match the oracle's, and blocks do pack."""
+    s = wl.random_signal(L + 51, L, "laplace", 0.1)
+    k = wl.random_signal(N + 52, N, "uniform")
+    mode = apx.OP_CONV | apx.CORE_DIRECT | apx.PACK_AUTO
+    want = np.zeros(L + N - 1, bool)
+    want[np.random.default_rng(N).choice(len(want), 3000, replace=False)] = True
+    r, rq, st, ro, rqo, so = run_both(ctx, s, k, Wb, mode, snr=target, want=want)
+    check(r, rq, st, ro, rqo, so, s, k, mode, Wb, want=want)
+    assert np.isin(st["mode"], PACKED).sum() >= 3
+
+
 def test_host_entry_point_matches_device_path(ctx):
     case = wl.single_conv(L=30000)
     sh = torch.from_numpy(case.s).pin_memory()
@@ -382,6 +399,7 @@ def test_host_entry_equals_device_path_large(ctx, core, L, N, Wb, mode_bits, snr
     (20000, 65, 8, 1024, apx.OP_CONV, "uniform"),        # small range: the exact form's digits
     (1 << 16, 800, 16, 8192, apx.OP_CONV, "u128"),       # Section IV.A's symmetric setting, beyond the exact bound
     (30000, 257, 16, 2048, apx.OP_XCORR, "laplace"),
+    (30000, 2500, 8, 8192, apx.OP_CONV, "laplace"),     # packed taps in two shared-memory chunks
 ])
 def test_paper_literal_form_matches_oracle(ctx, L, N, Q, Wb, op, dist):
     """APX_LITERAL (Eq. 6 eps, FP64 Eqs. 11-15 with u_sys, packed convolution

@@ -33,7 +33,7 @@ def test_xcorr_definition(L, N):
     g = np.random.default_rng(7 + L + N)
     s, t = g.standard_normal(L), g.standard_normal(N)
     np.testing.assert_allclose(O.xcorr_ref(s, t), np.correlate(s, t, "full"), atol=1e-12)
-    # reading c9: xcorr(s, t) = conv(s, reverse(t))
+    # xcorr(s, t) = conv(s, reverse(t))
     np.testing.assert_allclose(O.xcorr_ref(s, t), O.conv_ref(s, t[::-1]), atol=1e-12)
 
 
@@ -148,7 +148,8 @@ def test_sym_pack_unpack_reconstructs_integer_conv(nodd, n):
 
 
 def test_sym_printed_kernel_pairing_fails():
-    """Reading c2: Eq. (5) as printed does not reconstruct s~*k~."""
+    """Eq. (5) as printed (k~[2n] paired with 1, k~[2n+1] with eps^-1) does not
+    reconstruct s~*k~; the library and oracle swap the pair."""
     g = np.random.default_rng(99)
     fails = 0
     for trial in range(5):
@@ -163,7 +164,7 @@ def test_sym_printed_kernel_pairing_fails():
 
 @pytest.mark.parametrize("nodd", [1, 3, 65, 801, 4097])
 def test_sym_adversarial_extremes_at_bound(nodd):
-    """All samples at +-S_q, +-K_q with odd low bits, at the largest Q the c5
+    """All samples at +-S_q, +-K_q with odd low bits, at the largest Q the exactness
     bound admits: still exact.  At Q+1 the bound must reject."""
     Q = O.qmax_direct(SYM, nodd)
     assert O.exact_ok(SYM, nodd, Q, Q) and not O.exact_ok(SYM, nodd, Q + 1, Q + 1)
@@ -184,7 +185,7 @@ def test_sym_adversarial_extremes_at_bound(nodd):
 
 
 def test_sym_bound_is_needed():
-    """Beyond the c5 bound the FP64 packed convolution loses low digits."""
+    """Beyond the exactness bound the FP64 packed convolution loses low digits."""
     nodd = 65
     Q = O.qmax_direct(SYM, nodd) * 6
     sq, kq = np.full(2048, Q), np.full(nodd, Q)
@@ -282,7 +283,7 @@ def test_asym_pack_unpack_reconstructs_integer_conv(M, nodd, n):
 
 
 def test_exactness_bound_closed_forms():
-    """Reading c5: asym2 admits R_max up to 2^26 - 1, symmetric and asym3 up to
+    """Exactness bounds with eps = 2^-b: asym2 admits R_max up to 2^26 - 1, symmetric and asym3 up to
     2^17 - 1 (b = 18); the exact integer conditions reproduce those limits."""
     assert O.qmax_direct(ASYM2, 1) == 8191           # 8191^2 = 67,092,481 < 2^26
     assert O.exact_ok(ASYM2, 1, 8191, 8192)          # R_max = 2^26 - 8191
@@ -480,11 +481,11 @@ def test_selected_blocks_meet_the_target(core):
     assert packed > 200 and below_without_margin > 0
 
 
-# ------------------------------------------------------------ FFT core (reading c7)
+# ------------------------------------------------------------ FFT core error bound (Higham, Thm 24.2)
 @pytest.mark.parametrize("blk,nodd,wb", [(SYM, 65, 1024), (ASYM2, 65, 1024), (ASYM2, 257, 2048),
                                           (ASYM3, 65, 1024), (SYM, 33, 512)])
 def test_fft_core_error_within_bound(blk, nodd, wb):
-    """An FP64 FFT block convolution (textbook radix-2) stays within the c7
+    """An FP64 FFT block convolution (textbook radix-2) stays within the
     error bound, so rounding recovers the exact packed integers."""
     g = np.random.default_rng(nodd + wb)
     Q = O.qmax_fft(blk, nodd, wb)
@@ -519,7 +520,7 @@ def test_fft_core_error_within_bound(blk, nodd, wb):
     hi = n if blk == SYM else len(sbar) + nodd - 1 - 0
     hi = min(hi, n)
     err = np.max(np.abs(viafft[lo:hi] - exact[lo:hi])) * scale
-    assert err < bound                       # the c7 bound holds
+    assert err < bound                       # the error bound holds
     assert err < 0.01                        # and has a wide margin in practice
     if bound < 0.25:                         # then rounding recovers the exact packed integers
         np.testing.assert_array_equal(np.rint(viafft[lo:hi] * scale), exact[lo:hi] * scale)
