@@ -131,7 +131,7 @@ class Server:
             op = apx.OP_XCORR if q.xcorr else apx.OP_CONV
             Wb, core = self.choice(q.N, op, q.target)
             q.W_block, q.mode = Wb, op | core | apx.PACK_AUTO
-            reqs[j] = (sb + 4 * q.s_off, q.L, kb + krow * q.k_id, q.N, ob + 4 * off, Wb, q.mode, q.target, 0, 0)
+            reqs[j] = (sb + 4 * q.s_off, q.L, kb + krow * q.k_id, q.N, ob + 4 * off, Wb, q.mode, q.target, 0, 0, 0, 0)
             q.out = out[off:off + lens[j]]
             off += lens[j]
         self.ctxs[si].apx_conv_batch_host(reqs, stream=st)
