@@ -345,7 +345,7 @@ void apx_kernel_destroy(apx_kernel* kp);
  * device's memory pool.  It takes no context and calls no cudaMalloc, cudaFree
  * or other allocating routine: all of its scratch (twiddle tables, kernel
  * spectra, kernel statistics, claim, ready and ticket words) lives in one fixed device array of
- * about 490 KB that every GPU loading the library keeps until the process
+ * about 550 KB that every GPU loading the library keeps until the process
  * exits.
  *   s_in, k, r_out : device pointers as for apx_conv (L, N and L+N-1 floats)
  *   mode           : op | APX_CORE_FFT | pack bits (APX_PACK_AUTO uses

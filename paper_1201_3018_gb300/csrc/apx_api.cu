@@ -51,6 +51,10 @@ bool use_fused(const Params& p, cudaStream_t st) {
         (void)cudaGetLastError();
         return false;
     }
+    // A call that needs full precision only runs the two-CTA block kernel, whose
+    // launch follows the two preparation launches as their programmatic
+    // dependent (measured faster than the one-launch form with the one-CTA kernel).
+    if (fft_full_only(p)) return false;
     return cs == cudaStreamCaptureStatusNone && p.fft && p.P >= kFuseMinBlocks &&
            prep_jobs_count(p.Wb, fft_threads(p.Wb)) <= kMaxJobs;
 }
@@ -60,7 +64,7 @@ struct apx_ctx {
     size_t budget = 0;
     size_t in_use = 0;
     int64_t launches = 0;
-    DevBuf flags, ki, Hfull, Ysub, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
+    DevBuf flags, ki, Hfull, Ysub, Hpair, Hc[kMaxCand], tw64, tw32, hs, hk, hr;
     DevBuf barena, bparams, btab;       // batched calls: per-request workspace, parameters, CTA tables
     DevBuf tc_seg, tc_b, tc_cs, tc_inv;  // filterbank: block segments, Toeplitz B, c_s per block, 1/(c_s c_k) per block and kernel
     DevBuf bhost;                       // batched calls from host buffers: device copies of inputs and outputs
@@ -525,6 +529,11 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
     set_flag_ptrs(p, (unsigned*)ctx->flags.p);
     p.fused = use_fused(p, stream);
+    if (pl.fft && !p.fused && fft_full_only(p)) {  // the two-CTA block kernel: its staging-order spectrum
+        rc = ensure(ctx, ctx->Hpair, pair_table_bytes(Wb));
+        if (rc) return rc;
+        p.Hpair = (float2*)ctx->Hpair.p;
+    }
     p.ticket_base = ctx->tickets;
     p.Hfull = (float2*)ctx->Hfull.p;
     p.ki = (KInfo*)ctx->ki.p;
@@ -807,7 +816,7 @@ void apx_destroy(apx_ctx* c) {
     {
         DeviceGuard dg(c->device);
         cudaDeviceSynchronize();
-        DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
+        DevBuf* all[] = {&c->flags, &c->ki, &c->Hfull, &c->Ysub, &c->Hpair, &c->Hc[0], &c->Hc[1], &c->Hc[2], &c->tw64,
                          &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab,
                          &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_inv, &c->bhost};
         for (DevBuf* b : all) release(c, *b);
@@ -1193,7 +1202,8 @@ extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_
     const size_t off_taps = 256, off_ki = off_taps + al256b(sizeof(float) * (size_t)N);
     const size_t off_h = off_ki + al256b(sizeof(KInfo)), off_y = off_h + al256b(sizeof(float2) * (m1 + 1));
     const size_t off_c = off_y + al256b(sizeof(float2) * (size_t)W_block);
-    const size_t bytes = off_c + (size_t)p.ncand * al256b(sizeof(double2) * m1);
+    const size_t off_pair = off_c + (size_t)p.ncand * al256b(sizeof(double2) * m1);
+    const size_t bytes = off_pair + al256b(pair_table_bytes(W_block));
     apx_kernel* kp = new apx_kernel();
     kp->device = ctx->device;
     kp->N = N;
@@ -1217,6 +1227,7 @@ extern "C" int apx_kernel_create(apx_ctx* ctx, const float* k, int32_t N, int32_
     p.Hfull = (float2*)(a + off_h);
     p.Ysub = (float2*)(a + off_y);
     for (int j = 0; j < p.ncand; ++j) p.cand[j].H = (double2*)(a + off_c + (size_t)j * al256b(sizeof(double2) * m1));
+    p.Hpair = W_block >= 1024 ? (float2*)(a + off_pair) : nullptr;  // for calls that run the two-CTA kernel
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
     p.ntab = ctx->tw_wb;
@@ -1281,6 +1292,7 @@ extern "C" int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float
     p.ki = q.ki;
     p.Hfull = q.Hfull;
     p.Ysub = q.Ysub;
+    p.Hpair = q.Hpair;
     p.tw64 = (const double2*)ctx->tw64.p;
     p.tw32 = (const float2*)ctx->tw32.p;
     p.ntab = ctx->tw_wb;
@@ -1394,7 +1406,8 @@ constexpr size_t kSOffTw32 = kSOffYsub + al256(sizeof(float2) * kStaticWbMax);
 constexpr size_t kSOffTw64 = kSOffTw32 + al256(sizeof(float2) * kStaticWbMax);
 constexpr size_t kSOffHc = kSOffTw64 + al256(sizeof(double2) * kStaticWbMax);
 constexpr size_t kSHcBytes = al256(sizeof(double2) * (kStaticWbMax / 2 + 1));
-constexpr size_t kStaticBytes = kSOffHc + kMaxCand * kSHcBytes;  // about 490 KB
+constexpr size_t kSOffHpair = kSOffHc + kMaxCand * kSHcBytes;
+constexpr size_t kStaticBytes = kSOffHpair + al256(sizeof(float2) * 30 * (kStaticWbMax / 32));  // about 550 KB
 
 }  // namespace
 
@@ -1500,6 +1513,7 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
     const size_t smem = fft_smem_bytes(p);
     if (smem > (size_t)kMaxSmem) return APX_ERR_WBLOCK;
     p.fused = use_fused(p, st);
+    if (!p.fused && fft_full_only(p)) p.Hpair = (float2*)(base + kSOffHpair);
     if (p.fused) {
         std::lock_guard<std::mutex> lk(g_static_mu);
         p.ticket_base = g_static[dev].tickets;

@@ -56,7 +56,7 @@ struct Shared {
     float redf[32];
     int redi[32];
     long long redl[32];
-    double bcast[4];
+    double bcast[3];
 };
 
 // Tap n of the convolution kernel: reversed for cross-correlation

@@ -331,6 +331,11 @@ static cudaError_t fft_attrs() {
     return e;
 }
 
+// A call with no packing candidate and no per-block records, at W_block >= 1024,
+// can run the two-CTA full-precision kernel (apx_fft_pair.cu) when it is not a
+// one-launch call.
+bool fft_full_only(const Params& p) { return p.ncand == 0 && !p.st && p.Wb >= 1024; }
+
 // pdl: the programmatic dependent of the preparation launches just before it;
 // false when the kernel's preparation is already resident (a prepared kernel).
 cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st, bool pdl) {
@@ -338,6 +343,7 @@ cudaError_t launch_fft(const Params& p, size_t smem, cudaStream_t st, bool pdl) 
     cudaError_t e = fft_attrs<false>();
     if (e != cudaSuccess) return e;
     const BatchTab none = {nullptr, nullptr, 0};
+    if (fft_full_only(p) && p.Hpair) return launch_fft_pair(p, st, pdl);
     if (p.Wb / fft_threads(p.Wb) > 16)
         return launch_k(k_fft<32, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, pdl, p, none);
     return launch_k(k_fft<16, false>, dim3((unsigned)p.P), dim3(fft_threads(p.Wb)), smem, st, pdl, p, none);

@@ -71,6 +71,8 @@ struct Params {
     apx_block_stats* st;  // per-block stats or null
     float2* Hfull;        // FFT core: FP32 spectrum FFT_n(k) / (4m), m+1 entries
     float2* Ysub;         // FFT core: spectra of the R1 decimated tap sequences (n entries)
+    float2* Hpair;        // FFT core, two-CTA kernel: H and the real-step twiddles in the order its
+                          // CTAs stage them (2 x 15 x W_block/32 entries), or null
     KInfo* ki;            // FFT core: kernel statistics from the spectrum launch
     const double2* tw64;  // twiddles exp(-2 pi i t / ntab), t in [0, ntab)
     const float2* tw32;
@@ -92,6 +94,30 @@ struct Params {
     Cand cand[kMaxCand];
     DirectLayout dl;      // direct core
 };
+
+// Two-CTA form of the FP32 block kernel (apx_fft_pair.cu): with radix-8
+// passes the first forward pass sends output digit r to the class of slots
+// [r S, r S + S), S = m/8; CTA 0 holds classes {0, 1, 4, 7}, CTA 1 classes
+// {2, 3, 5, 6} (each set closed under r -> -r mod 8, so frequencies k and m-k
+// meet in one CTA).  pair_owner(r): the CTA holding class r; pair_local(r):
+// its position among that CTA's four classes.
+constexpr unsigned kPairMask1 = 0x6Cu;
+__host__ __device__ __forceinline__ int pair_owner(int r) { return (int)((kPairMask1 >> r) & 1u); }
+__host__ __device__ __forceinline__ int pair_local(int r) {
+    const unsigned mine = pair_owner(r) ? kPairMask1 : (~kPairMask1 & 0xFFu);
+    unsigned below = mine & ((1u << r) - 1u), c = 0;
+    while (below) { c += below & 1u; below >>= 1; }
+    return (int)c;
+}
+// Entry of the pair-ordered spectrum table for frequency k <= m/2: CTA `rank`,
+// thread t, item u (k = 8 t + c_u, or u = 4 for k = m/2 in CTA 0, thread 0).
+// Item u of thread t holds H[k], H[m-k], W^k at (3u + a) nt + t, a = 0, 1, 2,
+// after rank * 15 nt; nt = m/16 threads per CTA.
+__host__ __device__ __forceinline__ void pair_entry(int k, int m, int* rank, int* u, int* t) {
+    if (k == m / 2) { *rank = 0; *u = 4; *t = 0; return; }
+    const int c = k & 7;
+    *rank = pair_owner(c); *u = pair_local(c); *t = k >> 3;
+}
 
 // Several requests in one launch: request r owns CTAs [cta_start[r], cta_start[r+1]).
 struct BatchTab {
@@ -216,10 +242,19 @@ template <typename R> struct cpx;
 template <> struct cpx<float> { using T = float2; };
 template <> struct cpx<double> { using T = double2; };
 
+// Products are written out (one fused multiply-add and one rounded product per
+// component, rounded products elsewhere): the device compiler would otherwise
+// fuse multiplies into later additions as its schedule allows, and the block
+// kernels (general, full-precision-only, two-CTA, batched) could then differ
+// in the last bit.  Written this way every kernel performs the same operations.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     C r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
+    r.x = rfma(a.x, b.x, -rmul(a.y, b.y));
+    r.y = rfma(a.x, b.y, rmul(a.y, b.x));
     return r;
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
@@ -235,16 +270,16 @@ template <typename C, bool INV> __device__ __forceinline__ C mul_w8(C a) {  // e
     using R = decltype(a.x);
     const R h = (R)0.70710678118654752440;
     C r;
-    if (INV) { r.x = (a.x - a.y) * h; r.y = (a.x + a.y) * h; }
-    else     { r.x = (a.x + a.y) * h; r.y = (a.y - a.x) * h; }
+    if (INV) { r.x = rmul(a.x - a.y, h); r.y = rmul(a.x + a.y, h); }
+    else     { r.x = rmul(a.x + a.y, h); r.y = rmul(a.y - a.x, h); }
     return r;
 }
 template <typename C, bool INV> __device__ __forceinline__ C mul_w83(C a) {  // exp(-+ 3 i pi/4)
     using R = decltype(a.x);
     const R h = (R)0.70710678118654752440;
     C r;
-    if (INV) { r.x = (-a.x - a.y) * h; r.y = (a.x - a.y) * h; }
-    else     { r.x = (a.y - a.x) * h; r.y = (-a.x - a.y) * h; }
+    if (INV) { r.x = rmul(-a.x - a.y, h); r.y = rmul(a.x - a.y, h); }
+    else     { r.x = rmul(a.y - a.x, h); r.y = rmul(-a.x - a.y, h); }
     return r;
 }
 
@@ -285,8 +320,8 @@ template <typename C, bool INV> __device__ __forceinline__ C mul_w16(C a, int e)
     }
     if (INV) wi = -wi;
     C r;
-    r.x = a.x * wr - a.y * wi;
-    r.y = a.x * wi + a.y * wr;
+    r.x = rfma(a.x, wr, -rmul(a.y, wi));
+    r.y = rfma(a.x, wi, rmul(a.y, wr));
     return r;
 }
 // DFT16 as 4 x 4: X[b + 4d] = sum_a W4^(ad) W16^(ab) sum_c x[a + 4c] W4^(cb)
@@ -330,11 +365,13 @@ template <typename C, int RAD, bool INV>
 __device__ __forceinline__ void twiddles(C (&w)[RAD], const C* __restrict__ tw, int step) {
     using R = decltype(w[0].x);
     w[0].x = (R)1; w[0].y = (R)0;
+    // plain loads: the table is in global memory or, for the FP32 passes of
+    // some kernels, a copy of the bases in shared memory
     if constexpr (sizeof(R) == 8) {
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) w[r] = __ldg(&tw[r * step]);
+        for (int r = 1; r < RAD; ++r) w[r] = tw[r * step];
     } else {
-        if constexpr (RAD > 1) w[1] = __ldg(&tw[step]);
+        if constexpr (RAD > 1) w[1] = tw[step];
         if constexpr (RAD > 2) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[2], w[1]); }
         if constexpr (RAD > 4) {
             w[4] = cmul(w[2], w[2]);
@@ -357,9 +394,18 @@ __device__ __forceinline__ void twiddles(C (&w)[RAD], const C* __restrict__ tw, 
 // of 16, 8, 4 that still gives every thread a butterfly; FP64 transforms
 // always use radix 4 (their time is set by the FP64 rate, and the small
 // butterfly keeps the register count low).
+// Largest radix of the FP32 passes.  8: every block kernel (the general one,
+// the full-precision-only one at twice the threads, the two-CTA form) then
+// takes the same radix at each length, so they give the same bits; radix-16
+// butterflies measured no faster (the kernels wait on instruction fetch and
+// latency, and the smaller butterfly keeps their code and registers small).
+#ifndef APX_FFT_RMAX
+#define APX_FFT_RMAX 8
+#endif
 template <typename C>
 __host__ __device__ constexpr int fft_radix(int m, int nt) {
-    return sizeof(C) == 16 ? 4 : (m >= 16 * nt ? 16 : (m >= 8 * nt ? 8 : 4));
+    return sizeof(C) == 16 ? 4
+                           : ((APX_FFT_RMAX >= 16 && m >= 16 * nt) ? 16 : ((APX_FFT_RMAX >= 8 && m >= 8 * nt) ? 8 : 4));
 }
 
 // One in-place pass over sub-transforms of length M with radix RAD (stride

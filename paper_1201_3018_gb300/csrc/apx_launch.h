@@ -63,5 +63,11 @@ cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas,
 cudaError_t launch_spec_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st, bool pdl);
 cudaError_t launch_combine_batch(const Params& any, const BatchTab& bt, int ctas, cudaStream_t st);
 cudaError_t launch_fft_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st);
+bool fft_full_only(const Params& p);
+// Full precision only, outside a fused launch: one block per cluster of two CTAs.
+cudaError_t launch_fft_pair(const Params& p, cudaStream_t st, bool pdl);
+// bytes of its staging-order spectrum table (2 CTAs x 15 entries x W_block/32 threads)
+inline size_t pair_table_bytes(int Wb) { return sizeof(float2) * 30 * (size_t)(Wb / 32); }
+size_t fft_pair_smem_bytes(int Wb);
 
 }  // namespace apx

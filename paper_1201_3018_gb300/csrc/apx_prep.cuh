@@ -54,7 +54,21 @@ __device__ inline void spec_combine(const Params& p, int k) {
         }
     }
     const float scale = 1.f / (float)(4 * m);
-    p.Hfull[k] = make_float2(acc.x * scale, acc.y * scale);
+    const float2 h = make_float2(acc.x * scale, acc.y * scale);
+    p.Hfull[k] = h;
+    if (p.Hpair) {
+        // the same values in the two-CTA kernel's staging order: H[k] (a = 0) and
+        // W^k (a = 2) under frequency k <= m/2, H[m-k] (a = 1) under m - k
+        const int nt = m / 16, kk = k <= m / 2 ? k : m - k;
+        int rank, u, t;
+        pair_entry(kk, m, &rank, &u, &t);
+        float2* e = p.Hpair + rank * 15 * nt + 3 * u * nt + t;
+        if (k <= m / 2) {
+            e[0] = h;
+            e[2 * nt] = p.tw32[k * (p.ntab / n)];
+        }
+        if (k >= m / 2) e[nt] = h;
+    }
 }
 
 // Kernel statistics and candidate norms into *p.ki (the whole CTA).

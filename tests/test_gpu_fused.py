@@ -40,6 +40,15 @@ def _length_for_blocks(P, N, Wb, mode):
     return lo
 
 
+def _launches(L, N, Wb, mode, snr, P):
+    """Launches of a single call: one when it runs its kernel preparation in
+    the block kernel's own launch (at least FUSE_MIN_BLOCKS blocks and some
+    packing candidate left), else three; a call without any candidate runs the
+    two-CTA full-precision kernel after the two preparation launches."""
+    full_only = Wb >= 1024 and not apx.plan_candidates(L, N, Wb, mode, snr)
+    return 3 if (full_only or P < FUSE_MIN_BLOCKS) else 1
+
+
 def _single(ctx, s, k, Wb, mode, snr):
     r = torch.empty(s.numel() + k.numel() - 1, device="cuda")
     n0 = ctx.launch_count()
@@ -77,7 +86,7 @@ def test_one_launch_equals_three_launch_form(ctx, P, N, Wb, bits, snr):
     s = _dev(wl.random_signal(wl.SEED_BASE + 900 + P, L, "laplace", 0.1))
     k = _dev(wl.random_signal(wl.SEED_BASE + 950 + N, N, "uniform"))
     got, launches = _single(ctx, s, k, Wb, mode, snr)
-    assert launches == (1 if P >= FUSE_MIN_BLOCKS else 3)
+    assert launches == _launches(L, N, Wb, mode, snr, P)
     ref = _batch_of_one(ctx, s, k, Wb, mode, snr)
     assert np.array_equal(got, ref)
     # and sampled outputs against Eq. (1) in FP64 (full precision blocks within FP32 rounding;
@@ -93,21 +102,24 @@ def test_one_launch_equals_three_launch_form(ctx, P, N, Wb, bits, snr):
 
 
 def test_tickets_stay_in_step_across_interleaved_calls(ctx):
-    """One-launch calls between three-launch calls, batched calls and calls of
-    another W_block: every repeat gives the first result's bits."""
-    N, Wb, mode = 4096, 8192, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO
+    """One-launch calls between three-launch calls (the two-CTA kernel among
+    them), batched calls and one-launch calls of another W_block: every repeat
+    gives the first result's bits."""
+    N, Wb, mode, snr = 1024, 4096, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_AUTO, 30.0
+    assert apx.plan_candidates(1 << 20, N, Wb, mode, snr) and apx.plan_candidates(1 << 20, N, 8192, mode, snr)
     L = _length_for_blocks(150, N, Wb, mode)
     s = _dev(wl.random_signal(wl.SEED_BASE + 990, L, "laplace", 0.1))
     k = _dev(wl.random_signal(wl.SEED_BASE + 991, N, "uniform"))
     small_s = _dev(wl.random_signal(wl.SEED_BASE + 992, 20000, "laplace", 0.1))
     small_k = _dev(wl.random_signal(wl.SEED_BASE + 993, 300, "uniform"))
-    first, n = _single(ctx, s, k, Wb, mode, 45.0)
+    first, n = _single(ctx, s, k, Wb, mode, snr)
     assert n == 1
     for rep in range(4):
         _single(ctx, small_s, small_k, 2048, apx.OP_CONV | apx.CORE_FFT | apx.PACK_AUTO, 30.0)
         _batch_of_one(ctx, small_s, small_k, 4096, apx.OP_CONV | apx.CORE_FFT | apx.PACK_NONE, 0.0)
-        _single(ctx, s, k, 16384, mode, 45.0)  # another W_block, also one launch
-        again, n = _single(ctx, s, k, Wb, mode, 45.0)
+        _single(ctx, s, k, 4096, apx.OP_XCORR | apx.CORE_FFT | apx.PACK_NONE, 0.0)  # the two-CTA kernel
+        _single(ctx, s, k, 8192, mode, snr)  # another W_block, also one launch
+        again, n = _single(ctx, s, k, Wb, mode, snr)
         assert n == 1
         assert np.array_equal(again, first), rep
 
@@ -138,7 +150,7 @@ def test_captured_call_replays(ctx):
         torch.cuda.synchronize()
         got = r.cpu().numpy()
         want, n = _single(ctx, s, k, Wb, mode, 45.0)
-        assert n == 1
+        assert n == _launches(L, N, Wb, mode, 45.0, 150)
         assert np.array_equal(got, want), rep
 
 
