@@ -426,8 +426,9 @@ __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict
     const int tstep = ntab / M;
     const bool lin = (S & 255) == 0 || (M <= 256 && ((S & 15) == 0 || M <= 16));
     const int pstride = S + ((S & 15) == 0 ? S >> 4 : 0) + ((S & 255) == 0 ? S >> 8 : 0);
+    const int lS = 31 - __clz(S);  // S is a power of two: sub-transform and offset by shift and mask
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-        const int g = b / S, j = b - g * S;
+        const int g = b >> lS, j = b & (S - 1);
         const int base = g * M + j;
         C v[RAD], w[RAD];
         if (!APX_IN_BOUNDS(base + (RAD - 1) * S < m, st)) continue;
