@@ -549,6 +549,41 @@ def bench_serving(tuner, dev, seconds):
         srv.close()
 
 
+def bench_serving_persistent(tuner, dev, seconds):
+    """The same trace on the persistent serving kernel (apx_server): requests
+    submitted one by one through the mapped queue as they arrive, templates
+    resident between requests that share them, kernels longer than 4093 taps
+    through the host-batched path beside it."""
+    from paper_1201_3018_gb300 import serve
+    seed = wl.SEED_BASE + 5
+    s_host, k_host = serve.host_pools(seed)
+    srv = serve.PersistentServer(dev.index or 0, budget_bytes=40 << 30, tuner=tuner, slots=1024, templates=256,
+                                 out_floats=256 << 20)
+    try:
+        warm = serve.make_trace(seed + 100, duration_s=0.25)
+        srv.run(warm, s_host, k_host, realtime=False)
+        trace = serve.make_trace(seed, duration_s=seconds)
+        srv.max_overlap = srv.submitted = 0
+        n_fb0 = srv.fallback.batches
+        done = srv.run(trace, s_host, k_host, realtime=True)
+        p50, p99 = serve.latency_ms(done)
+        span = max(q.done for q in done) - min(q.arrival for q in done)
+        outs = sum(q.L + q.N - 1 for q in done)
+        return {"workload": "serving (persistent kernel): the same Poisson 2000 req/s trace for %.1f s" % seconds,
+                "requests": len(done), "p50_ms": p50, "p99_ms": p99, "value": outs / span / 1e9, "unit": UNIT,
+                "engine_requests": srv.submitted, "batched_path_requests": srv.fallback.batches - n_fb0,
+                "max_requests_in_flight": srv.max_overlap, "kernel_launches": srv.srv.launch_count(),
+                "errors": sum(1 for q in done if q.status),
+                "by_path": {path: dict(zip(("p50_ms", "p99_ms"), serve.latency_ms([q for q in done if q.path == path])))
+                            for path in ("engine", "batched") if any(q.path == path for q in done)},
+                "engine_p99_by_size": {lab: serve.latency_ms(sel)[1] for lab, sel in (
+                    ("L<2^18", [q for q in done if q.path == "engine" and q.L < (1 << 18)]),
+                    ("L>=2^18", [q for q in done if q.path == "engine" and q.L >= (1 << 18)])) if sel},
+                "latency": "arrival to result in pinned host memory (inputs read and results written in place)"}
+    finally:
+        srv.close()
+
+
 # ---------------------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -688,6 +723,7 @@ def main():
             extras["paper_comparison"] = bench_paper_comparison(ctx, dev, flush, stream)
         if "serving" in want:
             extras["serving"] = bench_serving(tuner, dev, args.serve_seconds)
+            extras["serving"]["persistent"] = bench_serving_persistent(tuner, dev, args.serve_seconds)
 
     if rank != 0:
         ctx.close()

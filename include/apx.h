@@ -337,6 +337,59 @@ int apx_conv_prepared(apx_ctx* ctx, const apx_kernel* kp, const float* s_in, int
                       float* r_out, int32_t* rq_out, apx_block_stats* stats, void* stream);
 void apx_kernel_destroy(apx_kernel* kp);
 
+/* ---- serving engine (persistent kernel) ------------------------------------
+ * Section IV.D adapts each block to a per-block SNR minimum; a server that
+ * receives such requests continuously keeps one persistent kernel on the GPU
+ * instead of launching per request.  Requests are appended to a queue in
+ * page-locked, device-mapped memory; the kernel's CTAs claim their work items
+ * (a template's preparation jobs, then the request's overlap-save blocks) in
+ * order and signal each request's completion through a host-mapped word.
+ * Templates (kernel buffer, N, W_block, op and packing bits) stay resident:
+ * the first request with a template prepares its statistics and spectra, and
+ * later requests with the same template only run their blocks, until the
+ * template's entry is taken for another one (least recently used first).
+ *
+ * apx_server_create: slots = requests in flight at most, templates = resident
+ * entries (about 300 KB of device memory each, outside the context budget),
+ * ctas = persistent CTAs (0: two per SM), idle_ms = how long a CTA waits for
+ * work before it leaves (the next submit relaunches the kernel).  The context
+ * provides the device and must outlive the server; the server runs on a
+ * stream of its own.  Errors: APX_ERR_ARG, APX_ERR_OOM, APX_ERR_CUDA.
+ *
+ * apx_server_submit: one request (apx_request; FFT core or APX_CORE_AUTO,
+ * APX_PACK_AUTO or APX_PACK_NONE, W_block <= 8192 or 0 for the default;
+ * rq_out and stats NULL).  s_in, k and r_out are device pointers or
+ * page-locked host buffers (read and written in place); the kernel buffer is
+ * the template's identity, so its contents must not change while it is
+ * resident.  Writes the request's sequence number (never 0).  Errors:
+ * APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_BUDGET (every slot or template entry is
+ * in use: poll and retry), APX_ERR_CUDA.
+ *
+ * apx_server_poll: 1 when request seq is complete (its outputs are then
+ * visible to the host; *status receives APX_OK, APX_ERR_NONFINITE, or
+ * APX_ERR_TIMEOUT when a block gave up waiting for its template's preparation,
+ * its outputs NaN), 0 while it is in flight; a request is reported complete
+ * once.  Errors: APX_ERR_ARG (unknown sequence number), APX_ERR_CUDA.
+ *
+ * apx_server_destroy: asks the CTAs to leave, waits for the kernel, frees the
+ * server (requests still in flight complete first).  NULL is a no-op.
+ *
+ * apx_server_test_stall_next (no counterpart in the paper; a failure-path
+ * test hook): the next submitted request prepares its template afresh but
+ * drops the preparation jobs, so each of its blocks waits in its bounded spin,
+ * gives up after about a second and writes NaN; the request completes with
+ * APX_ERR_TIMEOUT and the template is prepared anew by the next request.
+ * Nothing faults or hangs.  apx_server_launch_count: persistent-kernel
+ * launches so far. */
+typedef struct apx_server apx_server;
+int apx_server_create(apx_ctx* ctx, int32_t slots, int32_t templates, int32_t ctas, double idle_ms,
+                      apx_server** out);
+int apx_server_submit(apx_server* srv, const apx_request* req, int64_t* seq);
+int apx_server_poll(apx_server* srv, int64_t seq, int32_t* status);
+void apx_server_destroy(apx_server* srv);
+int apx_server_test_stall_next(apx_server* srv);
+int64_t apx_server_launch_count(const apx_server* srv);
+
 /* ---- allocation-free FFT core ---------------------------------------------
  * The paper has no counterpart: this is a deployment variant of apx_conv with
  * the FFT core for callers that may not allocate device memory once they are

@@ -78,6 +78,12 @@ SIGNATURES = {
     "apx_test_skew_tickets": (C.c_int, [_vp, _i64]),
     "apx_filterbank": (C.c_int, [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp, _vp]),
     "apx_filterbank_blocks": (C.c_int, [_i64, _i32, _i32, _i32, _i32, C.POINTER(_i32), C.POINTER(_i64)]),
+    "apx_server_create": (C.c_int, [_vp, _i32, _i32, _i32, _d, C.POINTER(C.c_void_p)]),
+    "apx_server_submit": (C.c_int, [_vp, _vp, C.POINTER(_i64)]),
+    "apx_server_poll": (C.c_int, [_vp, _i64, C.POINTER(_i32)]),
+    "apx_server_destroy": (None, [_vp]),
+    "apx_server_test_stall_next": (C.c_int, [_vp]),
+    "apx_server_launch_count": (_i64, [_vp]),
 }
 PHASES = ("direct", "spectra", "fft", "tc_prep", "tc_mma")
 
@@ -229,6 +235,60 @@ def apx_conv_fft_static(s, k, W_block, mode, snr_db, r, stream=None):
     _check_call(s, k, r, torch.cuda.current_device())  # the entry point's scratch belongs to the current device
     return _check("apx_conv_fft_static", lib().apx_conv_fft_static(_ptr(s), s.numel(), _ptr(k), k.numel(), W_block,
                                                                    mode, float(snr_db), _ptr(r), _stream(stream)))
+
+
+class Server:
+    """apx_server: the persistent serving kernel on a context's device.
+    submit() enqueues one request and returns its sequence number (None when
+    every slot or template entry is in use); poll(seq) returns None while the
+    request is in flight, else its status code (APX_OK, ...)."""
+
+    def __init__(self, ctx, slots: int = 256, templates: int = 64, ctas: int = 0, idle_ms: float = 20.0):
+        h = C.c_void_p()
+        _check("apx_server_create", lib().apx_server_create(ctx._h, slots, templates, ctas, float(idle_ms),
+                                                             C.byref(h)))
+        self._h = h
+        self._ctx = ctx  # the context must outlive the server
+        self._req = Request()
+        self._seq = _i64()
+        self._st = _i32()
+
+    def submit(self, s_ptr, L, k_ptr, N, r_ptr, W_block, mode, snr_db):
+        """Pointers are device addresses or page-locked host addresses (ints)."""
+        q = self._req
+        q.s_in, q.L, q.k, q.N, q.r_out = s_ptr, L, k_ptr, N, r_ptr
+        q.W_block, q.mode, q.snr_target_db = W_block, mode, float(snr_db)
+        q.S_q = q.K_q = 0
+        q.rq_out = q.stats = None
+        rc = lib().apx_server_submit(self._h, C.byref(q), C.byref(self._seq))
+        if rc == APX_ERR_BUDGET:
+            return None
+        _check("apx_server_submit", rc)
+        return self._seq.value
+
+    def poll(self, seq):
+        rc = lib().apx_server_poll(self._h, seq, C.byref(self._st))
+        if rc < 0:
+            raise ApxError("apx_server_poll", rc)
+        return self._st.value if rc == 1 else None
+
+    def test_stall_next(self):
+        """Failure-path test hook (apx_server_test_stall_next)."""
+        return _check("apx_server_test_stall_next", lib().apx_server_test_stall_next(self._h))
+
+    def launch_count(self):
+        return lib().apx_server_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

@@ -9,10 +9,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "apx_launch.h"
+#include "apx_serve.h"
 #include "apx_tc.h"
 
 using namespace apx;
@@ -77,6 +80,8 @@ struct apx_ctx {
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     unsigned long long tickets = 0;  // CTA tickets handed out by fused launches (the device counter's value)
     int stall_next = 0;     // test hook: pre-claim the next call's packed spectra
+    std::vector<void*> retired;       // device buffers replaced by larger ones (freed with the context)
+    std::vector<void*> retired_host;  // page-locked staging buffers replaced likewise
     // tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev;          // event pool, pairs
@@ -92,13 +97,16 @@ int cuda_status(cudaError_t e) {
 }
 
 // Grow a workspace buffer to at least `bytes` (256-byte aligned by cudaMalloc).
+// The buffer it replaces is retired, not freed: cudaFree waits for the whole
+// device, which would stall this host thread behind every kernel in flight (a
+// running serving kernel among them); retired buffers are freed with the
+// context.
 int ensure(apx_ctx* c, DevBuf& b, size_t bytes) {
     if (b.bytes >= bytes) return APX_OK;
     size_t want = bytes < 256 ? 256 : bytes;
     if (c->in_use - b.bytes + want > c->budget) return APX_ERR_BUDGET;
     if (b.p) {
-        cudaError_t e = cudaFree(b.p);
-        if (e != cudaSuccess) return cuda_status(e);
+        c->retired.push_back(b.p);
         c->in_use -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
@@ -775,7 +783,7 @@ int stage_upload(apx_ctx* c, const void* src1, size_t n1, void* dst1, const void
         return APX_ERR_CUDA;
     }
     if (c->hstage_bytes < need) {
-        if (c->hstage) cudaFreeHost(c->hstage);
+        if (c->hstage) c->retired_host.push_back(c->hstage);  // freed with the context (cudaFreeHost waits for the device)
         c->hstage = nullptr;
         c->hstage_bytes = 0;
         if (cudaMallocHost(&c->hstage, need) != cudaSuccess) { c->hstage = nullptr; return APX_ERR_OOM; }
@@ -820,6 +828,8 @@ void apx_destroy(apx_ctx* c) {
                          &c->tw32, &c->hs, &c->hk, &c->hr, &c->barena, &c->bparams, &c->btab,
                          &c->tc_seg, &c->tc_b, &c->tc_cs, &c->tc_inv, &c->bhost};
         for (DevBuf* b : all) release(c, *b);
+        for (void* p : c->retired) cudaFree(p);
+        for (void* p : c->retired_host) cudaFreeHost(p);
         if (c->hstage) cudaFreeHost(c->hstage);
         if (c->hp_in) cudaStreamDestroy(c->hp_in);
         for (cudaEvent_t e : c->hp_ev) cudaEventDestroy(e);
@@ -1532,3 +1542,314 @@ extern "C" int apx_conv_fft_static(const float* s_in, int64_t L, const float* k,
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Serving engine: a persistent kernel fed through a ticket queue in mapped
+// memory (apx_serve.h).  Requests share templates: the kernel statistics,
+// spectrum and packed spectra of a (kernel buffer, N, W_block, op, packing)
+// are prepared by the first request that uses them and stay resident for the
+// following ones until the entry is reused for another template.
+namespace {
+
+constexpr int kServeTmapBits = 20;  // ticket -> slot map: 2^20 entries
+
+struct ServeTemplate {
+    const float* k = nullptr;
+    int N = 0, Wb = 0;
+    uint32_t key = 0;        // op | pack bits
+    unsigned epoch = 0;      // 0: free (or to be prepared anew)
+    int inflight = 0;        // requests using it
+    uint64_t last_use = 0;
+    unsigned char* base = nullptr;  // device: KInfo | Hfull | Ysub | Hc[3] | claim/ready | jobready
+};
+
+// Template entry layout at the largest W_block (every entry has the same size).
+struct TplLayout {
+    size_t ki, hfull, ysub, hc, flags, bytes;
+};
+TplLayout tpl_layout() {
+    const size_t m1 = (size_t)kServeWbMax / 2 + 1;
+    TplLayout t;
+    t.ki = 0;
+    t.hfull = t.ki + al256b(sizeof(KInfo));
+    t.ysub = t.hfull + al256b(sizeof(float2) * m1);
+    t.hc = t.ysub + al256b(sizeof(float2) * kServeWbMax);
+    t.flags = t.hc + kMaxCand * al256b(sizeof(double2) * m1);
+    t.bytes = t.flags + al256b(sizeof(unsigned) * (2 * kMaxCand + kMaxJobs));
+    return t;
+}
+
+}  // namespace
+
+struct apx_server {
+    apx_ctx* ctx = nullptr;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ran = nullptr;      // recorded after each launch of the persistent kernel
+    bool launched = false;
+    int nslots = 0, ctas = 0;
+    size_t smem = 0;
+    ServeEnv env{};                 // device-side view
+    ServeHdr* hdr = nullptr;        // host views of the mapped words
+    ServeSlot* slots = nullptr;
+    int* tmap = nullptr;
+    unsigned* done_seq = nullptr;
+    unsigned* fstatus = nullptr;
+    void* dmem = nullptr;           // device: ticket counter, per-slot counts and status, template arena
+    long long published = 0;
+    std::vector<int> free_slots;
+    std::vector<unsigned> slot_seq; // 0: free
+    std::vector<int> slot_tpl;
+    std::vector<ServeTemplate> tpl;
+    unsigned next_seq = 0, next_epoch = 0;
+    uint64_t clock = 0;
+    int stall_next = 0;
+    int64_t launches = 0;
+    void* tw = nullptr;             // its own twiddle tables (the context's may be regrown meanwhile)
+    std::unordered_map<unsigned, int> seq_slot;
+};
+
+extern "C" void apx_server_destroy(apx_server* s) {
+    if (!s) return;
+    {
+        DeviceGuard dg(s->device);
+        if (s->hdr) *reinterpret_cast<volatile int*>(&s->hdr->stop) = 1;  // the CTAs leave at their next claim
+        if (s->stream) cudaStreamSynchronize(s->stream);
+        if (s->ran) cudaEventDestroy(s->ran);
+        if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->hdr) cudaFreeHost(s->hdr);
+        if (s->dmem) cudaFree(s->dmem);
+        if (s->tw) cudaFree(s->tw);
+    }
+    delete s;
+}
+
+extern "C" int apx_server_create(apx_ctx* ctx, int32_t slots, int32_t templates, int32_t ctas, double idle_ms,
+                                 apx_server** out) {
+    if (!ctx || !out || slots < 1 || slots > 65536 || templates < 1 || templates > 4096 || ctas < 0 ||
+        !(idle_ms > 0.0) || idle_ms > 60000.0)
+        return APX_ERR_ARG;
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    apx_server* s = new apx_server();
+    s->ctx = ctx;
+    s->device = ctx->device;
+    s->nslots = slots;
+    int sms = 0, khz = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+    if (e != cudaSuccess) { delete s; return cuda_status(e); }
+    s->ctas = ctas > 0 ? ctas : 2 * sms;  // two CTAs per SM fit the block body's registers
+    s->smem = serve_smem_bytes();
+    // twiddle tables for every W_block up to the maximum, the engine's own copy
+    int rc = ensure_twiddles(ctx, kServeWbMax, nullptr);
+    if (rc) { delete s; return rc; }
+    const size_t ntw = (size_t)ctx->tw_wb;
+    e = cudaMalloc(&s->tw, (sizeof(double2) + sizeof(float2)) * ntw);
+    if (e == cudaSuccess) e = cudaMemcpy(s->tw, ctx->tw64.p, sizeof(double2) * ntw, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy((char*)s->tw + sizeof(double2) * ntw, ctx->tw32.p, sizeof(float2) * ntw, cudaMemcpyDeviceToDevice);
+    // mapped host words: header | slots | ticket map | completion words | final status
+    const size_t tsz = (size_t)1 << kServeTmapBits;
+    const size_t o_slots = 256, o_tmap = o_slots + al256b(sizeof(ServeSlot) * (size_t)slots);
+    const size_t o_seq = o_tmap + al256b(sizeof(int) * tsz), o_st = o_seq + al256b(sizeof(unsigned) * (size_t)slots);
+    const size_t hbytes = o_st + al256b(sizeof(unsigned) * (size_t)slots);
+    void* h = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc(&h, hbytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) { apx_server_destroy(s); return cuda_status(e); }
+    memset(h, 0, hbytes);
+    s->hdr = (ServeHdr*)h;
+    s->slots = (ServeSlot*)((char*)h + o_slots);
+    s->tmap = (int*)((char*)h + o_tmap);
+    s->done_seq = (unsigned*)((char*)h + o_seq);
+    s->fstatus = (unsigned*)((char*)h + o_st);
+    void* hd = nullptr;
+    e = cudaHostGetDevicePointer(&hd, h, 0);
+    // device words: ticket counter | finished items per slot | status per slot | template arena
+    const TplLayout tl = tpl_layout();
+    const size_t d_done = 256, d_st = d_done + al256b(sizeof(int) * (size_t)slots);
+    const size_t d_tpl = d_st + al256b(sizeof(unsigned) * (size_t)slots);
+    const size_t dbytes = d_tpl + tl.bytes * (size_t)templates;
+    if (e == cudaSuccess) e = cudaMalloc(&s->dmem, dbytes);
+    if (e == cudaSuccess) e = cudaMemset(s->dmem, 0, dbytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ran, cudaEventDisableTiming);
+    if (e != cudaSuccess) { apx_server_destroy(s); return cuda_status(e); }
+    unsigned char* d = (unsigned char*)s->dmem;
+    s->env.hdr = (ServeHdr*)hd;
+    s->env.slots = (ServeSlot*)((char*)hd + o_slots);
+    s->env.tmap = (int*)((char*)hd + o_tmap);
+    s->env.tmask = (long long)tsz - 1;
+    s->env.next = (unsigned long long*)d;
+    s->env.done_items = (int*)(d + d_done);
+    s->env.dstatus = (unsigned*)(d + d_st);
+    s->env.done_seq = (unsigned*)((char*)hd + o_seq);
+    s->env.fstatus = (unsigned*)((char*)hd + o_st);
+    s->env.idle_cycles = (long long)(idle_ms * (double)khz);
+    s->tpl.resize(templates);
+    for (int t = 0; t < templates; ++t) s->tpl[t].base = d + d_tpl + tl.bytes * (size_t)t;
+    s->slot_seq.assign(slots, 0u);
+    s->slot_tpl.assign(slots, -1);
+    for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    *out = s;
+    return APX_OK;
+}
+
+namespace {
+
+// (Re)launch the persistent kernel when tickets are published that no CTA will
+// claim: its CTAs leave after a bounded time without work, possibly just before
+// the host published more.
+int serve_ensure_running(apx_server* s) {
+    if (s->launched) {
+        const cudaError_t q = cudaEventQuery(s->ran);
+        if (q == cudaErrorNotReady) return APX_OK;  // still running: it will claim them
+        if (q != cudaSuccess) return cuda_status(q);
+        s->launched = false;
+    }
+    unsigned long long next = 0;  // the kernel has left: its counter is stable
+    cudaError_t e = cudaMemcpyAsync(&next, s->env.next, sizeof next, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if ((long long)next >= s->published) return APX_OK;
+    e = launch_serve(s->env, s->ctas, s->smem, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ran, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->launched = true;
+    s->launches += 1;
+    return APX_OK;
+}
+
+// A template entry for this request: the resident one with the same key, else
+// the least recently used entry that no request in flight uses (prepared anew).
+int serve_template(apx_server* s, const float* k, int N, int Wb, uint32_t key, bool fresh, bool* prepare) {
+    int best = -1;
+    for (int t = 0; t < (int)s->tpl.size(); ++t) {
+        const ServeTemplate& e = s->tpl[t];
+        if (!fresh && e.epoch && e.k == k && e.N == N && e.Wb == Wb && e.key == key) { *prepare = false; return t; }
+        if (e.inflight == 0 && (best < 0 || e.last_use < s->tpl[best].last_use)) best = t;
+    }
+    if (best < 0) return -1;
+    ServeTemplate& e = s->tpl[best];
+    e.k = k; e.N = N; e.Wb = Wb; e.key = key;
+    if (++s->next_epoch == 0) s->next_epoch = 1;  // words of earlier uses never equal a new epoch
+    e.epoch = s->next_epoch;
+    *prepare = true;
+    return best;
+}
+
+}  // namespace
+
+extern "C" int apx_server_submit(apx_server* s, const apx_request* q, int64_t* seq_out) {
+    if (!s || !q || !q->s_in || !q->k || !q->r_out || q->L < 1 || q->N < 1 || q->rq_out || q->stats) return APX_ERR_ARG;
+    const uint32_t core = q->mode & 0xF0u, pack = q->mode & 0xF00u;
+    if ((core != APX_CORE_FFT && core != APX_CORE_AUTO) || (pack != APX_PACK_AUTO && pack != APX_PACK_NONE) ||
+        (q->mode & ~0xFFFu))
+        return APX_ERR_ARG;
+    const int Nodd = q->N % 2 ? q->N : q->N + 1;
+    const int Wb = q->W_block > 0 ? q->W_block : default_wblock(Nodd);
+    if (Wb > kServeWbMax) return APX_ERR_WBLOCK;
+    const uint32_t mode = (q->mode & ~0xF0u) | APX_CORE_FFT;
+    DeviceGuard dg(s->device);
+    // page-locked host buffers are read and written in place
+    const float* sa = (const float*)host_alias(q->s_in);
+    const float* ka = (const float*)host_alias(q->k);
+    float* ra = (float*)host_alias(q->r_out);
+    Params p;
+    size_t smem = 0;
+    // every candidate: a template's norms and spectra are indexed by candidate position
+    int rc = make_params(sa ? sa : q->s_in, q->L, ka ? ka : q->k, q->N, Wb, mode, pack == APX_PACK_NONE ? 2 : 0,
+                         q->snr_target_db, 0, 0, ra ? ra : q->r_out, nullptr, nullptr, &p, &smem, false);
+    if (rc) return rc;
+    if (s->free_slots.empty()) return APX_ERR_BUDGET;
+    const int njobs = prep_jobs_count(Wb, kServeThreads);
+    const long long nblk = p.P;
+    bool prepare = false;
+    const bool stall = s->stall_next != 0;
+    const int ti = serve_template(s, q->k, q->N, Wb, mode & 0xF0Fu, stall, &prepare);
+    if (ti < 0) return APX_ERR_BUDGET;
+    const int nprep = prepare ? njobs : 0;
+    const long long nitems = nprep + nblk;
+    // the ticket map must not wrap onto a request still in flight
+    long long oldest = s->published;
+    for (int i = 0; i < s->nslots; ++i)
+        if (s->slot_seq[i] && s->slots[i].base < oldest) oldest = s->slots[i].base;
+    if (nitems > 0x7fffffffLL || s->published + nitems - oldest > (1LL << kServeTmapBits)) {
+        if (prepare) s->tpl[ti].epoch = 0;
+        return APX_ERR_BUDGET;
+    }
+    s->stall_next = 0;
+    ServeTemplate& tp = s->tpl[ti];
+    const TplLayout tl = tpl_layout();
+    unsigned* flags = (unsigned*)(tp.base + tl.flags);
+    p.ki = (KInfo*)(tp.base + tl.ki);
+    p.Hfull = (float2*)(tp.base + tl.hfull);
+    p.Ysub = (float2*)(tp.base + tl.ysub);
+    for (int j = 0; j < p.ncand; ++j) p.cand[j].H = (double2*)(tp.base + tl.hc + (size_t)j * al256b(sizeof(double2) * (kServeWbMax / 2 + 1)));
+    p.claim = flags;
+    p.ready = flags + kMaxCand;
+    p.jobready = flags + 2 * kMaxCand;
+    p.epoch = tp.epoch;
+    const size_t ntw = (size_t)s->ctx->tw_wb;
+    p.tw64 = (const double2*)s->tw;
+    p.tw32 = (const float2*)((char*)s->tw + sizeof(double2) * ntw);
+    p.ntab = (int)ntw;
+    p.fused = 0;
+    p.Hpair = nullptr;
+    const int slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    p.status = s->env.dstatus + slot;
+    if (++s->next_seq == 0) s->next_seq = 1;
+    ServeSlot& sl = s->slots[slot];
+    memcpy(&sl.p, &p, sizeof p);
+    sl.base = s->published;
+    sl.nprep = nprep;
+    sl.njobs = njobs;
+    sl.nitems = (int)nitems;
+    sl.seq = s->next_seq;
+    sl.skip_prep = stall ? 1 : 0;
+    for (long long t = 0; t < nitems; ++t) s->tmap[(s->published + t) & s->env.tmask] = slot;
+    // the slot and the map before the count that publishes them
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s->published += nitems;
+    *reinterpret_cast<volatile long long*>(&s->hdr->published) = s->published;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s->slot_seq[slot] = sl.seq;
+    s->slot_tpl[slot] = ti;
+    s->seq_slot[sl.seq] = slot;
+    tp.inflight += 1;
+    tp.last_use = ++s->clock;
+    if (seq_out) *seq_out = sl.seq;
+    return serve_ensure_running(s);
+}
+
+extern "C" int apx_server_poll(apx_server* s, int64_t seq, int32_t* status) {
+    if (!s) return APX_ERR_ARG;
+    auto it = s->seq_slot.find((unsigned)seq);
+    if (it == s->seq_slot.end()) return APX_ERR_ARG;  // unknown or already collected
+    const int slot = it->second;
+    if (*reinterpret_cast<volatile unsigned*>(&s->done_seq[slot]) != (unsigned)seq) {
+        DeviceGuard dg(s->device);
+        const int rc = serve_ensure_running(s);
+        return rc ? rc : 0;
+    }
+    std::atomic_thread_fence(std::memory_order_seq_cst);  // the outputs after the completion word
+    const unsigned st = *reinterpret_cast<volatile unsigned*>(&s->fstatus[slot]);
+    ServeTemplate& tp = s->tpl[s->slot_tpl[slot]];
+    tp.inflight -= 1;
+    if (st & 2u) tp.epoch = 0;  // a preparation that did not finish: prepare the template anew next time
+    s->slot_seq[slot] = 0;
+    s->slot_tpl[slot] = -1;
+    s->seq_slot.erase(it);
+    s->free_slots.push_back(slot);
+    if (status) *status = (st & 4u) ? APX_ERR_CHECK : (st & 2u) ? APX_ERR_TIMEOUT : (st & 1u) ? APX_ERR_NONFINITE : APX_OK;
+    return 1;
+}
+
+extern "C" int apx_server_test_stall_next(apx_server* s) {
+    if (!s) return APX_ERR_ARG;
+    s->stall_next = 1;
+    return APX_OK;
+}
+
+extern "C" int64_t apx_server_launch_count(const apx_server* s) { return s ? s->launches : 0; }

@@ -41,10 +41,10 @@ __device__ __forceinline__ void load_window(const Params& p, const BlockGeom& g,
         const long long gi = g.start + t;
         float2 v;
         if (aligned && gi >= 0 && gi + 1 < p.L) {
-            v = __ldg(reinterpret_cast<const float2*>(s + gi));
+            v = APX_LD_IN(reinterpret_cast<const float2*>(s + gi));
         } else {
-            v.x = (gi >= 0 && gi < p.L) ? __ldg(&s[gi]) : 0.f;
-            v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? __ldg(&s[gi + 1]) : 0.f;
+            v.x = (gi >= 0 && gi < p.L) ? APX_LD_IN(&s[gi]) : 0.f;
+            v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? APX_LD_IN(&s[gi + 1]) : 0.f;
         }
         xs[t] = v.x;
         xs[t + 1] = v.y;
@@ -63,7 +63,7 @@ struct Shared {
 // (xcorr(s, t) = conv(s, reverse(t)); the paper only names Matlab's xcorr),
 // zero past N (the odd-length pad of Section III).
 __device__ __forceinline__ float ktap(const Params& p, int n) {
-    return n < p.N ? __ldg(&p.k[p.xcorr ? p.N - 1 - n : n]) : 0.f;
+    return n < p.N ? APX_LD_IN(&p.k[p.xcorr ? p.N - 1 - n : n]) : 0.f;
 }
 
 // Fixed-point second-moment sum: q = trunc(x 2^sh) with ||x||_inf 2^sh in

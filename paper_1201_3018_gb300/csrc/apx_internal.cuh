@@ -22,6 +22,17 @@
 #define APX_IN_BOUNDS(cond, status) true
 #endif
 
+// Loads of a call's input samples and taps: through the read-only data cache,
+// except in the serving engine's persistent kernel, whose requests may reuse
+// an input buffer with new contents during its lifetime; its translation unit
+// defines APX_INPUT_COHERENT, and its loads stay inside the memory model
+// (plain loads, ordered after the acquire that published the request).
+#ifdef APX_INPUT_COHERENT
+#define APX_LD_IN(ptr) (*(ptr))
+#else
+#define APX_LD_IN(ptr) __ldg(ptr)
+#endif
+
 namespace apx {
 
 constexpr int kMaxWblock = 16384;

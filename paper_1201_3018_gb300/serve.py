@@ -47,6 +47,8 @@ class Request:
     W_block: int = 0      # what was launched (0: library default)
     mode: int = 0
     out: object = None    # pinned host result
+    status: int = 0       # completion status (APX_OK, ...)
+    path: str = ""        # which path served it ("engine" or "batched")
 
 
 def device_bytes(q) -> int:
@@ -220,3 +222,165 @@ def host_pools(seed, pool=1 << 23, ntemplates=32, nmax=8192):
 def latency_ms(done):
     lat = np.array([(q.done - q.arrival) * 1e3 for q in done])
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+
+class OutputRing:
+    """Regions of a circular buffer of `cap` elements, handed out in order and
+    released in any order; space is reclaimed from the oldest region on, so a
+    region is never overwritten while it is held."""
+
+    def __init__(self, cap: int):
+        self.cap = cap
+        self.regions = collections.deque()  # [start, end, released] in allocation order
+
+    def alloc(self, n: int):
+        if n < 1 or n > self.cap:
+            return None
+        if not self.regions:
+            start = 0
+        else:
+            head, tail = self.regions[-1][1], self.regions[0][0]
+            if head > tail or (head == tail and head == self.cap):
+                start = head if head + n <= self.cap else (0 if n <= tail else None)
+            elif head == tail:  # full
+                start = None
+            else:
+                start = head if head + n <= tail else None
+        if start is None:
+            return None
+        reg = [start, start + n, False]
+        self.regions.append(reg)
+        return reg
+
+    def unalloc(self, reg):
+        """Take back the newest region (its request was not accepted)."""
+        assert self.regions and self.regions[-1] is reg
+        self.regions.pop()
+
+    def free(self, reg):
+        reg[2] = True
+        while self.regions and self.regions[0][2]:
+            self.regions.popleft()
+
+
+class PersistentServer:
+    """The same serving on the library's persistent kernel (apx_server): each
+    admitted request is submitted on its own as it arrives (no host batching:
+    the kernel's CTAs take the blocks of whatever is in flight), its signal is
+    read in place from the pinned pool and its result written in place into a
+    pinned output ring, and completion is read from a host-mapped word.
+    Templates stay resident on the device between requests that share them.
+    The engine serves the FFT core at W_block 8192, kernels of up to 4093
+    taps; longer kernels go to the host-batched path (Server) on its own
+    streams, beside the persistent kernel (one CTA per two SMs)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, tuner=None, slots: int = 512,
+                 templates: int = 128, out_floats: int = 64 << 20, idle_ms: float = 20.0, fallback_streams: int = 2,
+                 ctas: int = 0):
+        import torch
+        from . import apx
+        self.apx, self.torch = apx, torch
+        self.ctx = apx.Context(device)
+        # one persistent CTA per two SMs: the batched path's block kernels (up to
+        # 512 threads) still find room beside it
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        self.srv = apx.Server(self.ctx, slots=slots, templates=templates, ctas=ctas or max(1, sms // 2),
+                              idle_ms=idle_ms)
+        self.out = torch.empty(out_floats, dtype=torch.float32, pin_memory=True)
+        self.ring = OutputRing(out_floats)
+        self.budget = budget_bytes
+        self.tuner = tuner
+        self.inflight = {}                  # seq -> (request, bytes)
+        self.in_flight = 0
+        self.peak_in_flight = 0
+        self.max_overlap = 0
+        self.submitted = 0
+        self.fallback = Server(device, budget_bytes=budget_bytes, streams=fallback_streams, tuner=tuner, max_batch=1)
+
+    def close(self):
+        self.srv.close()
+        self.fallback.close()
+        self.ctx.close()
+
+    def engine_choice(self, N, op, target):
+        """W_block for the engine, or None for the batched path.  The engine's
+        CTAs take one block per work item, so each item should carry many
+        outputs: W_block 8192 (the engine's largest) for kernels of up to 4093
+        taps, whose blocks then keep at least 4098 outputs."""
+        return None if (N | 1) > 4093 else 8192
+
+    def _submit(self, q, s_host, k_host):
+        apx = self.apx
+        op = apx.OP_XCORR if q.xcorr else apx.OP_CONV
+        Wb = self.engine_choice(q.N, op, q.target)
+        n = q.L + q.N - 1
+        reg = self.ring.alloc(n)
+        if reg is None:
+            return False
+        q.W_block, q.mode = Wb, op | apx.CORE_FFT | apx.PACK_AUTO
+        q.out = self.out[reg[0]:reg[1]]
+        seq = self.srv.submit(s_host.data_ptr() + 4 * q.s_off, q.L, k_host.data_ptr() + 4 * k_host.stride(0) * q.k_id,
+                              q.N, q.out.data_ptr(), Wb, q.mode, q.target)
+        if seq is None:  # every slot or template entry in use
+            self.ring.unalloc(reg)
+            return False
+        nbytes = device_bytes(q)
+        q.path = "engine"
+        self.inflight[seq] = (q, nbytes, reg)
+        self.in_flight += nbytes
+        self.peak_in_flight = max(self.peak_in_flight, self.in_flight)
+        self.max_overlap = max(self.max_overlap, len(self.inflight))
+        self.submitted += 1
+        return True
+
+    def _poll(self, on_done=None):
+        done = []
+        for seq in list(self.inflight):
+            st = self.srv.poll(seq)
+            if st is None:
+                continue
+            q, nbytes, reg = self.inflight.pop(seq)
+            q.done = time.perf_counter()
+            q.status = st
+            if on_done is not None:
+                on_done(q)  # q.out is valid until its region of the ring is reused
+            self.ring.free(reg)
+            self.in_flight -= nbytes
+            done.append(q)
+        return done
+
+    def run(self, trace, s_host, k_host, realtime: bool = True, on_done=None):
+        """Serve `trace` as Server.run does; returns the completed requests."""
+        apx = self.apx
+        pending = collections.deque(trace)
+        waiting = collections.deque()
+        finished = []
+        fb = self.fallback
+        t0 = time.perf_counter()
+        while pending or waiting or self.inflight or any(b is not None for b in fb.busy):
+            now = time.perf_counter()
+            while pending and (not realtime or pending[0].t <= now - t0):
+                q = pending.popleft()
+                q.arrival = t0 + q.t if realtime else now
+                waiting.append(q)
+            finished.extend(self._poll(on_done))
+            finished.extend(fb._poll(on_done))
+            # admission in arrival order: the engine, or the batched path for long kernels
+            while waiting:
+                q = waiting[0]
+                op = apx.OP_XCORR if q.xcorr else apx.OP_CONV
+                if self.engine_choice(q.N, op, q.target) is None:
+                    free = [i for i, b in enumerate(fb.busy) if b is None]
+                    if not free:
+                        break
+                    q.path = "batched"
+                    fb._launch(free[0], [waiting.popleft()], s_host, k_host)
+                    continue
+                if self.in_flight + device_bytes(q) > self.budget and self.inflight:
+                    break
+                if not self._submit(q, s_host, k_host):
+                    break
+                waiting.popleft()
+            if realtime and pending and not waiting and not self.inflight:
+                time.sleep(max(0.0, min(1e-4, pending[0].t - (time.perf_counter() - t0))))
+        return finished

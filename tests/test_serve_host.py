@@ -58,3 +58,30 @@ def test_trace_shape():
         assert q.target in (30.0, 45.0, 60.0)
     # mean inter-arrival close to 1 / rate
     assert abs(np.diff(t).mean() - 5e-4) < 1e-4
+
+
+def test_output_ring_never_overlaps_held_regions():
+    """Regions handed out in order and released in any order: no two held
+    regions overlap, every region lies inside the buffer, and a request that
+    cannot be placed is refused rather than placed over a held one."""
+    g = np.random.default_rng(9)
+    ring = serve.OutputRing(1000)
+    held = []
+    refused = 0
+    for step in range(5000):
+        if held and (g.random() < 0.45 or len(held) > 20):
+            reg = held.pop(int(g.integers(0, len(held))))
+            ring.free(reg)
+            continue
+        reg = ring.alloc(int(g.integers(1, 300)))
+        if reg is None:
+            refused += 1
+            continue
+        assert 0 <= reg[0] < reg[1] <= 1000
+        for h in held:
+            assert reg[1] <= h[0] or h[1] <= reg[0], (reg, h)
+        held.append(reg)
+    assert refused > 0 and ring.alloc(2000) is None
+    for reg in held:
+        ring.free(reg)
+    assert ring.alloc(1000) == [0, 1000, False]
