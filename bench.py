@@ -634,14 +634,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # warm-up after the sampler's start, so that the timed steps follow busy ones
     for _ in range(max(3, args.warmup)):
         step()
         step_full()
     ctx.apx_sync(stream)
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     barrier()
     n0 = ctx.launch_count()
     clocks.mark("t0")
@@ -739,9 +739,12 @@ def main():
     roof = {"kernel": dom, "avg_launch_us": avg_ms * 1e3}
     packed_blocks = int(sum(hist[1:4]))
     if dom == "fft":
-        # the blocks' transforms plus the kernel spectrum (one real FFT of W_block
-        # points), which this single call's launch computes too
-        flops = sum(fft_flops(Wb) if m == apx.BLK_FULL else 0.0 for m in st["mode"]) + 2.5 * Wb * math.log2(Wb)
+        # the blocks' transforms, plus the kernel spectrum (one real FFT of W_block
+        # points) when the block kernel's own launch computes it (a fused call,
+        # with no separate spectrum launches)
+        flops = sum(fft_flops(Wb) if m == apx.BLK_FULL else 0.0 for m in st["mode"])
+        if not prof.get("spectra", (0.0, 0))[1]:
+            flops += 2.5 * Wb * math.log2(Wb)
         fp64 = sum(fft_flops(Wb // 2 if m == apx.BLK_SYM else Wb) for m in st["mode"] if m in (1, 2, 3))
         if fp64 > flops:
             roof.update(bound="alu", achieved=fp64 / (avg_ms * 1e-3) / 1e12, peak=pk["fp64_tflops"],
