@@ -105,8 +105,9 @@ struct KStats {
     double sig2k;
 };
 
-// ||k||_inf and the kernel's second moment over its N taps (block-wide); taps
-// are fetched 8 per thread at a time so the loads overlap.
+// ||k||_inf and, when a packing candidate needs it, the kernel's second moment
+// over its N taps (block-wide); taps are fetched 8 per thread at a time so the
+// loads overlap.
 constexpr int kTapBatch = 8;
 __device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
     float m = 0.f;
@@ -127,7 +128,7 @@ __device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
     k.Mk = block_reduce<float, true>(m, sh.redf);
     k.bad = block_reduce<int, true>(bad, sh.redi);
     k.sig2k = 0.0;
-    if (!k.bad && k.Mk > 0.f) {
+    if (!k.bad && k.Mk > 0.f && p.ncand > 0) {  // the moment feeds only the packing candidates' model
         const FxScale f = fx_scale(k.Mk);
         long long acc = 0;
         for (int n0 = threadIdx.x; n0 < p.N; n0 += step) {

@@ -111,8 +111,8 @@ struct Params {
 // [r S, r S + S), S = m/8; CTA 0 holds classes {0, 1, 4, 7}, CTA 1 classes
 // {2, 3, 5, 6} (each set closed under r -> -r mod 8, so frequencies k and m-k
 // meet in one CTA).  pair_owner(r): the CTA holding class r; pair_local(r):
-// its position among that CTA's four classes.
-constexpr unsigned kPairMask1 = 0x6Cu;
+// its position among that CTA's four classes (ascending class order).
+constexpr unsigned kPairMask1 = 0x6Cu;  // the classes of CTA 1
 __host__ __device__ __forceinline__ int pair_owner(int r) { return (int)((kPairMask1 >> r) & 1u); }
 __host__ __device__ __forceinline__ int pair_local(int r) {
     const unsigned mine = pair_owner(r) ? kPairMask1 : (~kPairMask1 & 0xFFu);
@@ -649,6 +649,18 @@ __device__ void spectral_multiply(C* Z, int m, const C* H, const C* __restrict__
 // wait for the previous one's results.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Cluster barrier in two halves (every thread of every CTA of the cluster).
+// arrive.relaxed orders nothing (it only says that this CTA has started, so
+// that the others may access its shared memory after their wait); arrive
+// (release) makes this thread's earlier memory accesses, those to other CTAs'
+// shared memory included, visible to the threads past the matching wait
+// (acquire).  Work placed between the halves overlaps the barrier.
+__device__ __forceinline__ void cl_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
     unsigned v;

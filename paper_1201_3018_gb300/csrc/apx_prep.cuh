@@ -33,19 +33,16 @@ __device__ inline void spec_subfft(const Params& p, int r, float2* Z) {
     __syncthreads();  // Z is free again
 }
 
-// H[k] for one k <= m, from the sub-spectra (read around L1: written during this call).
-__device__ inline void spec_combine(const Params& p, int k) {
-    const int n = p.Wb, m = n / 2, R1 = spec_r1(n), ns = n / R1;
+// H[k] for one k <= m from y[r] = Y_r[k mod n/R1], r < R1 (the last
+// decimation stage), into Hfull and, when the call runs the two-CTA block
+// kernel, its staging-order table.
+__device__ inline void spec_combine_y(const Params& p, int k, const float2 (&y)[16]) {
+    const int n = p.Wb, m = n / 2, R1 = spec_r1(n);
     float2 acc = make_float2(0.f, 0.f);
-    const int kk = k & (ns - 1);
-    float2 y[16], w[16];
+    float2 w[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        if (r < R1) {
-            y[r] = __ldcg(&p.Ysub[r * ns + kk]);
-            w[r] = __ldg(&p.tw32[(r * k * (p.ntab / n)) & (p.ntab - 1)]);
-        }
-    }
+    for (int r = 0; r < 16; ++r)
+        if (r < R1) w[r] = __ldg(&p.tw32[(r * k * (p.ntab / n)) & (p.ntab - 1)]);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         if (r < R1) {
@@ -69,6 +66,17 @@ __device__ inline void spec_combine(const Params& p, int k) {
         }
         if (k >= m / 2) e[nt] = h;
     }
+}
+
+// H[k] for one k <= m, from the sub-spectra (read around L1: written during this call).
+__device__ inline void spec_combine(const Params& p, int k) {
+    const int n = p.Wb, R1 = spec_r1(n), ns = n / R1;
+    const int kk = k & (ns - 1);
+    float2 y[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        if (r < R1) y[r] = __ldcg(&p.Ysub[r * ns + kk]);
+    spec_combine_y(p, k, y);
 }
 
 // Kernel statistics and candidate norms into *p.ki (the whole CTA).
