@@ -17,8 +17,17 @@
 // {2, 3, 5, 6}.  The first forward pass (butterflies split between the CTAs,
 // inputs straight from the window) writes each output to the CTA that holds
 // its class; the forward inner passes, the spectral product and the inverse
-// inner passes stay inside a CTA; the last inverse pass (M = m) reads the
-// partner's four classes and writes the block's outputs (Eq. 17).
+// inner passes stay inside a CTA; for the last inverse pass (M = m) each CTA
+// sends the partner the values of its four classes that the partner's
+// butterflies take, and writes the block's outputs (Eq. 17).
+//
+// The exchanges are asynchronous remote stores (st.async) that count their
+// bytes on the receiving CTA's transaction barrier (mbarrier): the sender
+// waits for nothing, the receiver waits for its barrier's phase, and no CTA
+// ever reads another's shared memory, so only one cluster-wide barrier remains
+// (at the start, so that both CTAs and their barriers exist before any remote
+// store).  Every wait is bounded (about a second; then the status word's
+// timeout bit is set and the CTA leaves).
 //
 // The kernel is compiled for each W_block (m = 2^LM), so that the passes'
 // strides, slot arithmetic and digit reversals are constants (measured 17 %
@@ -82,6 +91,55 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Shared-memory addresses in the cluster window and the transaction barrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+// the barrier inits, visible to the cluster before its next barrier wait
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the phase's only arrival, expecting `bytes` of remote stores
+__device__ __forceinline__ void mbar_expect(unsigned long long* b, unsigned bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                     smem_addr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Wait (bounded) for phase 0 of the barrier: the remote stores it counts are
+// then visible to this thread.  False after about a second.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* b) {
+    const unsigned a = smem_addr(b);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kPrepSpinCycles) return false;
+    }
+}
+// 8 and 4 bytes into another CTA's shared memory, counted on its barrier
+__device__ __forceinline__ void st_async(unsigned raddr, float2 v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(v.x), "f"(v.y), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned raddr, unsigned v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr), "r"(v),
+                 "r"(rbar)
+                 : "memory");
+}
+
 // threads per CTA (m = 2^LM, W_block = 2m) and the CTAs per SM the register
 // budget is set for (64 registers per thread)
 constexpr int pair_threads(int LM) { return (1 << LM) / 16; }
@@ -97,10 +155,22 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
     constexpr int Q = 2, m = 1 << LM, S = m / 8, nt = S / Q, ML = m / Q;
     constexpr int NW = nt / 32;  // warps per CTA
     static_assert(nt >= 32 && nt % 32 == 0, "whole warps");
+    // bytes each CTA receives: the partner's first-pass outputs of this CTA's four
+    // classes and its warps' flags; then the partner's classes at this CTA's
+    // last-pass butterflies
+    constexpr unsigned kBytesA = 32u * nt + 4u * NW, kBytesB = 32u * nt;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_wf[Q * NW];  // every warp's input flags, cluster-wide: bit 0 non-finite, bit 1 non-zero
+    __shared__ __align__(8) unsigned long long s_bar[2];  // the two exchanges' transaction barriers
     if (!APX_IN_BOUNDS(blockDim.x == nt, p.status)) return;  // every CTA alike: none reaches a barrier
-    cl_arrive_relaxed();  // this CTA has started: the others write its shared memory only after their wait
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0]);
+        mbar_init(&s_bar[1]);
+        mbar_init_fence();
+        mbar_expect(&s_bar[0], kBytesA);
+        mbar_expect(&s_bar[1], kBytesB);
+    }
+    cl_arrive_relaxed();  // this CTA and its barriers exist: the partner stores into it only after its wait
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const long long i = (long long)(blockIdx.x / Q);
@@ -122,14 +192,21 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
     const int j = rank * nt + t;
     float2 v[8];
     const bool al8 = ((reinterpret_cast<uintptr_t>(p.s + g.start) & 7u) == 0);
+    const long long g0 = g.start + 2ll * j;
+    if (al8 && g0 >= 0 && g0 + 14ll * S + 1 < p.L) {  // all eight pairs inside the signal
+        const float2* src = reinterpret_cast<const float2*>(p.s + g0);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const long long gi = g.start + 2ll * (j + q * S);
-        if (al8 && gi >= 0 && gi + 1 < p.L) {
-            v[q] = __ldg(reinterpret_cast<const float2*>(p.s + gi));
-        } else {
-            v[q].x = (gi >= 0 && gi < p.L) ? __ldg(p.s + gi) : 0.f;
-            v[q].y = (gi + 1 >= 0 && gi + 1 < p.L) ? __ldg(p.s + gi + 1) : 0.f;
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q * S);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long gi = g0 + 2ll * q * S;
+            if (al8 && gi >= 0 && gi + 1 < p.L) {
+                v[q] = __ldg(reinterpret_cast<const float2*>(p.s + gi));
+            } else {
+                v[q].x = (gi >= 0 && gi < p.L) ? __ldg(p.s + gi) : 0.f;
+                v[q].y = (gi + 1 >= 0 && gi + 1 < p.L) ? __ldg(p.s + gi + 1) : 0.f;
+            }
         }
     }
     bool bad = false, nz = false;
@@ -148,24 +225,29 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
 #pragma unroll
         for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
     }
-    cl_wait();  // every CTA of the cluster has started
+    cl_wait();  // the partner has started and its barriers are initialised
+    const unsigned prank = (unsigned)(rank ^ 1);
     {
-        float2* dst[Q];
-        unsigned* wf[Q];
+        const unsigned zr = cluster_addr(smem_addr(Z), prank), br = cluster_addr(smem_addr(&s_bar[0]), prank);
+        const int pj = pad16(j);  // slot of class position u: pj + pad16(u S), as j < S
 #pragma unroll
-        for (int o = 0; o < Q; ++o) {
-            dst[o] = o == rank ? Z : cl.map_shared_rank(Z, o);
-            wf[o] = o == rank ? s_wf : cl.map_shared_rank(s_wf, o);
+        for (int r = 0; r < 8; ++r) {
+            const int sl = pj + pad16(pair_local(r) * S);
+            if (pair_owner(r) == rank) Z[sl] = v[r];
+            else st_async(zr + (unsigned)sizeof(float2) * sl, v[r], br);
         }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) dst[pair_owner(r)][pad16(pair_local(r) * S + j)] = v[r];
         if ((t & 31) == 0) {
-#pragma unroll
-            for (int o = 0; o < Q; ++o) wf[o][rank * NW + (t >> 5)] = wbits;
+            unsigned* f = &s_wf[rank * NW + (t >> 5)];
+            *f = wbits;
+            st_async(cluster_addr(smem_addr(f), prank), wbits, br);
         }
     }
-    cl_arrive();  // release: this thread's writes into the cluster's shared memory
-    cl_wait();    // every CTA's first-pass outputs, flags and twiddle copies are in place
+    // this CTA's own outputs and flags (barrier), the partner's (transaction
+    // barrier: it counts kBytesA); on a timeout the status says so and the
+    // block's outputs are not valid
+    const bool got_a = mbar_wait0(&s_bar[0]);
+    __syncthreads();
+    if (!got_a) atomicOr(p.status, 2u);
     unsigned fl = 0;
 #pragma unroll
     for (int w = 0; w < Q * NW; ++w) fl |= s_wf[w];
@@ -191,8 +273,8 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
     const int kbad = __ldcg(&p.ki->bad);
     if (any_bad || kbad || !live || Mk == 0.f) {
         // the same for every CTA of the cluster: NaN for a non-finite block or
-        // kernel, zeros for a silent one; no access to another CTA's shared
-        // memory after the barrier above
+        // kernel, zeros for a silent one; neither CTA sends the second
+        // exchange, and the first has been received
         const float c = (any_bad || kbad) ? __int_as_float(0x7fc00000) : 0.f;
         for (int jj = g.lo + rank * nt + t; jj < g.hi; jj += Q * nt) {
             const long long o = g.start + jj;
@@ -233,9 +315,9 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
                     if (c == 0) {
                         pk = pad16(rt);
                         pmk = pad16(fft_perm_rc<8, S>(S - t, S));
-                    } else {
-                        pk = pad16(u * S + rt);
-                        pmk = pad16(partner_local(rank, u) * S + (S - 1 - rt));
+                    } else {  // pad16(a S + x) = pad16(a S) + pad16(x) for x < S
+                        pk = pad16(u * S) + pad16(rt);
+                        pmk = pad16(partner_local(rank, u) * S) + pad16(S - 1 - rt);
                     }
                 }
                 const float2 a = Z[pk], b = Z[pmk];
@@ -249,35 +331,43 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
         }
     }
     __syncthreads();
-    pair_inner_passes<LM, true>(Z, tws, p.status);
-    cl_arrive();  // release: this CTA's classes are complete
+    pair_inner_passes<LM, true>(Z, tws, p.status);  // (ends with a barrier: the classes are complete)
 
-    // Last inverse pass (M = m): butterfly j reads its eight slots r S + j (the
-    // other CTAs' classes among them) and yields the natural-order points
-    // z[j + S q].  Its twiddles come first, while the barrier completes.
+    // Last inverse pass (M = m): butterfly j takes its eight slots r S + j and
+    // yields the natural-order points z[j + S q].  Each thread first sends the
+    // partner's thread t (butterfly prank nt + t) this CTA's four values of it,
+    // into the partner's receive buffer at u nt + t (u: class position).
+    float2* Rb = tws + S;  // the partner's four classes at this CTA's butterflies
+    {
+        const unsigned rr = cluster_addr(smem_addr(Rb), prank), br = cluster_addr(smem_addr(&s_bar[1]), prank);
+        const int pjp = pad16((int)prank * nt + t);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            st_async(rr + (unsigned)sizeof(float2) * (u * nt + t), Z[pjp + pad16(u * S)], br);
+    }
     float2 w[8];
     twiddles<float2, 8, true>(w, tws, j);
-    cl_wait();
+    if (!mbar_wait0(&s_bar[1])) atomicOr(p.status, 2u);
     {
-        const float2* srcq[Q];
+        const int pj = pad16(j);
 #pragma unroll
-        for (int o = 0; o < Q; ++o) srcq[o] = o == rank ? Z : cl.map_shared_rank(Z, o);
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = srcq[pair_owner(r)][pad16(pair_local(r) * S + j)];
+        for (int r = 0; r < 8; ++r)
+            v[r] = pair_owner(r) == rank ? Z[pj + pad16(pair_local(r) * S)] : Rb[pair_local(r) * nt + t];
     }
 #pragma unroll
     for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
     dft8<float2, true>(v);
-    cl_arrive();  // this thread's reads of other CTAs' shared memory are complete (their values are used)
 
     // Eq. (17): point e = j + S q holds outputs 2e and 2e+1 of the block.
     const bool oal8 = ((reinterpret_cast<uintptr_t>(p.r) & 7u) == 0);
+    const long long o0 = g.start + 2ll * j;
+    const bool oin = oal8 && o0 >= 0 && o0 + 14ll * S + 1 < p.out_len;  // every pair inside the output
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int jj = 2 * (j + q * S);
         if (jj < g.lo || jj >= g.hi) continue;
         const long long o = g.start + jj;
-        if (oal8 && o >= 0 && o + 1 < p.out_len) {
+        if (oin || (oal8 && o >= 0 && o + 1 < p.out_len)) {
             *reinterpret_cast<float2*>(p.r + o) = v[q];
             if (p.rq) *reinterpret_cast<int2*>(p.rq + o) = make_int2(0, 0);
         } else {
@@ -285,11 +375,13 @@ __global__ void __launch_bounds__(pair_threads(LM), pair_min_ctas(pair_threads(L
             if (o + 1 >= 0 && o + 1 < p.out_len) { p.r[o + 1] = v[q].y; if (p.rq) p.rq[o + 1] = 0; }
         }
     }
-    cl_wait();  // no CTA leaves while another still reads its shared memory
+    // Leaving needs no cluster barrier: no CTA reads another's shared memory,
+    // and each CTA has received all the partner's stores into it (its waits).
 }
 
-// the CTA's classes and the twiddle bases (m/8 = W_block/16 entries)
-size_t fft_pair_smem_bytes(int Wb) { return sizeof(float2) * (padded_len(Wb / 4) + Wb / 16); }
+// the CTA's classes, the twiddle bases (m/8 = W_block/16 entries), the receive
+// buffer of the last pass (4 W_block/32 entries)
+size_t fft_pair_smem_bytes(int Wb) { return sizeof(float2) * (padded_len(Wb / 4) + Wb / 16 + Wb / 8); }
 
 namespace {
 

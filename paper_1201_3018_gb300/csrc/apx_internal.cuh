@@ -425,19 +425,20 @@ __host__ __device__ constexpr int fft_radix(int m, int nt) {
 // inverse DFT.  Each butterfly reads and writes the same slots, so a pass needs
 // no barrier inside; callers separate passes with __syncthreads().
 //
-// Slot addresses: pad16 adds i >> 4 and i >> 8, which is linear over a
-// butterfly's slots base + q S when S is a multiple of 256, or when the
-// sub-transform lies inside one 256-entry span (M <= 256) and S is a multiple
-// of 16 or the sub-transform inside one 16-entry run (M <= 16): then slot q is
-// pad16(base) + q (S + S/16 + S/256) (the terms present), one multiply-add
-// instead of a pad16 per slot.  The choice is uniform over the pass.
+// Slot addresses: for base = g M + j with j < S (all powers of two),
+// pad16(base + q S) = pad16(base) + pad16(q S): the i >> 4 and i >> 8 terms of
+// base + q S split into those of base and of q S, because base's aligned part
+// g M is a multiple of 16 (of 256) whenever the run from base to base + (RAD-1)
+// S crosses a multiple of 16 (of 256).  So a butterfly's slots are one pad16
+// and per-q offsets, constants where S is.
 template <typename C, int RAD, bool INV>
 __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict__ tw, int ntab, unsigned* st) {
     const int S = M / RAD, nbf = m / RAD;
     const int tstep = ntab / M;
-    const bool lin = (S & 255) == 0 || (M <= 256 && ((S & 15) == 0 || M <= 16));
-    const int pstride = S + ((S & 15) == 0 ? S >> 4 : 0) + ((S & 255) == 0 ? S >> 8 : 0);
     const int lS = 31 - __clz(S);  // S is a power of two: sub-transform and offset by shift and mask
+    int off[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) off[q] = pad16(q * S);
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
         const int g = b >> lS, j = b & (S - 1);
         const int base = g * M + j;
@@ -446,7 +447,7 @@ __device__ __forceinline__ void fft_pass(C* Z, int m, int M, const C* __restrict
         int slot[RAD];
         const int p0 = pad16(base);
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) slot[q] = lin ? p0 + q * pstride : pad16(base + q * S);
+        for (int q = 0; q < RAD; ++q) slot[q] = p0 + off[q];
 #pragma unroll
         for (int q = 0; q < RAD; ++q) v[q] = Z[slot[q]];
         if (S > 1) twiddles<C, RAD, INV>(w, tw, j * tstep);
