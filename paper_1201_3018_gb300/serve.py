@@ -26,10 +26,27 @@ default.
 from __future__ import annotations
 
 import collections
+import contextlib
 import dataclasses
+import gc
 import time
 
 import numpy as np
+
+
+@contextlib.contextmanager
+def gc_paused():
+    """No cyclic garbage collection while requests are in flight: a full
+    collection of a large heap stops the host loop for tens of milliseconds,
+    which every request then in flight pays (one collection before)."""
+    enabled = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if enabled:
+            gc.enable()
 
 
 @dataclasses.dataclass
@@ -167,6 +184,10 @@ class Server:
         A request's result q.out is a view of its stream's pinned buffer, valid
         until that stream's next batch: `on_done(q)` runs at completion, before
         the buffer is reused, for a consumer that keeps results."""
+        with gc_paused():
+            return self._run(trace, s_host, k_host, realtime, on_done)
+
+    def _run(self, trace, s_host, k_host, realtime, on_done):
         pending = collections.deque(trace)
         waiting = collections.deque()
         finished = []
@@ -351,6 +372,10 @@ class PersistentServer:
 
     def run(self, trace, s_host, k_host, realtime: bool = True, on_done=None):
         """Serve `trace` as Server.run does; returns the completed requests."""
+        with gc_paused():
+            return self._run(trace, s_host, k_host, realtime, on_done)
+
+    def _run(self, trace, s_host, k_host, realtime, on_done):
         apx = self.apx
         pending = collections.deque(trace)
         waiting = collections.deque()
