@@ -365,6 +365,40 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
                 "frac": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "bytes": byts,
                 "peak_source": "measured copy bandwidth" if pk.get("source") != "fallback" else "fallback"}
 
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cl = pk.get("clocks_under_load") or {}
+    cublas_per_cycle = (pk["bf16_tflops_sustained"] * 1e12 / (sms * cl["sm_mhz_median"] * 1e6)
+                        if pk.get("bf16_tflops_sustained") and cl.get("sm_mhz_median") else None)
+
+    def per_clock(stepf, n, executed):
+        """The GEMM kernel back to back for about half a second with the SM clock
+        sampled: its executed flops per SM cycle at the clock it held, against
+        the sustained cuBLAS bf16 figure per SM cycle at the clock that held."""
+        cs = ClockSampler(dev.index or 0)
+        cs.start()
+        time.sleep(0.3)
+        ctx.profile(True)
+        cs.mark("t0")
+        for _ in range(n):
+            stepf()
+        torch.cuda.synchronize()
+        cs.mark("t1")
+        pr = ctx.profile_read()
+        ctx.profile(False)
+        cs.stop()
+        ms = pr["tc_mma"][0] / max(pr["tc_mma"][1], 1)
+        c = cs.summary()
+        out = {"kernel_ms": ms, "clocks": c, "calls": n}
+        if c.get("sm_mhz"):
+            fpc = executed / (ms * 1e-3) / (sms * c["sm_mhz"] * 1e6)
+            out["executed_flop_per_sm_cycle"] = fpc
+            if cublas_per_cycle:
+                out["cublas_bf16_sustained_flop_per_sm_cycle"] = cublas_per_cycle
+                out["frac_per_cycle"] = fpc / cublas_per_cycle
+        return out
+
+    clk16 = per_clock(step, 3000, useful * kpad / N)
+
     # S_q = K_q = 16: every companded integer is exact in FP8 E4M3 (the paper's
     # 16-level setting), and the library runs the FP8 tensor-core path
     y8 = torch.empty(F, ldy, device=dev)
@@ -380,6 +414,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
     prof8 = ctx.profile_read()
     ctx.profile(False)
     mma8 = prof8["tc_mma"][0] / max(prof8["tc_mma"][1], 1)
+    clk8 = per_clock(step8, 4000, useful * (-(-(N + 127) // 128) * 128) / N)
     assert ctx.apx_sync(stream) == 0
     d8 = (y8[:, :out_len].double() - yfull.double())
     snr8 = (10 * torch.log10((yfull.double() ** 2).sum(1) / (d8 * d8).sum(1))).cpu().numpy()
@@ -392,7 +427,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
                                "unit": "TFLOP/s", "frac": useful / (mma8 * 1e-3) / 1e12 / (2 * peak),
                                "peak_source": "measured cuBLAS bf16 x 2 (nominal FP8 : FP16 dense ratio)",
                                "kernel_ms": mma8, "traffic": traffic_for("tc_mma_fp8")},
-           "roofline_hbm_write": hbm_write(mma8)}
+           "roofline_hbm_write": hbm_write(mma8), "sustained_per_clock": clk8}
     return {"workload": "filterbank: 2^22 N(0,1) samples, 32 Hann-windowed-sinc band-pass kernels of 1024 taps "
                         "(log-spaced 50 Hz - 20 kHz at 44.1 kHz), S_q = K_q = 127, FP16 integers on the tensor cores",
             "outputs_per_step": F * out_len, "value": F * out_len / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t,
@@ -406,7 +441,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
                                 "unit": "TFLOP/s", "frac": useful / (mma_ms * 1e-3) / 1e12 / peak,
                                 "peak_source": "measured cuBLAS bf16 (FP16 runs at the same tensor rate)",
                                 "executed_over_useful": kpad / N, "traffic": traffic_for("tc_mma")},
-            "roofline_hbm_write": hbm_write(mma_ms),
+            "roofline_hbm_write": hbm_write(mma_ms), "sustained_per_clock": clk16,
             "blocks": nb, "outputs_per_block": T, "fp8_sq16": fp8}
 
 
