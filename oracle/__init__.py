@@ -29,10 +29,10 @@ _lib = None
 
 # mode word (op | core | pack), same bit layout as the public ABI
 OP_CONV, OP_XCORR = 0x0, 0x1
-CORE_DIRECT, CORE_FFT = 0x00, 0x10
+CORE_DIRECT, CORE_FFT, CORE_TC = 0x00, 0x10, 0x30
 PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
 LITERAL = 0x2000  # the paper-literal symmetric form (Eq. 6 eps, FP64 Eqs. 11-15 with u_sys)
-BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
+BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE, BLK_TC = 0, 1, 2, 3, 4, 5, 6
 OK, ERR_ARG, ERR_WBLOCK, ERR_RANGE, ERR_INEXACT = 0, -1, -2, -3, -4
 
 

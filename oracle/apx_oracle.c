@@ -186,6 +186,13 @@ int32_t or_bits(int64_t Rmax) {
  *   asymmetric, Eq. (7):  R_max (sum_{q<M} 2^{b q}) <= 2^53.                  */
 int or_exact_ok(int blkmode, int32_t Nodd, int32_t Sq, int32_t Kq) {
     if (Nodd < 1 || Sq < 1 || Kq < 1) return 0;
+    if (blkmode == OR_BLK_TC) {
+        /* Tensor-core core: every companded integer (|x| <= 2048) is exact in
+         * FP16, every product exact in FP32, and FP32 sums of integers stay
+         * exact while their magnitude is at most 2^24 (the 24-bit significand);
+         * a partial sum of the N' taps is bounded by N' S K. */
+        return Sq <= 2048 && Kq <= 2048 && (int64_t)Nodd * Sq * Kq <= ((int64_t)1 << 24);
+    }
     u128 SK = (u128)(uint32_t)Sq * (u128)(uint32_t)Kq;
     u128 Rmax = SK * (u128)(uint32_t)Nodd;
     const u128 lim = (u128)1 << 53;
@@ -642,6 +649,17 @@ static int run_packed_block(const mode_t_* md, const or_plan_t* p, int64_t i, co
         if (!(ferr < 0.25)) return 0;
     }
     int32_t Wstart = (!fft && i == 0) ? 0 : (Nodd - 1) / 2;          /* Eq. (10) */
+    if (md->blk == OR_BLK_TC) {
+        /* the exact integer convolution of the block, Eq. (1) on s~ and k~ */
+        for (int32_t j = 0; j < Wb; ++j) {
+            int64_t acc = 0;
+            for (int32_t n = 0; n < Nodd && n <= j; ++n) acc += (int64_t)q[j - n] * (int64_t)md->kpk[n];
+            rq_blk[j] = acc;
+        }
+        st->mode = OR_BLK_TC; st->Sq = md->S; st->Kq = md->K; st->b = 0; st->cs = cs;
+        st->fft_err = 0.0;
+        return 1;
+    }
     if (md->literal) {
         /* the paper's own form: eps of Eq. (6), Eq. (4) and Eq. (9) in FP64,
          * Eqs. (11)-(15) in FP64 with u_sys; rounding may move a digit */
@@ -675,9 +693,14 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
                 const uint8_t* want) {
     if (!s || !k || !r_out) return OR_ERR_ARG;
     uint32_t op = mode & OR_OP_MASK, core = mode & OR_CORE_MASK, pack = mode & OR_PACK_MASK;
-    if (op > OR_OP_XCORR || (core != OR_CORE_DIRECT && core != OR_CORE_FFT) || pack > OR_PACK_ASYM3)
+    if (op > OR_OP_XCORR || (core != OR_CORE_DIRECT && core != OR_CORE_FFT && core != OR_CORE_TC) ||
+        pack > OR_PACK_ASYM3)
         return OR_ERR_ARG;
     int fft = core == OR_CORE_FFT;
+    /* the tensor-core core: the direct core's blocks, one candidate (OR_BLK_TC at
+     * the largest S_q = K_q its bound admits) or full precision */
+    int tc = core == OR_CORE_TC;
+    if (tc && pack != OR_PACK_AUTO && pack != OR_PACK_NONE) return OR_ERR_ARG;
     /* the paper-literal form: symmetric packing, direct core, fixed quantiser */
     int literal = (mode & OR_LITERAL) != 0;
     if (literal && (fft || pack != OR_PACK_SYM)) return OR_ERR_ARG;
@@ -699,7 +722,13 @@ int or_apx_conv(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     int nmodes = 0;
     int order[3] = {OR_BLK_SYM, OR_BLK_ASYM3, OR_BLK_ASYM2};  /* Table 1 ranking */
     if (kfinite && Mk > 0.0f) {
-        if (pack == OR_PACK_AUTO) {
+        if (pack == OR_PACK_AUTO && tc) {
+            int32_t Q = or_qmax_direct(OR_BLK_TC, Nodd);
+            if (Q >= 1) {
+                if (prep_mode(&modes[0], OR_BLK_TC, Q, Q, kr, N, Nodd, Mk, Wb, 0)) rc = OR_ERR_ARG;
+                else nmodes = 1;
+            }
+        } else if (pack == OR_PACK_AUTO) {
             for (int j = 0; j < 3; ++j) {
                 int32_t Q = fft ? or_qmax_fft(order[j], Nodd, Wb) : or_qmax_direct(order[j], Nodd);
                 if (Q < 1) continue;

@@ -29,6 +29,7 @@ extern "C" {
 #define OR_OP_MASK      0xFu
 #define OR_CORE_DIRECT  0x00u
 #define OR_CORE_FFT     0x10u
+#define OR_CORE_TC      0x30u   /* time-domain core on the tensor cores: FP16 integers, FP32 sums */
 #define OR_CORE_MASK    0xF0u
 #define OR_PACK_AUTO    0x000u
 #define OR_PACK_NONE    0x100u
@@ -49,6 +50,7 @@ extern "C" {
 #define OR_BLK_ASYM3 3
 #define OR_BLK_ZERO  4   /* ||s||_inf == 0 or ||k||_inf == 0: output is exactly 0 */
 #define OR_BLK_NONFINITE 5
+#define OR_BLK_TC    6   /* the block's companded integers convolved exactly in FP16 x FP16 -> FP32 */
 
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
