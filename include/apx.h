@@ -56,6 +56,15 @@ extern "C" {
 #define APX_CORE_DIRECT  0x000u  /* time-domain block convolution             */
 #define APX_CORE_FFT     0x010u  /* frequency-domain block convolution (W_block a power of two) */
 #define APX_CORE_AUTO    0x020u  /* batched calls only: the library picks the core */
+#define APX_CORE_TC      0x030u  /* time-domain blocks on the tensor cores: one
+                                    candidate, the block's companded integers in
+                                    FP16 at the largest S_q = K_q with
+                                    N' S_q K_q <= 2^24 (and <= 2048), summed
+                                    exactly in FP32 (Eq. 2 range, Eq. 3); blocks
+                                    the Section IV.D model does not admit run
+                                    full precision.  W_block a multiple of 64 up
+                                    to 8192, N' <= 449; APX_PACK_AUTO or
+                                    APX_PACK_NONE */
 #define APX_PACK_AUTO    0x000u  /* per-block choice under snr_target_db (Section IV.D) */
 #define APX_PACK_NONE    0x100u  /* full precision, FP32                        */
 #define APX_PACK_SYM     0x200u  /* symmetric packing, Eqs. (4)-(5)            */
@@ -84,6 +93,7 @@ extern "C" {
 #define APX_BLK_ASYM3     3
 #define APX_BLK_ZERO      4      /* ||s||_inf = 0 or ||k||_inf = 0: exact zeros   */
 #define APX_BLK_NONFINITE 5
+#define APX_BLK_TC        6      /* companded integers convolved on the tensor cores (APX_CORE_TC) */
 
 /* What one block did.  48 bytes, naturally aligned. */
 typedef struct {

@@ -22,11 +22,11 @@ _lib = None
 APX_OK, APX_ERR_ARG, APX_ERR_WBLOCK, APX_ERR_RANGE, APX_ERR_NONFINITE = 0, -1, -2, -3, -4
 APX_ERR_OOM, APX_ERR_BUDGET, APX_ERR_CUDA, APX_ERR_TIMEOUT, APX_ERR_CHECK = -5, -6, -7, -8, -9
 OP_CONV, OP_XCORR = 0x000, 0x001
-CORE_DIRECT, CORE_FFT, CORE_AUTO = 0x000, 0x010, 0x020
+CORE_DIRECT, CORE_FFT, CORE_AUTO, CORE_TC = 0x000, 0x010, 0x020, 0x030
 PACK_AUTO, PACK_NONE, PACK_SYM, PACK_ASYM2, PACK_ASYM3 = 0x000, 0x100, 0x200, 0x300, 0x400
 FULL_FP64 = 0x1000
 LITERAL = 0x2000
-BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE = 0, 1, 2, 3, 4, 5
+BLK_FULL, BLK_SYM, BLK_ASYM2, BLK_ASYM3, BLK_ZERO, BLK_NONFINITE, BLK_TC = 0, 1, 2, 3, 4, 5, 6
 
 # apx_request as a numpy record (80 bytes, natural C alignment)
 REQUEST_DTYPE = np.dtype({"names": ["s_in", "L", "k", "N", "r_out", "W_block", "mode", "snr_target_db", "S_q", "K_q",

@@ -142,6 +142,8 @@ typedef unsigned __int128 u128;
 // replaces Table 1's companding-range row for a power-of-two eps).
 bool exact_ok(int blk, int Nodd, int S, int K) {
     if (Nodd < 1 || S < 1 || K < 1) return false;
+    if (blk == APX_BLK_TC)  // FP16 operands (every integer up to 2048), FP32 sums of integers up to 2^24
+        return S <= kTcbQMax && K <= kTcbQMax && (long long)Nodd * S * K <= kTcbSumMax;
     u128 SK = (u128)(unsigned)S * (unsigned)K;
     u128 R = SK * (unsigned)Nodd;
     const u128 lim = (u128)1 << 53;
@@ -232,7 +234,9 @@ struct Plan {
 
 int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
     if (L < 1 || N < 1) return APX_ERR_ARG;
-    if ((mode & 0xFu) > APX_OP_XCORR || ((mode >> 4) & 0xFu) > 1u || ((mode >> 8) & 0xFu) > 4u ||
+    const uint32_t core = mode & 0xF0u;
+    if ((mode & 0xFu) > APX_OP_XCORR || (core != APX_CORE_DIRECT && core != APX_CORE_FFT && core != APX_CORE_TC) ||
+        ((mode >> 8) & 0xFu) > 4u ||
         (mode & ~(0xFFFu | APX_FULL_FP64 | APX_LITERAL)))
         return APX_ERR_ARG;
     if ((mode & APX_FULL_FP64) && ((mode & 0xF00u) != APX_PACK_NONE || (mode & 0xF0u) != APX_CORE_DIRECT))
@@ -245,6 +249,12 @@ int plan(int64_t L, int32_t N, int32_t Wb, uint32_t mode, Plan* p) {
     int W = Wb - Nodd - 1;
     if (W < 2) return APX_ERR_WBLOCK;
     if (fft && (Wb & (Wb - 1))) return APX_ERR_WBLOCK;
+    if (core == APX_CORE_TC) {  // the tensor-core block: 64-sample rows, at most one 128-row MMA tile
+        if (Wb % kTcbRow || Wb > 128 * kTcbRow) return APX_ERR_WBLOCK;
+        if (tcb_kslices(Nodd) > kTcbMaxSlices) return APX_ERR_ARG;
+        const uint32_t pack = mode & 0xF00u;
+        if (pack != APX_PACK_AUTO && pack != APX_PACK_NONE) return APX_ERR_ARG;
+    }
     long long span = L + N - Nodd;
     long long P = (span + W - 1) / W;
     if (P < 1) P = 1;
@@ -269,6 +279,18 @@ size_t direct_layout(const Cand* c, int nc, int Wb, int Nodd, DirectLayout* dl, 
     dl->offK = (int)al16((size_t)4 * (dl->padF + Wb + 8));
     const int kcf = round_up(Nodd, 8) < kDirectTapChunkF ? round_up(Nodd, 8) : kDirectTapChunkF;
     const size_t full_end = (size_t)dl->offK + (size_t)4 * kcf;
+    if (nc == 1 && c[0].blk == APX_BLK_TC) {
+        // the tensor-core candidate (tc_block): 1024 bytes of alignment slack, the
+        // segment of 128 + slices - 1 rows of 128 bytes (rounded up to 1024), the
+        // tap slices of 64 rows of 128 bytes; the FP32 window and tap chunk stay
+        // in front for the blocks that run full precision
+        const int ns = tcb_kslices(Nodd);
+        dl->padS = tcb_kshift(Nodd);
+        dl->nS = ns;
+        dl->offS = (int)al16(full_end);
+        dl->offT = dl->offKb = 0;
+        return (size_t)dl->offS + 1024 + (size_t)round_up((128 + ns - 1) * 128, 1024) + (size_t)ns * 8192;
+    }
     if (full64) {  // the window and every tap as FP64, behind the FP32 region
         const int nkb = round_up(Nodd, 4);
         dl->offS = (int)al16(full_end);
@@ -449,7 +471,18 @@ int make_params(const float* s, int64_t L, const float* k, int32_t N, int32_t Wb
     p.full64 = (mode & APX_FULL_FP64) ? 1 : 0;
     p.thr = target_thr(snr_db, pl.W);  // Section IV.D minimum with the model margin
     int nc = 0;
-    if (sel_kind == 0) {
+    if (sel_kind == 0 && (mode & 0xF0u) == APX_CORE_TC) {
+        // the tensor-core candidate at the largest S_q = K_q its bound admits
+        const int Q = qmax_direct(APX_BLK_TC, pl.Nodd);
+        if (Q >= 1) {
+            Cand c = make_cand(APX_BLK_TC, Q, Q, pl.Nodd, Wb);
+            c.M = 1;
+            c.b = 0;  // no packing: integers, not digits
+            c.sc = 0;
+            p.cand[nc++] = c;
+        }
+        if (prune) nc = prune_unreachable(p.cand, nc, p.thr);
+    } else if (sel_kind == 0) {
         const int order[3] = {APX_BLK_SYM, APX_BLK_ASYM3, APX_BLK_ASYM2};  // Table 1 ranking
         for (int j = 0; j < 3; ++j) {
             int Q = pl.fft ? qmax_fft(order[j], pl.Nodd, Wb) : qmax_direct(order[j], pl.Nodd);
@@ -608,6 +641,7 @@ struct BatchPlan {
     struct Group {
         int fft, Wb;
         int packed;  // whether its requests keep packing candidates (their buffers set the shared memory)
+        int tc;      // tensor-core candidate (a kernel instantiation of its own)
         std::vector<int> reqs;
         size_t smem = 0;
         std::vector<int> start_blk, start_spec, start_comb;  // CTA offsets, nreq + 1 each
@@ -660,14 +694,18 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
     for (int r = 0; r < n; ++r) {
         const Params& p = bp->prm[r];
         const int packed = p.ncand > 0;
+        const int tc = p.ncand == 1 && p.cand[0].blk == APX_BLK_TC;
         int g = -1;
         for (size_t j = 0; j < bp->groups.size(); ++j)
-            if (bp->groups[j].fft == p.fft && bp->groups[j].Wb == p.Wb && bp->groups[j].packed == packed) g = (int)j;
+            if (bp->groups[j].fft == p.fft && bp->groups[j].Wb == p.Wb && bp->groups[j].packed == packed &&
+                bp->groups[j].tc == tc)
+                g = (int)j;
         if (g < 0) {
             bp->groups.emplace_back();
             bp->groups.back().fft = p.fft;
             bp->groups.back().Wb = p.Wb;
             bp->groups.back().packed = packed;
+            bp->groups.back().tc = tc;
             g = (int)bp->groups.size() - 1;
         }
         bp->groups[g].reqs.push_back(r);

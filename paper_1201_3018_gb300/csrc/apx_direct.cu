@@ -6,9 +6,13 @@
 // convolution (Eqs. 8-9) with a register sliding window, digit extraction
 // (Eqs. 11-15), inverse companding (Eq. 16) and the Eq. (17) store.  Blocks
 // without an admissible packing run the FP32 full-precision convolution in the
-// same CTA.
+// same CTA.  With APX_CORE_TC the candidate is the block's companded integers
+// convolved on the tensor cores instead (tc_block below).
+#include <cuda_fp16.h>
+
 #include "apx_block.cuh"
 #include "apx_launch.h"
+#include "apx_umma.cuh"
 
 namespace apx {
 
@@ -103,10 +107,127 @@ __device__ __forceinline__ void conv_f64_full(const double* sig, const double* t
 
 __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
+// ---- the tensor-core candidate (APX_CORE_TC)
+// Eq. (1) on the block's companded integers (Eq. 2) as a product on the
+// tensor cores.  Output j = q R + p of the block (R = kTcbRow phases, q < RB =
+// W_block / R rows) is
+//   r~[j] = sum_x A[q][x] B[p][x],  A[q][x] = s~[q R + x - KN],  B[p][x] = k~[p + KN - x],
+// x < KN + R (s~ zero outside the window, k~ zero outside [0, N')).  Every row
+// of A is a row of one segment S[r][x'] = s~[r R + x' - KN] (x' < R): K slice
+// kt of A is rows kt .. kt+127 of S, so S is written once and each slice's
+// descriptor starts kt rows further in; rows past the block's own are read
+// by the MMA but never read back.  FP16 holds every |s~|, |k~| <= 2048, their
+// products are exact in FP32, and so is every partial sum (N' S_q K_q <= 2^24):
+// the integers are exact, as the packed FP64 forms' are.
+__device__ __forceinline__ uint32_t pack_h2(int a, int b) {
+    return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
+}
+
+__device__ void tc_block(const Params& p, long long i, const BlockGeom& g, const Cand& c, const KStats& ks,
+                         const Pro& pr, float* xs, unsigned char* smem, Shared& sh) {
+    __shared__ __align__(8) unsigned long long s_bar;  // the MMAs' completion
+    __shared__ uint32_t s_tmem;
+    const DirectLayout& dl = p.dl;
+    const int KN = dl.padS, NS = dl.nS, RB = p.Wb / kTcbRow, t = threadIdx.x;
+    const float cs = compand_factor(c.S, pr.Ms);  // Eq. (2)
+    const float ck = compand_factor(c.K, ks.Mk);
+    // 1024-byte-aligned operands: the segment (128 + NS - 1 rows of 128 bytes),
+    // then NS tap slices of 64 rows of 128 bytes, both in the 128-byte swizzle
+    const uint32_t raw = smem_u32(smem + dl.offS);
+    const uint32_t abase = (raw + 1023u) & ~1023u;
+    const uint32_t aspan = ((uint32_t)(128 + NS - 1) * 128u + 1023u) & ~1023u;
+    const uint32_t bbase = abase + aspan;
+    unsigned char* abuf = smem + dl.offS + (abase - raw);
+    unsigned char* bbuf = abuf + aspan;
+    short* kh = reinterpret_cast<short*>(smem + dl.offK);  // the companded taps (the FP32 tap chunk's space)
+    for (int n = t; n < p.Nodd; n += blockDim.x) kh[n] = (short)kq(p, ck, n);
+    for (int ch = t; ch < (RB + NS - 1) * 8; ch += blockDim.x) {
+        const int r = ch >> 3, c16 = ch & 7, t0 = r * kTcbRow + c16 * 8 - KN;
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int ta = t0 + 2 * h, tb = ta + 1;
+            w[h] = pack_h2((ta >= 0 && ta < p.Wb) ? compand(cs, xs[ta]) : 0,
+                           (tb >= 0 && tb < p.Wb) ? compand(cs, xs[tb]) : 0);
+        }
+        *reinterpret_cast<uint4*>(abuf + r * 128 + ((c16 ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();  // the companded taps
+    for (int ch = t; ch < NS * 512; ch += blockDim.x) {
+        const int kt = ch >> 9, ph = (ch >> 3) & 63, c16 = ch & 7;
+        const int n0 = ph + KN - kt * kTcbRow - c16 * 8;  // element x of the chunk is tap n0 - x
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int na = n0 - 2 * h, nb = na - 1;
+            w[h] = pack_h2((na >= 0 && na < p.Nodd) ? kh[na] : 0, (nb >= 0 && nb < p.Nodd) ? kh[nb] : 0);
+        }
+        *reinterpret_cast<uint4*>(bbuf + kt * 8192 + ph * 128 + ((c16 ^ (ph & 7)) << 4)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, visible to the tensor core
+    if (t == 0) {
+        mbar_init(smem_u32(&s_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (t < 32) tmem_alloc(&s_tmem, 64);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (t == 0) {
+        for (int kt = 0; kt < NS; ++kt)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)  // four K = 16 steps of 32 bytes per 128-byte row
+                umma_f16_id(tmem, sdesc_sw128(abase + (uint32_t)kt * 128u + 32u * k),
+                            sdesc_sw128(bbase + (uint32_t)kt * 8192u + 32u * k), umma_idesc_f16(128, kTcbRow),
+                            (kt | k) != 0);
+        umma_commit(smem_u32(&s_bar));
+    }
+    const bool ok = mbar_wait(smem_u32(&s_bar), 0, true);  // bounded: false after about two seconds
+    tc_fence_after();
+    // Accumulator row q (tensor-memory lane q) into the FP32 window's space, now
+    // dead: element (q, x) at q R + (x ^ (q mod 32)), so that the 32 lanes of a
+    // warp, one row each, store to 32 different banks.
+    float* stage = xs;
+    const int warp = t >> 5, lane = t & 31;
+    if (warp < 4 && warp * 32 < RB) {
+        const int q = warp * 32 + lane;
+        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int hx = 0; hx < 2; ++hx) {
+            uint32_t v[32];
+            tmem_ld32_nowait(tw + 32u * hx, v);
+            tmem_wait_ld(v);
+            if (q < RB) {
+#pragma unroll
+                for (int x = 0; x < 32; ++x) stage[q * kTcbRow + ((hx * 32 + x) ^ (q & 31))] = __uint_as_float(v[x]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (t < 32) tmem_free(tmem, 64);
+    if (!ok && t == 0) atomicOr(p.status, 2u);  // timed out: the block's outputs are not valid
+    if (t == 0) sh.bcast[0] = 1.0 / ((double)cs * (double)ck);
+    __syncthreads();
+    const float inv = (float)sh.bcast[0];
+    // Inverse compand (Eq. 16), place (Eq. 17).
+    for (int j = g.lo + t; j < g.hi; j += blockDim.x) {
+        const long long o = g.start + j;
+        if (o < 0 || o >= p.out_len) continue;
+        const int q = j / kTcbRow;
+        const long long rt = (long long)stage[q * kTcbRow + ((j % kTcbRow) ^ (q & 31))];  // an exact integer
+        p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
+        if (p.rq) p.rq[o] = (int)rt;
+    }
+    write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
+}
+
 // LIT: the paper-literal symmetric form (APX_LITERAL, single calls only) in
 // an instantiation of its own, so that the other kernels are compiled as if
 // it did not exist.
-template <bool BATCH, bool LIT>
+template <bool BATCH, bool LIT, bool TC>
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
@@ -197,6 +318,10 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     }
 
     const Cand& c = p.cand[ci];
+    if constexpr (TC) {
+        tc_block(p, i, g, c, ks, pr, xs, smem, sh);
+        return;
+    }
     const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
     const float ck = compand_factor(c.K, ks.Mk);
     const double eps = LIT ? c.eps_l : ldexp(1.0, -c.b);
@@ -278,32 +403,47 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
-template <bool BATCH, bool LIT>
+template <bool BATCH, bool LIT, bool TC>
 static cudaError_t direct_attrs() {
     static int attr_dev = -1;
     int dev;
     cudaGetDevice(&dev);
     if (attr_dev == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_direct<BATCH, LIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    // the largest dynamic shared memory beside this instantiation's static
+    // shared memory (227 KB per CTA in all; layouts never ask for more than kMaxSmem)
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_direct<BATCH, LIT, TC>);
+    if (e != cudaSuccess) return e;
+    const int dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(k_direct<BATCH, LIT, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dyn < kMaxSmem ? dyn : kMaxSmem);
     if (e == cudaSuccess) attr_dev = dev;
     return e;
 }
 
+// the tensor-core candidate's instantiation when the call's one candidate is it
+static bool tc_call(const Params& p) { return p.ncand == 1 && p.cand[0].blk == APX_BLK_TC; }
+
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
-    const bool lit = p.ncand == 1 && p.cand[0].literal;
-    cudaError_t e = lit ? direct_attrs<false, true>() : direct_attrs<false, false>();
+    const bool lit = p.ncand == 1 && p.cand[0].literal, tc = tc_call(p);
+    cudaError_t e = lit ? direct_attrs<false, true, false>()
+                        : (tc ? direct_attrs<false, false, true>() : direct_attrs<false, false, false>());
     if (e != cudaSuccess) return e;
     if (p.P <= 0) return cudaSuccess;
     const BatchTab none = {nullptr, nullptr, 0};
-    if (lit) return launch_k(k_direct<false, true>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
-    return launch_k(k_direct<false, false>, dim3((unsigned)p.P), dim3(kDirectThreads), smem, st, false, p, none);
+    const dim3 grid((unsigned)p.P), block(kDirectThreads);
+    if (lit) return launch_k(k_direct<false, true, false>, grid, block, smem, st, false, p, none);
+    if (tc) return launch_k(k_direct<false, false, true>, grid, block, smem, st, false, p, none);
+    return launch_k(k_direct<false, false, false>, grid, block, smem, st, false, p, none);
 }
 
 cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {
-    cudaError_t e = direct_attrs<true, false>();
+    const bool tc = tc_call(any);  // batched groups keep tensor-core requests apart from the others
+    cudaError_t e = tc ? direct_attrs<true, false, true>() : direct_attrs<true, false, false>();
     if (e != cudaSuccess) return e;
     if (ctas <= 0) return cudaSuccess;
-    return launch_k(k_direct<true, false>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
+    if (tc) return launch_k(k_direct<true, false, true>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
+    return launch_k(k_direct<true, false, false>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
 }
 
 }  // namespace apx

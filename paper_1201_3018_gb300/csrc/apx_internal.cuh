@@ -40,7 +40,7 @@ constexpr int kMaxCand = 3;
 
 // One packing candidate (set by the host from N' and W_block).
 struct Cand {
-    int blk;          // APX_BLK_SYM / ASYM2 / ASYM3
+    int blk;          // APX_BLK_SYM / ASYM2 / ASYM3, or APX_BLK_TC (the direct core's tensor-core candidate)
     int M;            // 1 for symmetric, 2 or 3 for asymmetric
     int S, K, b;      // companding ranges and eps = 2^-b
     int sc;           // exponent of the finest digit: b (sym, asym2) or 2b (asym3)
@@ -129,6 +129,19 @@ __host__ __device__ __forceinline__ void pair_entry(int k, int m, int* rank, int
     const int c = k & 7;
     *rank = pair_owner(c); *u = pair_local(c); *t = k >> 3;
 }
+
+// The direct core's tensor-core candidate (APX_CORE_TC): a block's outputs as
+// rows of kTcbRow phases (at most 128 rows, one MMA tile), its companded
+// window as rows of kTcbRow samples behind a shift of KN = kTcbRow
+// ceil((N'-1) / kTcbRow) zeros, the Toeplitz band of its taps in K slices of
+// kTcbRow (KN / kTcbRow + 1 slices).  Exact while |s~|, |k~| <= 2048 (FP16)
+// and N' S_q K_q <= 2^24 (FP32 sums of integers).
+constexpr int kTcbRow = 64;
+constexpr int kTcbMaxSlices = 8;
+constexpr int kTcbQMax = 2048;
+constexpr long long kTcbSumMax = 1LL << 24;
+__host__ __device__ constexpr int tcb_kshift(int Nodd) { return (Nodd - 1 + kTcbRow - 1) / kTcbRow * kTcbRow; }
+__host__ __device__ constexpr int tcb_kslices(int Nodd) { return tcb_kshift(Nodd) / kTcbRow + 1; }
 
 // Several requests in one launch: request r owns CTAs [cta_start[r], cta_start[r+1]).
 struct BatchTab {

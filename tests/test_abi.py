@@ -89,6 +89,37 @@ def test_candidates_forced_and_none(libapx):
         libapx.plan_candidates(5000, 65, 65, libapx.CORE_DIRECT | libapx.PACK_AUTO, 0.0)  # W_block too small
 
 
+@pytest.mark.parametrize("N,Wb,snr", [(64, 1024, 45.0), (1, 512, 30.0), (449, 2048, 40.0), (200, 8192, 55.0),
+                                      (64, 1024, 70.0)])
+def test_tc_candidates_match_oracle(libapx, N, Wb, snr):
+    """The tensor-core core's one candidate: the largest S_q = K_q with
+    N' S_q K_q <= 2^24 and S_q <= 2048, no packing digits (b = 0), left out
+    when its model misses the target even at ratios 1."""
+    got = libapx.plan_candidates(100000, N, Wb, libapx.CORE_TC | libapx.PACK_AUTO, snr)
+    nodd = N if N % 2 else N + 1
+    thr = 10.0 ** ((snr + O.snr_margin_db(Wb - nodd - 1)) / 10.0)
+    Q = O.qmax_direct(O.BLK_TC, nodd)
+    want = [(O.BLK_TC, Q, 0)] if O.snr_model_lin(1.0, 1.0, 1.0, 1.0, Q, Q) >= 0.99 * thr else []
+    assert got == want
+    assert libapx.plan_candidates(100000, N, Wb, libapx.CORE_TC | libapx.PACK_NONE, snr) == []
+
+
+def test_tc_geometry_errors(libapx):
+    """W_block a multiple of 64 up to 8192 (the block's rows fill at most one
+    128-row tile), N' <= 449 (at most eight K slices), automatic or no packing."""
+    for N, Wb, status in ((64, 1000, libapx.APX_ERR_WBLOCK), (64, 16384, libapx.APX_ERR_WBLOCK),
+                          (450, 2048, libapx.APX_ERR_ARG)):
+        with pytest.raises(libapx.ApxError) as e:
+            libapx.plan_candidates(100000, N, Wb, libapx.CORE_TC | libapx.PACK_AUTO, 45.0)
+        assert e.value.status == status
+    with pytest.raises(libapx.ApxError) as e:
+        libapx.plan_candidates(100000, 64, 1024, libapx.CORE_TC | libapx.PACK_ASYM2, 45.0)
+    assert e.value.status == libapx.APX_ERR_ARG
+    assert libapx.plan_candidates(100000, 449, 2048, libapx.CORE_TC | libapx.PACK_AUTO, 30.0)[0][0] == O.BLK_TC
+    P, W = libapx.plan_blocks(100000, 64, 1024, libapx.CORE_TC)  # the direct core's blocks
+    assert (P, W) == libapx.plan_blocks(100000, 64, 1024, libapx.CORE_DIRECT)
+
+
 def test_plan_errors(libapx):
     with pytest.raises(libapx.ApxError) as e:
         libapx.plan_blocks(100, 3, 31, 0)
