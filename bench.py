@@ -470,6 +470,7 @@ def bench_paper_comparison(ctx, dev, flush, stream):
     rbuf = torch.empty(R, n_out, device=dev)
     res = {}
     for name, mode in (("auto_45db", apx.CORE_DIRECT | apx.PACK_AUTO),
+                       ("tc_45db", apx.CORE_TC | apx.PACK_AUTO),
                        ("full_fp64", apx.CORE_DIRECT | apx.PACK_NONE | apx.FULL_FP64),
                        ("full_fp32", apx.CORE_DIRECT | apx.PACK_NONE)):
         items = [dict(s=s, k=k, r=rbuf[j], mode=mode, W_block=case.Wblock, snr_db=45.0) for j in range(R)]
@@ -482,31 +483,56 @@ def bench_paper_comparison(ctx, dev, flush, stream):
         res[name] = {"value": R * n_out / (t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t}
     P, _ = apx.plan_blocks(len(case.s), len(case.k), case.Wblock, apx.CORE_DIRECT)
     st = torch.empty(P * apx.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    ctx.apx_conv(s, k, case.Wblock, apx.CORE_DIRECT | apx.PACK_AUTO, 45.0, rbuf[0], None, st, stream=stream)
-    ctx.apx_sync(stream)
-    modes = np.bincount(np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)["mode"], minlength=6)
-    res["block_modes_45db"] = {"full": int(modes[0]), "sym": int(modes[1]), "asym2": int(modes[2]),
-                               "asym3": int(modes[3])}
-    # SNR of the packed result against the FP32 full-precision twin: global and per block
     ref = torch.empty(n_out, device=dev)
     ctx.apx_conv_full(s, k, case.Wblock, apx.CORE_DIRECT | apx.PACK_NONE, ref, stream=stream)
-    ctx.apx_sync(stream)
-    rr, dd = ref.double(), (rbuf[0].double() - ref.double())
     Wb, Nodd = case.Wblock, len(case.k) | 1
     W = Wb - Nodd - 1
-    per = []
-    for w in range(P):
-        lo, hi = (0, W + Nodd - 1) if w == 0 else (w * W - 2 + Nodd + 1, w * W - 2 + Wb)
-        lo, hi = max(lo, 0), min(hi, n_out)
-        if hi > lo:
-            num, den = float((rr[lo:hi] ** 2).sum()), float((dd[lo:hi] ** 2).sum())
-            if den > 0:
-                per.append(10 * math.log10(num / den))
-    res["snr_vs_full_db"] = float(10 * torch.log10((rr ** 2).sum() / (dd * dd).sum()))
-    res["snr_per_block_db"] = {"min": float(min(per)), "mean": float(np.mean(per)), "blocks": len(per),
-                               "at_or_above_target": int(sum(x >= 45.0 for x in per))}
+
+    def selected(mode):
+        """One call with per-block records: the modes, and the SNR of its result
+        against the FP32 full-precision twin, globally and per block."""
+        ctx.apx_conv(s, k, case.Wblock, mode, 45.0, rbuf[0], None, st, stream=stream)
+        ctx.apx_sync(stream)
+        m = np.bincount(np.frombuffer(st.cpu().numpy().tobytes(), dtype=apx.STATS_DTYPE)["mode"], minlength=7)
+        rr, dd = ref.double(), (rbuf[0].double() - ref.double())
+        per = []
+        for w in range(P):
+            lo, hi = (0, W + Nodd - 1) if w == 0 else (w * W - 2 + Nodd + 1, w * W - 2 + Wb)
+            lo, hi = max(lo, 0), min(hi, n_out)
+            if hi > lo:
+                num, den = float((rr[lo:hi] ** 2).sum()), float((dd[lo:hi] ** 2).sum())
+                if den > 0:
+                    per.append(10 * math.log10(num / den))
+        return m, float(10 * torch.log10((rr ** 2).sum() / (dd * dd).sum())), {
+            "min": float(min(per)), "mean": float(np.mean(per)), "max": float(max(per)), "blocks": len(per),
+            "at_or_above_target": int(sum(x >= 45.0 for x in per))}
+
+    modes, res["snr_vs_full_db"], res["snr_per_block_db"] = selected(apx.CORE_DIRECT | apx.PACK_AUTO)
+    res["block_modes_45db"] = {"full": int(modes[0]), "sym": int(modes[1]), "asym2": int(modes[2]),
+                               "asym3": int(modes[3])}
     res["speedup_packed_vs_full_fp64"] = res["full_fp64"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
     res["speedup_packed_vs_full_fp32"] = res["full_fp32"]["ms_per_step"] / res["auto_45db"]["ms_per_step"]
+    # the tensor-core core: the same blocks, each block's companded integers on the tensor cores
+    modes, snr_g, snr_b = selected(apx.CORE_TC | apx.PACK_AUTO)
+    t_tc = res["tc_45db"]["ms_per_step"]
+    ns = (((Nodd - 1 + 63) // 64) * 64) // 64 + 1     # K slices of 64 taps
+    useful = 2.0 * len(case.k) * n_out * R             # Eq. (1) on the integers, every copy
+    executed = 2.0 * 128 * 64 * 64 * ns * P * R         # M 128 x N 64 x K 64 per slice and block
+    byts = 4.0 * (len(case.s) + n_out) * R              # every copy's input once and its outputs
+    pk = peaks()
+    res["tc_core"] = {
+        "block_modes": {"tc": int(modes[apx.BLK_TC]), "full": int(modes[apx.BLK_FULL])},
+        "snr_vs_full_db": snr_g, "snr_per_block_db": snr_b,
+        "speedup_vs_full_fp32": res["full_fp32"]["ms_per_step"] / t_tc,
+        "speedup_vs_full_fp64": res["full_fp64"]["ms_per_step"] / t_tc,
+        "speedup_vs_packed_fp64": res["auto_45db"]["ms_per_step"] / t_tc,
+        "roofline": {"bound": "hbm", "achieved": byts / (t_tc * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": byts / (t_tc * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     "note": "whole batched call (1024 k_direct launches' worth of blocks in one graph launch)"},
+        "tensor": {"useful_tflops": useful / (t_tc * 1e-3) / 1e12, "executed_tflops": executed / (t_tc * 1e-3) / 1e12,
+                   "peak": float(pk.get("bf16_tflops", 1899.0)),
+                   "frac_executed": executed / (t_tc * 1e-3) / 1e12 / float(pk.get("bf16_tflops", 1899.0)),
+                   "note": "the tensor work is tiny (a 64-tap kernel); the call is bound by memory and latency"}}
     res["copies"] = R
     out["single_conv"] = res
 

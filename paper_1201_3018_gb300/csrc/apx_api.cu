@@ -729,8 +729,9 @@ int plan_batch(const apx_request* reqs, int n, BatchPlan* bp) {
         G.start_comb.push_back(0);
         for (int r : G.reqs) {
             const Params& p = bp->prm[r];
-            if (p.P > 0x7fffffffLL - a) return APX_ERR_ARG;  // one launch's grid: fewer than 2^31 blocks
-            a += (int)p.P;
+            const long long nctas = G.tc ? tcb_ctas(p.P) : p.P;  // the tensor-core kernel takes several blocks per CTA
+            if (nctas > 0x7fffffffLL - a) return APX_ERR_ARG;  // one launch's grid: fewer than 2^31 CTAs
+            a += (int)nctas;
             G.start_blk.push_back(a);
             if (G.fft) {
                 b += spec_ctas(p.Wb);

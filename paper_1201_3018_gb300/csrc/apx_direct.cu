@@ -107,6 +107,44 @@ __device__ __forceinline__ void conv_f64_full(const double* sig, const double* t
 
 __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
+// Full precision (FP32), Eq. (1) over the window, taps staged in shared memory
+// a chunk at a time; a later chunk continues the sums the thread stored for
+// its outputs.  xs: the window behind a zero pad of dl.padF samples.
+__device__ void full_block_f32(const Params& p, long long i, const BlockGeom& g, const Pro& pr, const float* xs,
+                               unsigned char* smem) {
+    const DirectLayout& dl = p.dl;
+    const int nkp = round_up(p.Nodd, kRf);
+    float* kf = reinterpret_cast<float*>(smem + dl.offK);
+    const int nout = g.hi - g.lo;
+    for (int n0 = 0; n0 < nkp; n0 += kKcF) {
+        const int n1 = min(nkp, n0 + kKcF);
+        if (n0 > 0) __syncthreads();  // every thread is done with the previous chunk
+        for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) kf[n - n0] = ktap(p, n);
+        __syncthreads();
+        for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
+            const int j0 = g.lo + ch * kRf;
+            if (!APX_IN_BOUNDS(j0 - n1 >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
+            float acc[kRf];
+#pragma unroll
+            for (int r = 0; r < kRf; ++r) {
+                const long long o = g.start + j0 + r;
+                acc[r] = (n0 > 0 && j0 + r < g.hi && o >= 0 && o < p.out_len) ? p.r[o] : 0.f;
+            }
+            conv_f32<kRf>(xs, kf, n0, n1, j0, acc);
+#pragma unroll
+            for (int r = 0; r < kRf; ++r) {
+                const int j = j0 + r;
+                const long long o = g.start + j;
+                if (j < g.hi && o >= 0 && o < p.out_len) {
+                    p.r[o] = acc[r];
+                    if (p.rq && n1 == nkp) p.rq[o] = 0;
+                }
+            }
+        }
+    }
+    write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+}
+
 // ---- the tensor-core candidate (APX_CORE_TC)
 // Eq. (1) on the block's companded integers (Eq. 2) as a product on the
 // tensor cores.  Output j = q R + p of the block (R = kTcbRow phases, q < RB =
@@ -123,36 +161,32 @@ __device__ __forceinline__ uint32_t pack_h2(int a, int b) {
     return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
 }
 
-__device__ void tc_block(const Params& p, long long i, const BlockGeom& g, const Cand& c, const KStats& ks,
-                         const Pro& pr, float* xs, unsigned char* smem, Shared& sh) {
-    __shared__ __align__(8) unsigned long long s_bar;  // the MMAs' completion
-    __shared__ uint32_t s_tmem;
+// Operand buffers of a CTA (1024-byte aligned, in the 128-byte swizzle): the
+// segment (128 + NS - 1 rows of 128 bytes), then NS tap slices of 64 rows.
+struct TcBufs {
+    uint32_t abase, bbase;  // shared-memory addresses
+    unsigned char *abuf, *bbuf;
+};
+__device__ __forceinline__ TcBufs tc_bufs(const Params& p, unsigned char* smem) {
     const DirectLayout& dl = p.dl;
-    const int KN = dl.padS, NS = dl.nS, RB = p.Wb / kTcbRow, t = threadIdx.x;
-    const float cs = compand_factor(c.S, pr.Ms);  // Eq. (2)
-    const float ck = compand_factor(c.K, ks.Mk);
-    // 1024-byte-aligned operands: the segment (128 + NS - 1 rows of 128 bytes),
-    // then NS tap slices of 64 rows of 128 bytes, both in the 128-byte swizzle
+    TcBufs t;
     const uint32_t raw = smem_u32(smem + dl.offS);
-    const uint32_t abase = (raw + 1023u) & ~1023u;
-    const uint32_t aspan = ((uint32_t)(128 + NS - 1) * 128u + 1023u) & ~1023u;
-    const uint32_t bbase = abase + aspan;
-    unsigned char* abuf = smem + dl.offS + (abase - raw);
-    unsigned char* bbuf = abuf + aspan;
-    short* kh = reinterpret_cast<short*>(smem + dl.offK);  // the companded taps (the FP32 tap chunk's space)
+    t.abase = (raw + 1023u) & ~1023u;
+    const uint32_t aspan = ((uint32_t)(128 + dl.nS - 1) * 128u + 1023u) & ~1023u;
+    t.bbase = t.abase + aspan;
+    t.abuf = smem + dl.offS + (t.abase - raw);
+    t.bbuf = t.abuf + aspan;
+    return t;
+}
+
+// The kernel's Toeplitz slices B[p][x] = k~[p + KN - x] (Eq. 2 on the taps),
+// once per CTA.  The companded taps are staged in the FP32 tap chunk's space.
+__device__ void tc_prepare_taps(const Params& p, const TcBufs& tb, float ck, unsigned char* smem) {
+    const DirectLayout& dl = p.dl;
+    const int KN = dl.padS, NS = dl.nS, t = threadIdx.x;
+    short* kh = reinterpret_cast<short*>(smem + dl.offK);
     for (int n = t; n < p.Nodd; n += blockDim.x) kh[n] = (short)kq(p, ck, n);
-    for (int ch = t; ch < (RB + NS - 1) * 8; ch += blockDim.x) {
-        const int r = ch >> 3, c16 = ch & 7, t0 = r * kTcbRow + c16 * 8 - KN;
-        uint32_t w[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int ta = t0 + 2 * h, tb = ta + 1;
-            w[h] = pack_h2((ta >= 0 && ta < p.Wb) ? compand(cs, xs[ta]) : 0,
-                           (tb >= 0 && tb < p.Wb) ? compand(cs, xs[tb]) : 0);
-        }
-        *reinterpret_cast<uint4*>(abuf + r * 128 + ((c16 ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __syncthreads();  // the companded taps
+    __syncthreads();
     for (int ch = t; ch < NS * 512; ch += blockDim.x) {
         const int kt = ch >> 9, ph = (ch >> 3) & 63, c16 = ch & 7;
         const int n0 = ph + KN - kt * kTcbRow - c16 * 8;  // element x of the chunk is tap n0 - x
@@ -162,29 +196,46 @@ __device__ void tc_block(const Params& p, long long i, const BlockGeom& g, const
             const int na = n0 - 2 * h, nb = na - 1;
             w[h] = pack_h2((na >= 0 && na < p.Nodd) ? kh[na] : 0, (nb >= 0 && nb < p.Nodd) ? kh[nb] : 0);
         }
-        *reinterpret_cast<uint4*>(bbuf + kt * 8192 + ph * 128 + ((c16 ^ (ph & 7)) << 4)) =
+        *reinterpret_cast<uint4*>(tb.bbuf + kt * 8192 + ph * 128 + ((c16 ^ (ph & 7)) << 4)) =
             make_uint4(w[0], w[1], w[2], w[3]);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, visible to the tensor core
-    if (t == 0) {
-        mbar_init(smem_u32(&s_bar), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();  // the tap chunk's space is free again (a full-precision block may use it)
+}
+
+// One block on the tensor cores: the segment of its companded window, the
+// MMAs (completion on bar, phase `parity`), the rows back from tensor memory,
+// Eq. (16) and Eq. (17).
+__device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, const Cand& c, const KStats& ks,
+                              const Pro& pr, float ck, float* xs, const TcBufs& tb, uint32_t tmem, uint32_t bar,
+                              uint32_t parity, Shared& sh) {
+    const DirectLayout& dl = p.dl;
+    const int KN = dl.padS, NS = dl.nS, RB = p.Wb / kTcbRow, t = threadIdx.x;
+    const float cs = compand_factor(c.S, pr.Ms);  // Eq. (2)
+    for (int ch = t; ch < (RB + NS - 1) * 8; ch += blockDim.x) {
+        const int r = ch >> 3, c16 = ch & 7, t0 = r * kTcbRow + c16 * 8 - KN;
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int ta = t0 + 2 * h, tb2 = ta + 1;
+            w[h] = pack_h2((ta >= 0 && ta < p.Wb) ? compand(cs, xs[ta]) : 0,
+                           (tb2 >= 0 && tb2 < p.Wb) ? compand(cs, xs[tb2]) : 0);
+        }
+        *reinterpret_cast<uint4*>(tb.abuf + r * 128 + ((c16 ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    if (t < 32) tmem_alloc(&s_tmem, 64);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, visible to the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s_tmem;
     if (t == 0) {
         for (int kt = 0; kt < NS; ++kt)
 #pragma unroll
             for (int k = 0; k < 4; ++k)  // four K = 16 steps of 32 bytes per 128-byte row
-                umma_f16_id(tmem, sdesc_sw128(abase + (uint32_t)kt * 128u + 32u * k),
-                            sdesc_sw128(bbase + (uint32_t)kt * 8192u + 32u * k), umma_idesc_f16(128, kTcbRow),
+                umma_f16_id(tmem, sdesc_sw128(tb.abase + (uint32_t)kt * 128u + 32u * k),
+                            sdesc_sw128(tb.bbase + (uint32_t)kt * 8192u + 32u * k), umma_idesc_f16(128, kTcbRow),
                             (kt | k) != 0);
-        umma_commit(smem_u32(&s_bar));
+        umma_commit(bar);
     }
-    const bool ok = mbar_wait(smem_u32(&s_bar), 0, true);  // bounded: false after about two seconds
+    const bool ok = mbar_wait(bar, parity, true);  // bounded: false after about two seconds
     tc_fence_after();
     // Accumulator row q (tensor-memory lane q) into the FP32 window's space, now
     // dead: element (q, x) at q R + (x ^ (q mod 32)), so that the 32 lanes of a
@@ -206,28 +257,29 @@ __device__ void tc_block(const Params& p, long long i, const BlockGeom& g, const
         }
     }
     tc_fence_before();
-    __syncthreads();
-    if (t < 32) tmem_free(tmem, 64);
     if (!ok && t == 0) atomicOr(p.status, 2u);  // timed out: the block's outputs are not valid
     if (t == 0) sh.bcast[0] = 1.0 / ((double)cs * (double)ck);
     __syncthreads();
     const float inv = (float)sh.bcast[0];
-    // Inverse compand (Eq. 16), place (Eq. 17).
+    // Inverse compand (Eq. 16), place (Eq. 17).  The integers are exact in FP32
+    // (|r~| <= 2^24): no 64-bit conversion, whose FP64 pipe is slow on this part.
     for (int j = g.lo + t; j < g.hi; j += blockDim.x) {
         const long long o = g.start + j;
         if (o < 0 || o >= p.out_len) continue;
         const int q = j / kTcbRow;
-        const long long rt = (long long)stage[q * kTcbRow + ((j % kTcbRow) ^ (q & 31))];  // an exact integer
-        p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
-        if (p.rq) p.rq[o] = (int)rt;
+        const float v = stage[q * kTcbRow + ((j % kTcbRow) ^ (q & 31))];
+        p.r[o] = __fmul_rn(v, inv);
+        if (p.rq) p.rq[o] = __float2int_rn(v);
     }
-    write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
+    if (p.st && t == 0)  // (the model's FP64 log10 only where a record is written)
+        write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K),
+                    0.0);
 }
 
 // LIT: the paper-literal symmetric form (APX_LITERAL, single calls only) in
 // an instantiation of its own, so that the other kernels are compiled as if
 // it did not exist.
-template <bool BATCH, bool LIT, bool TC>
+template <bool BATCH, bool LIT>
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
@@ -281,47 +333,11 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         return;
     }
     if (ci < 0) {
-        // Full precision (FP32), Eq. (1) over the window, taps staged in
-        // shared memory a chunk at a time; a later chunk continues the sums
-        // the thread stored for its outputs.
-        const int nkp = round_up(p.Nodd, kRf);
-        float* kf = reinterpret_cast<float*>(smem + dl.offK);
-        const int nout = g.hi - g.lo;
-        for (int n0 = 0; n0 < nkp; n0 += kKcF) {
-            const int n1 = min(nkp, n0 + kKcF);
-            if (n0 > 0) __syncthreads();  // every thread is done with the previous chunk
-            for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) kf[n - n0] = ktap(p, n);
-            __syncthreads();
-            for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
-                const int j0 = g.lo + ch * kRf;
-                if (!APX_IN_BOUNDS(j0 - n1 >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
-                float acc[kRf];
-#pragma unroll
-                for (int r = 0; r < kRf; ++r) {
-                    const long long o = g.start + j0 + r;
-                    acc[r] = (n0 > 0 && j0 + r < g.hi && o >= 0 && o < p.out_len) ? p.r[o] : 0.f;
-                }
-                conv_f32<kRf>(xs, kf, n0, n1, j0, acc);
-#pragma unroll
-                for (int r = 0; r < kRf; ++r) {
-                    const int j = j0 + r;
-                    const long long o = g.start + j;
-                    if (j < g.hi && o >= 0 && o < p.out_len) {
-                        p.r[o] = acc[r];
-                        if (p.rq && n1 == nkp) p.rq[o] = 0;
-                    }
-                }
-            }
-        }
-        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        full_block_f32(p, i, g, pr, xs, smem);
         return;
     }
 
     const Cand& c = p.cand[ci];
-    if constexpr (TC) {
-        tc_block(p, i, g, c, ks, pr, xs, smem, sh);
-        return;
-    }
     const float cs = compand_factor(c.S, pr.Ms);                        // Eq. (2)
     const float ck = compand_factor(c.K, ks.Mk);
     const double eps = LIT ? c.eps_l : ldexp(1.0, -c.b);
@@ -399,51 +415,116 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
         if (p.rq) p.rq[o] = (int)rt;
     }
-    if (threadIdx.x == 0)
+    if (p.st && threadIdx.x == 0)
         write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
-template <bool BATCH, bool LIT, bool TC>
-static cudaError_t direct_attrs() {
-    static int attr_dev = -1;
-    int dev;
-    cudaGetDevice(&dev);
-    if (attr_dev == dev) return cudaSuccess;
-    // the largest dynamic shared memory beside this instantiation's static
-    // shared memory (227 KB per CTA in all; layouts never ask for more than kMaxSmem)
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_direct<BATCH, LIT, TC>);
-    if (e != cudaSuccess) return e;
-    const int dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(k_direct<BATCH, LIT, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             dyn < kMaxSmem ? dyn : kMaxSmem);
-    if (e == cudaSuccess) attr_dev = dev;
-    return e;
+// The tensor-core candidate's kernel (APX_CORE_TC): each CTA takes kTcbBlocks
+// consecutive blocks of one request, so that the kernel statistics, the tap
+// slices and the tensor memory are set up once for all of them; every block
+// then runs as in k_direct (window, statistics, Section IV.D selection), on
+// the tensor cores when its candidate is admitted, else in FP32.
+template <bool BATCH>
+__global__ void __launch_bounds__(kDirectThreads, 3) k_direct_tc(const Params p0, const BatchTab bt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    __shared__ unsigned s_feas;
+    __shared__ Params sp;
+    __shared__ __align__(8) unsigned long long s_bar;  // completion of a block's MMAs
+    __shared__ uint32_t s_tmem;
+    const long long c0 = BATCH ? batch_enter(bt, sp) : (long long)blockIdx.x;
+    const Params& p = BATCH ? sp : p0;
+    const DirectLayout& dl = p.dl;
+    float* xs = reinterpret_cast<float*>(smem) + dl.padF;
+    for (int t = threadIdx.x; t < dl.padF; t += blockDim.x) xs[t - dl.padF] = 0.f;
+    for (int t = threadIdx.x; t < kRf; t += blockDim.x) xs[p.Wb + t] = 0.f;
+    const KStats ks = kernel_stats(p, sh);  // Section IV kernel initialisation, once for the CTA's blocks
+    const TcBufs tb = tc_bufs(p, smem);
+    const bool live_k = !ks.bad && ks.Mk > 0.f;
+    const float ck = live_k ? compand_factor(p.cand[0].K, ks.Mk) : 0.f;
+    if (live_k) tc_prepare_taps(p, tb, ck, smem);
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&s_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) tmem_alloc(&s_tmem, 64);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t phase = 0;
+    for (int u = 0; u < kTcbBlocks; ++u) {
+        const long long i = c0 * kTcbBlocks + u;
+        if (i >= p.P) break;  // the same for the whole CTA
+        const BlockGeom g = block_geom(p, i);
+        load_window(p, g, xs);
+        const Pro pr = block_prologue(p, xs, ks, sh);
+        if (pr.kind != 0) {
+            handle_trivial(p, i, g, pr);
+        } else if (!feasible_mask(p, pr.sig2, pr.Ms, ks.sig2k, ks.Mk, &s_feas)) {
+            full_block_f32(p, i, g, pr, xs, smem);
+        } else {
+            tc_block_body(p, i, g, p.cand[0], ks, pr, ck, xs, tb, tmem, smem_u32(&s_bar), phase, sh);
+            phase ^= 1u;
+        }
+        __syncthreads();  // the window's space is read before the next block's window lands
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_free(tmem, 64);
 }
 
-// the tensor-core candidate's instantiation when the call's one candidate is it
+template <typename K>
+static cudaError_t set_smem_attr(K kern, int* attr_dev) {
+    int dev;
+    cudaGetDevice(&dev);
+    if (*attr_dev == dev) return cudaSuccess;
+    // the largest dynamic shared memory beside this kernel's static shared memory
+    // (227 KB per CTA in all; layouts never ask for more than kMaxSmem)
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const int dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn < kMaxSmem ? dyn : kMaxSmem);
+    if (e == cudaSuccess) *attr_dev = dev;
+    return e;
+}
+template <bool BATCH, bool LIT>
+static cudaError_t direct_attrs() {
+    static int attr_dev = -1;
+    return set_smem_attr(k_direct<BATCH, LIT>, &attr_dev);
+}
+template <bool BATCH>
+static cudaError_t direct_tc_attrs() {
+    static int attr_dev = -1;
+    return set_smem_attr(k_direct_tc<BATCH>, &attr_dev);
+}
+
+// the tensor-core kernel when the call's one candidate is the tensor-core one
 static bool tc_call(const Params& p) { return p.ncand == 1 && p.cand[0].blk == APX_BLK_TC; }
 
 cudaError_t launch_direct(const Params& p, size_t smem, cudaStream_t st) {
     const bool lit = p.ncand == 1 && p.cand[0].literal, tc = tc_call(p);
-    cudaError_t e = lit ? direct_attrs<false, true, false>()
-                        : (tc ? direct_attrs<false, false, true>() : direct_attrs<false, false, false>());
+    cudaError_t e = lit ? direct_attrs<false, true>() : (tc ? direct_tc_attrs<false>() : direct_attrs<false, false>());
     if (e != cudaSuccess) return e;
     if (p.P <= 0) return cudaSuccess;
     const BatchTab none = {nullptr, nullptr, 0};
-    const dim3 grid((unsigned)p.P), block(kDirectThreads);
-    if (lit) return launch_k(k_direct<false, true, false>, grid, block, smem, st, false, p, none);
-    if (tc) return launch_k(k_direct<false, false, true>, grid, block, smem, st, false, p, none);
-    return launch_k(k_direct<false, false, false>, grid, block, smem, st, false, p, none);
+    const dim3 block(kDirectThreads);
+    if (lit) return launch_k(k_direct<false, true>, dim3((unsigned)p.P), block, smem, st, false, p, none);
+    if (tc) return launch_k(k_direct_tc<false>, dim3((unsigned)tcb_ctas(p.P)), block, smem, st, false, p, none);
+    return launch_k(k_direct<false, false>, dim3((unsigned)p.P), block, smem, st, false, p, none);
 }
 
+// Batched groups keep tensor-core requests apart from the others; their CTA
+// table counts tcb_ctas(P) CTAs per request.
 cudaError_t launch_direct_batch(const Params& any, const BatchTab& bt, int ctas, size_t smem, cudaStream_t st) {
-    const bool tc = tc_call(any);  // batched groups keep tensor-core requests apart from the others
-    cudaError_t e = tc ? direct_attrs<true, false, true>() : direct_attrs<true, false, false>();
+    const bool tc = tc_call(any);
+    cudaError_t e = tc ? direct_tc_attrs<true>() : direct_attrs<true, false>();
     if (e != cudaSuccess) return e;
     if (ctas <= 0) return cudaSuccess;
-    if (tc) return launch_k(k_direct<true, false, true>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
-    return launch_k(k_direct<true, false, false>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
+    if (tc) return launch_k(k_direct_tc<true>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
+    return launch_k(k_direct<true, false>, dim3(ctas), dim3(kDirectThreads), smem, st, false, any, bt);
 }
 
 }  // namespace apx

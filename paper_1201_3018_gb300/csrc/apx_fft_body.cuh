@@ -260,7 +260,7 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
         p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
         if (p.rq) p.rq[o] = (int)rt;
     }
-    if (threadIdx.x == 0)
+    if (p.st && threadIdx.x == 0)
         write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, sig2k, Mk, c.S, c.K), ferr);
 }
 

@@ -142,6 +142,9 @@ constexpr int kTcbQMax = 2048;
 constexpr long long kTcbSumMax = 1LL << 24;
 __host__ __device__ constexpr int tcb_kshift(int Nodd) { return (Nodd - 1 + kTcbRow - 1) / kTcbRow * kTcbRow; }
 __host__ __device__ constexpr int tcb_kslices(int Nodd) { return tcb_kshift(Nodd) / kTcbRow + 1; }
+// blocks per CTA of the tensor-core kernel (its setup is shared by them)
+constexpr int kTcbBlocks = 8;
+__host__ __device__ constexpr long long tcb_ctas(long long P) { return (P + kTcbBlocks - 1) / kTcbBlocks; }
 
 // Several requests in one launch: request r owns CTAs [cta_start[r], cta_start[r+1]).
 struct BatchTab {
