@@ -211,6 +211,9 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
     const DirectLayout& dl = p.dl;
     const int KN = dl.padS, NS = dl.nS, RB = p.Wb / kTcbRow, t = threadIdx.x;
     const float cs = compand_factor(c.S, pr.Ms);  // Eq. (2)
+    // the Eq. (16) factor (an FP64 division, slow on this part) from the last
+    // thread, which takes no part in the MMA issue, while the operands are built
+    if (t == blockDim.x - 1) sh.bcast[0] = 1.0 / ((double)cs * (double)ck);
     for (int ch = t; ch < (RB + NS - 1) * 8; ch += blockDim.x) {
         const int r = ch >> 3, c16 = ch & 7, t0 = r * kTcbRow + c16 * 8 - KN;
         uint32_t w[4];
@@ -258,7 +261,6 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
     }
     tc_fence_before();
     if (!ok && t == 0) atomicOr(p.status, 2u);  // timed out: the block's outputs are not valid
-    if (t == 0) sh.bcast[0] = 1.0 / ((double)cs * (double)ck);
     __syncthreads();
     const float inv = (float)sh.bcast[0];
     // Inverse compand (Eq. 16), place (Eq. 17).  The integers are exact in FP32
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
 // then runs as in k_direct (window, statistics, Section IV.D selection), on
 // the tensor cores when its candidate is admitted, else in FP32.
 template <bool BATCH>
-__global__ void __launch_bounds__(kDirectThreads, 3) k_direct_tc(const Params p0, const BatchTab bt) {
+__global__ void __launch_bounds__(kDirectThreads, 4) k_direct_tc(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ unsigned s_feas;
