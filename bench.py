@@ -314,7 +314,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
     against the same bank through the FP32 full-precision path (32 calls of
     apx_conv_full with the tuned core and W_block)."""
     import torch
-    from paper_1201_3018_gb300 import apx
+    from paper_1201_3018_gb300 import apx, tune
     s, kb = wl.filterbank()
     F, N = kb.shape
     L = len(s)
@@ -339,7 +339,7 @@ def bench_filterbank(ctx, tuner, dev, steps, flush, stream, pk):
     mma_ms = prof["tc_mma"][0] / max(prof["tc_mma"][1], 1)
     prep_ms = prof["tc_prep"][0] / max(prof["tc_prep"][1], 1)
     ch = tuner.choose(N, apx.OP_CONV, apx.PACK_NONE, 0.0)
-    core = apx.CORE_FFT if ch["core"] == "fft" else apx.CORE_DIRECT
+    core = tune.core_bits(ch["core"])
     yfull = torch.empty(F, out_len, device=dev)
 
     def full():

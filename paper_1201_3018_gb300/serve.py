@@ -126,11 +126,12 @@ class Server:
             c.close()
 
     def choice(self, N, op, target):
+        from . import tune
         apx = self.apx
         if self.tuner is None:
             return 0, apx.CORE_AUTO
         ch = self.tuner.choose(n_bucket(N), op, apx.PACK_AUTO, target)
-        return ch["W_block"], apx.CORE_FFT if ch["core"] == "fft" else apx.CORE_DIRECT
+        return ch["W_block"], tune.core_bits(ch["core"])
 
     def _launch(self, si, batch, s_host, k_host):
         """One apx_conv_batch_host call: the library copies each request's

@@ -56,8 +56,11 @@ def flops_per_output(core: str, N: int, Wb: int, method: str = "full") -> float:
     return per_block / W
 
 
-def candidates(N: int, max_wb: int = 16384):
-    """(core, W_block) pairs that satisfy the block-geometry rules."""
+def candidates(N: int, max_wb: int = 16384, pack: int = 0):
+    """(core, W_block) pairs that satisfy the block-geometry rules.  The
+    tensor-core core ("tc": the direct core's blocks, the companded integers on
+    the tensor cores) serves per-block selection (APX_PACK_AUTO) for kernels of
+    at most 449 taps, W_block a multiple of 64 up to 8192."""
     Nodd = N | 1
     out = []
     wb = 64
@@ -66,8 +69,16 @@ def candidates(N: int, max_wb: int = 16384):
             out.append(("fft", wb))
             if wb <= 8192:
                 out.append(("direct", wb))
+                if pack == 0 and Nodd <= 449 and wb >= 128:
+                    out.append(("tc", wb))
         wb *= 2
     return out
+
+
+def core_bits(core: str) -> int:
+    """The mode bits of a core name the tuner returns."""
+    from . import apx
+    return {"fft": apx.CORE_FFT, "direct": apx.CORE_DIRECT, "tc": apx.CORE_TC}[core]
 
 
 # ---------------------------------------------------------------- measurement
@@ -115,17 +126,19 @@ class Tuner:
         key = self.key(N, op, pack, target)
         if key in self.cache:
             return self.cache[key]
-        cands = candidates(N)
-        ranked = sorted(cands, key=lambda c: flops_per_output(c[0], N, c[1], method))
-        # the model cannot see the relative efficiency of the two cores (nor the
-        # cost of the halo each block reloads), so keep the best few of each
-        picks = [c for c in ranked if c[0] == "fft"][: self.top] + [c for c in ranked if c[0] == "direct"][: self.top]
+        cands = candidates(N, pack=pack)
+        ranked = sorted(cands, key=lambda c: flops_per_output("direct" if c[0] == "tc" else c[0], N, c[1], method))
+        # the model cannot see the relative efficiency of the cores (nor the cost
+        # of the halo each block reloads), so keep the best few of each
+        picks = []
+        for name in ("fft", "direct", "tc"):
+            picks += [c for c in ranked if c[0] == name][: self.top]
         s = torch.from_numpy(workloads.random_signal(workloads.SEED_BASE + 77, self.L, "laplace", 0.1)).cuda()
         k = torch.from_numpy(workloads.random_signal(workloads.SEED_BASE + 78, N, "uniform")).cuda()
         r = torch.empty(self.L + N - 1, device="cuda")
         measured = []
         for core, Wb in picks:
-            mode = op | (apx.CORE_FFT if core == "fft" else apx.CORE_DIRECT) | pack
+            mode = op | core_bits(core) | pack
             try:
                 ms = self._time(s, k, r, Wb, mode, target)
             except apx.ApxError:
@@ -153,7 +166,7 @@ def batch_items(case, tuner, device, op: int = 0, pack: int | None = None, tenso
     items = []
     for i, (s, k, t) in enumerate(zip(case.signals, case.kernels, case.targets)):
         ch = tuner.choose(len(k), op, pack, t)
-        core = apx.CORE_FFT if ch["core"] == "fft" else apx.CORE_DIRECT
+        core = core_bits(ch["core"])
         if tensors is None:
             sd, kd = torch.from_numpy(s).to(device), torch.from_numpy(k).to(device)
         else:

@@ -57,7 +57,12 @@ def test_generalised_model_at_table1_block():
 
 
 def test_candidates_respect_geometry():
-    for N in (1, 64, 800, 8192):
-        for core, Wb in tune.candidates(N):
+    for N in (1, 64, 449, 800, 8192):
+        cands = tune.candidates(N)
+        for core, Wb in cands:
             assert Wb & (Wb - 1) == 0 and Wb - (N | 1) - 1 >= 2
             assert core == "fft" or Wb <= 8192
+            if core == "tc":  # the tensor-core core's own limits
+                assert (N | 1) <= 449 and Wb % 64 == 0
+        assert any(c == "tc" for c, _ in cands) == ((N | 1) <= 449)
+        assert not any(c == "tc" for c, _ in tune.candidates(N, pack=0x100))  # per-block selection only
