@@ -77,6 +77,8 @@ struct apx_ctx {
     size_t hstage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;     // last upload from hstage
     int tw_wb = 0;          // W_block the twiddle tables were built for
+    const void* res_ptr = nullptr;  // the pointer device_resident last classified
+    bool res_dev = false;
     unsigned epoch = 0;     // FFT-core call number (claims of on-demand spectra)
     unsigned long long tickets = 0;  // CTA tickets handed out by fused launches (the device counter's value)
     int stall_next = 0;     // test hook: pre-claim the next call's packed spectra
@@ -542,6 +544,20 @@ cudaError_t copy_stream_begin(apx_ctx* ctx, cudaStream_t st) {
 }
 
 // Shared body of apx_conv / apx_conv_fixed / apx_conv_full.
+// Whether p is device memory of the context's device (the last answer is kept
+// per pointer: the query costs host time on every call).
+bool device_resident(apx_ctx* ctx, const void* ptr) {
+    if (ptr == ctx->res_ptr) return ctx->res_dev;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    ctx->res_ptr = ptr;
+    ctx->res_dev = a.type == cudaMemoryTypeDevice && a.device == ctx->device;
+    return ctx->res_dev;
+}
+
 int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int32_t Wb, uint32_t mode,
         int sel_kind /*0 auto, 1 fixed, 2 none*/, double snr_db, int S, int K, float* r, int32_t* rq,
         apx_block_stats* st, cudaStream_t stream, cudaEvent_t before_blocks = nullptr) {
@@ -570,6 +586,9 @@ int run(apx_ctx* ctx, const float* s, int64_t L, const float* k, int32_t N, int3
     for (int j = 0; j < nc; ++j) p.cand[j].H = (double2*)ctx->Hc[j].p;
     set_flag_ptrs(p, (unsigned*)ctx->flags.p);
     p.fused = use_fused(p, stream);
+    // the spectrum launch prefetches a device-resident signal into L2 (not one
+    // still being copied in: its copy is waited for only before the blocks)
+    p.pf = pl.fft && !p.fused && !before_blocks && device_resident(ctx, s);
     if (pl.fft && !p.fused && fft_full_only(p)) {  // the two-CTA block kernel: its staging-order spectrum
         rc = ensure(ctx, ctx->Hpair, pair_table_bytes(Wb));
         if (rc) return rc;

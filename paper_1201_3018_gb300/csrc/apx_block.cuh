@@ -31,25 +31,111 @@ __device__ __forceinline__ BlockGeom block_geom(const Params& p, long long i) {
     return g;
 }
 
-// Coalesced window load into shared memory, zeros outside [0, L); pairs of
-// samples per load when the window start is 8-byte aligned (W_block and the
-// block origins are even).
+// Elements from a up to its next 16-byte boundary (FP32 and int32 arrays are
+// 4-byte aligned).
+__device__ __forceinline__ int head16(const void* a) {
+    return (int)((4u - ((uint32_t)reinterpret_cast<uintptr_t>(a) >> 2)) & 3u);
+}
+
+// Coalesced window load into shared memory (xs 16-byte aligned), zeros
+// outside [0, L).  Where the window starts on an even sample of the signal
+// (W_block and the block origins are even), 16-byte loads between the
+// signal's 16-byte boundaries: with the boundary h = 0 samples in, 16-byte
+// shared-memory stores; with h = 2 (a block origin wW - 2 with W a multiple of
+// 4), two 8-byte stores, lanes 8 .. 15 and 24 .. 31 of a warp storing their
+// halves in the other order so that each store hits every bank at most twice
+// (256 bytes in two wavefronts); the samples before the first boundary and
+// after the last one one at a time.  Otherwise single samples.
 __device__ __forceinline__ void load_window(const Params& p, const BlockGeom& g, float* xs) {
     const float* __restrict__ s = p.s;
-    const bool aligned = ((reinterpret_cast<uintptr_t>(s + g.start) & 7u) == 0);
-    for (int t = 2 * threadIdx.x; t < p.Wb; t += 2 * blockDim.x) {
-        const long long gi = g.start + t;
-        float2 v;
-        if (aligned && gi >= 0 && gi + 1 < p.L) {
-            v = APX_LD_IN(reinterpret_cast<const float2*>(s + gi));
-        } else {
-            v.x = (gi >= 0 && gi < p.L) ? APX_LD_IN(&s[gi]) : 0.f;
-            v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? APX_LD_IN(&s[gi + 1]) : 0.f;
+    const int h = head16(s + g.start);
+    if ((h & 1) == 0) {
+        const int nq = (p.Wb - h) >> 2, tail = h + 4 * nq;
+        const bool swap = (threadIdx.x & 8) != 0;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const int t = h + 4 * q;
+            const long long gi = g.start + t;
+            float4 v;
+            if (gi >= 0 && gi + 3 < p.L) {
+                v = APX_LD_IN(reinterpret_cast<const float4*>(s + gi));
+            } else {
+                v.x = (gi >= 0 && gi < p.L) ? APX_LD_IN(&s[gi]) : 0.f;
+                v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? APX_LD_IN(&s[gi + 1]) : 0.f;
+                v.z = (gi + 2 >= 0 && gi + 2 < p.L) ? APX_LD_IN(&s[gi + 2]) : 0.f;
+                v.w = (gi + 3 >= 0 && gi + 3 < p.L) ? APX_LD_IN(&s[gi + 3]) : 0.f;
+            }
+            if (h == 0) {
+                *reinterpret_cast<float4*>(xs + t) = v;
+            } else {
+                const float2 a = make_float2(v.x, v.y), b = make_float2(v.z, v.w);
+                *reinterpret_cast<float2*>(xs + t + (swap ? 2 : 0)) = swap ? b : a;
+                *reinterpret_cast<float2*>(xs + t + (swap ? 0 : 2)) = swap ? a : b;
+            }
         }
-        xs[t] = v.x;
-        xs[t + 1] = v.y;
+        if ((int)threadIdx.x < h + (p.Wb - tail)) {  // at most 2 + 3 samples
+            const int t = (int)threadIdx.x < h ? (int)threadIdx.x : tail + ((int)threadIdx.x - h);
+            const long long gi = g.start + t;
+            xs[t] = (gi >= 0 && gi < p.L) ? APX_LD_IN(&s[gi]) : 0.f;
+        }
+    } else {
+        for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) {
+            const long long gi = g.start + t;
+            xs[t] = (gi >= 0 && gi < p.L) ? APX_LD_IN(&s[gi]) : 0.f;
+        }
     }
     __syncthreads();
+}
+
+// Eq. (17) on a whole CTA: output j of the block, kept where g.lo <= j < g.hi
+// and 0 <= g.start + j < out_len, is out(j, rq_j) (rq_j: its integer, where
+// integers are asked for).  The kept outputs go out as 16-byte stores between
+// the 16-byte boundaries of r, one by one at the ragged ends.  ONE: a single
+// inlined copy of out (a long unpacking) in a loop over the four outputs.
+template <bool ONE = false, class F>
+__device__ __forceinline__ void store_kept(const Params& p, const BlockGeom& g, F out) {
+    const long long olo = g.start + g.lo > 0 ? g.start + g.lo : 0;
+    const long long ohi = g.start + g.hi < p.out_len ? g.start + g.hi : p.out_len;
+    if (olo >= ohi) return;
+    const long long oa = olo + head16(p.r + olo) < ohi ? olo + head16(p.r + olo) : ohi;
+    const int nq = (int)((ohi - oa) >> 2);
+    const long long ot = oa + 4ll * nq;
+    const bool rq4 = p.rq && head16(p.rq + oa) == 0;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const long long o = oa + 4ll * q;
+        const int j = (int)(o - g.start);
+        float4 v;
+        int4 iv;
+        if (ONE) {
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                int ic;
+                const float x = out(j + c, ic);
+                v.x = c == 0 ? x : v.x; iv.x = c == 0 ? ic : iv.x;
+                v.y = c == 1 ? x : v.y; iv.y = c == 1 ? ic : iv.y;
+                v.z = c == 2 ? x : v.z; iv.z = c == 2 ? ic : iv.z;
+                v.w = c == 3 ? x : v.w; iv.w = c == 3 ? ic : iv.w;
+            }
+        } else {
+            v.x = out(j, iv.x);
+            v.y = out(j + 1, iv.y);
+            v.z = out(j + 2, iv.z);
+            v.w = out(j + 3, iv.w);
+        }
+        *reinterpret_cast<float4*>(p.r + o) = v;
+        if (rq4) {
+            *reinterpret_cast<int4*>(p.rq + o) = iv;
+        } else if (p.rq) {
+            p.rq[o] = iv.x; p.rq[o + 1] = iv.y; p.rq[o + 2] = iv.z; p.rq[o + 3] = iv.w;
+        }
+    }
+    const int nh = (int)(oa - olo), nt = (int)(ohi - ot);
+    if ((int)threadIdx.x < nh + nt) {  // at most 3 + 3 outputs
+        const long long o = (int)threadIdx.x < nh ? olo + threadIdx.x : ot + ((int)threadIdx.x - nh);
+        int iv;
+        const float v = out((int)(o - g.start), iv);
+        p.r[o] = v;
+        if (p.rq) p.rq[o] = iv;
+    }
 }
 
 struct Shared {
@@ -171,12 +257,7 @@ __device__ inline long long kbar_l1(const Params& p, const Cand& c, float ck, Sh
 
 // Fill every kept output of the block with `v` (zero block or non-finite).
 __device__ __forceinline__ void store_constant(const Params& p, const BlockGeom& g, float v) {
-    for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
-        long long o = g.start + j;
-        if (o < 0 || o >= p.out_len) continue;
-        p.r[o] = v;
-        if (p.rq) p.rq[o] = 0;
-    }
+    store_kept(p, g, [v](int, int& iv) { iv = 0; return v; });
 }
 
 __device__ __forceinline__ void write_stats(const Params& p, long long i, int mode, const Cand* c, float cs,

@@ -107,6 +107,29 @@ __device__ __forceinline__ void conv_f64_full(const double* sig, const double* t
 
 __device__ __forceinline__ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
+// A thread's run of R outputs j0 .. j0+R-1 (R a multiple of 4) goes out as
+// 16-byte stores when it is kept whole and starts on a 16-byte boundary of r.
+template <int R>
+__device__ __forceinline__ bool run_vec(const Params& p, const BlockGeom& g, int j0) {
+    const long long o = g.start + j0;
+    return j0 + R <= g.hi && o >= 0 && o + R <= p.out_len && head16(p.r + o) == 0;
+}
+template <int R>
+__device__ __forceinline__ void store_run(const Params& p, long long o, const float (&v)[R], bool zero_rq) {
+#pragma unroll
+    for (int r = 0; r < R; r += 4)
+        *reinterpret_cast<float4*>(p.r + o + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+    if (zero_rq) {
+        if (head16(p.rq + o) == 0) {
+#pragma unroll
+            for (int r = 0; r < R; r += 4) *reinterpret_cast<int4*>(p.rq + o + r) = make_int4(0, 0, 0, 0);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) p.rq[o + r] = 0;
+        }
+    }
+}
+
 // Full precision (FP32), Eq. (1) over the window, taps staged in shared memory
 // a chunk at a time; a later chunk continues the sums the thread stored for
 // its outputs.  xs: the window behind a zero pad of dl.padF samples.
@@ -124,20 +147,34 @@ __device__ void full_block_f32(const Params& p, long long i, const BlockGeom& g,
         for (int ch = threadIdx.x; ch * kRf < nout; ch += blockDim.x) {
             const int j0 = g.lo + ch * kRf;
             if (!APX_IN_BOUNDS(j0 - n1 >= -dl.padF && j0 + kRf <= p.Wb + 8, p.status)) continue;
+            const bool vec = run_vec<kRf>(p, g, j0);
             float acc[kRf];
+            if (vec) {
 #pragma unroll
-            for (int r = 0; r < kRf; ++r) {
-                const long long o = g.start + j0 + r;
-                acc[r] = (n0 > 0 && j0 + r < g.hi && o >= 0 && o < p.out_len) ? p.r[o] : 0.f;
+                for (int r = 0; r < kRf; r += 4) {
+                    const float4 a = n0 > 0 ? *reinterpret_cast<const float4*>(p.r + g.start + j0 + r)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    acc[r] = a.x; acc[r + 1] = a.y; acc[r + 2] = a.z; acc[r + 3] = a.w;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kRf; ++r) {
+                    const long long o = g.start + j0 + r;
+                    acc[r] = (n0 > 0 && j0 + r < g.hi && o >= 0 && o < p.out_len) ? p.r[o] : 0.f;
+                }
             }
             conv_f32<kRf>(xs, kf, n0, n1, j0, acc);
+            if (vec) {
+                store_run<kRf>(p, g.start + j0, acc, p.rq && n1 == nkp);
+            } else {
 #pragma unroll
-            for (int r = 0; r < kRf; ++r) {
-                const int j = j0 + r;
-                const long long o = g.start + j;
-                if (j < g.hi && o >= 0 && o < p.out_len) {
-                    p.r[o] = acc[r];
-                    if (p.rq && n1 == nkp) p.rq[o] = 0;
+                for (int r = 0; r < kRf; ++r) {
+                    const int j = j0 + r;
+                    const long long o = g.start + j;
+                    if (j < g.hi && o >= 0 && o < p.out_len) {
+                        p.r[o] = acc[r];
+                        if (p.rq && n1 == nkp) p.rq[o] = 0;
+                    }
                 }
             }
         }
@@ -157,6 +194,14 @@ __device__ void full_block_f32(const Params& p, long long i, const BlockGeom& g,
 // by the MMA but never read back.  FP16 holds every |s~|, |k~| <= 2048, their
 // products are exact in FP32, and so is every partial sum (N' S_q K_q <= 2^24):
 // the integers are exact, as the packed FP64 forms' are.
+// Column of accumulator element (q, x) in the staging rows of 64 FP32 values:
+// the 32 lanes of a warp writing one row each (q = lane, x fixed) hit 32
+// different banks, and the 32 lanes reading four consecutive outputs each
+// (x = 4 lane + c over two rows) at most two to a bank, none when the warp's
+// first output starts a row.  x ^ (q mod 32) spreads the rows; bit 5 of x,
+// moved to bit 1, separates x from x + 32 within a row.
+__device__ __forceinline__ int tc_stage_col(int q, int x) { return x ^ (q & 31) ^ ((x >> 4) & 2); }
+
 __device__ __forceinline__ uint32_t pack_h2(int a, int b) {
     return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
 }
@@ -241,8 +286,7 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
     const bool ok = mbar_wait(bar, parity, true);  // bounded: false after about two seconds
     tc_fence_after();
     // Accumulator row q (tensor-memory lane q) into the FP32 window's space, now
-    // dead: element (q, x) at q R + (x ^ (q mod 32)), so that the 32 lanes of a
-    // warp, one row each, store to 32 different banks.
+    // dead, at the columns tc_stage_col gives.
     float* stage = xs;
     const int warp = t >> 5, lane = t & 31;
     if (warp < 4 && warp * 32 < RB) {
@@ -255,7 +299,7 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
             tmem_wait_ld(v);
             if (q < RB) {
 #pragma unroll
-                for (int x = 0; x < 32; ++x) stage[q * kTcbRow + ((hx * 32 + x) ^ (q & 31))] = __uint_as_float(v[x]);
+                for (int x = 0; x < 32; ++x) stage[q * kTcbRow + tc_stage_col(q, hx * 32 + x)] = __uint_as_float(v[x]);
             }
         }
     }
@@ -265,14 +309,12 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
     const float inv = (float)sh.bcast[0];
     // Inverse compand (Eq. 16), place (Eq. 17).  The integers are exact in FP32
     // (|r~| <= 2^24): no 64-bit conversion, whose FP64 pipe is slow on this part.
-    for (int j = g.lo + t; j < g.hi; j += blockDim.x) {
-        const long long o = g.start + j;
-        if (o < 0 || o >= p.out_len) continue;
+    store_kept(p, g, [&](int j, int& iv) {
         const int q = j / kTcbRow;
-        const float v = stage[q * kTcbRow + ((j % kTcbRow) ^ (q & 31))];
-        p.r[o] = __fmul_rn(v, inv);
-        if (p.rq) p.rq[o] = __float2int_rn(v);
-    }
+        const float v = stage[q * kTcbRow + tc_stage_col(q, j % kTcbRow)];
+        iv = __float2int_rn(v);
+        return __fmul_rn(v, inv);
+    });
     if (p.st && t == 0)  // (the model's FP64 log10 only where a record is written)
         write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K),
                     0.0);
@@ -321,13 +363,20 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
             const int j0 = g.lo + ch * kRd;
             double acc[kRd];
             conv_f64_full<kRd>(sd, kd, nkp, j0, acc);
+            float accf[kRd];
 #pragma unroll
-            for (int r = 0; r < kRd; ++r) {
-                const int j = j0 + r;
-                const long long o = g.start + j;
-                if (j < g.hi && o >= 0 && o < p.out_len) {
-                    p.r[o] = __double2float_rn(acc[r]);
-                    if (p.rq) p.rq[o] = 0;
+            for (int r = 0; r < kRd; ++r) accf[r] = __double2float_rn(acc[r]);
+            if (run_vec<kRd>(p, g, j0)) {
+                store_run<kRd>(p, g.start + j0, accf, p.rq != nullptr);
+            } else {
+#pragma unroll
+                for (int r = 0; r < kRd; ++r) {
+                    const int j = j0 + r;
+                    const long long o = g.start + j;
+                    if (j < g.hi && o >= 0 && o < p.out_len) {
+                        p.r[o] = accf[r];
+                        if (p.rq) p.rq[o] = 0;
+                    }
                 }
             }
         }
@@ -408,15 +457,13 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
     __syncthreads();
     const float inv = (float)sh.bcast[0];
     auto Tat = [&](int m) { return scaled(tb[m], c.sc); };
-    for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
-        const long long o = g.start + j;
-        if (o < 0 || o >= p.out_len) continue;
-        long long rt = LIT                      ? unpack_sym_literal(c, j, g.wstart, tb)
-                       : c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat)
-                                              : unpack_asym(c, j, Ls, nr, Tat);
-        p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
-        if (p.rq) p.rq[o] = (int)rt;
-    }
+    store_kept<false>(p, g, [&](int j, int& iv) {
+        const long long rt = LIT                    ? unpack_sym_literal(c, j, g.wstart, tb)
+                             : c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat)
+                                                    : unpack_asym(c, j, Ls, nr, Tat);
+        iv = (int)rt;
+        return __fmul_rn(__ll2float_rn(rt), inv);
+    });
     if (p.st && threadIdx.x == 0)
         write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }

@@ -18,20 +18,55 @@ __device__ __forceinline__ bool pair_ok(const Params& p, int i) { return threadI
 
 template <int kVals>
 __device__ __forceinline__ void load_window_regs(const Params& p, long long start, float (&xv)[kVals]) {
+    static_assert(kVals % 4 == 0, "runs in couples");
     const bool aligned = ((reinterpret_cast<uintptr_t>(p.s + start) & 7u) == 0);
-#pragma unroll
-    for (int i = 0; i < kVals / 2; ++i) {
-        xv[2 * i] = 0.f;
-        xv[2 * i + 1] = 0.f;
+    const int nt = (int)blockDim.x, t = (int)threadIdx.x;
+    auto pair_at = [&](int i) {  // pair t + i nt, one thread alone
+        float2 v = make_float2(0.f, 0.f);
         if (pair_ok(p, i)) {
-            const long long gi = start + 2ll * (threadIdx.x + i * blockDim.x);
-            float2 v;
+            const long long gi = start + 2ll * (t + i * nt);
             if (aligned && gi >= 0 && gi + 1 < p.L) {
                 v = APX_LD_IN(reinterpret_cast<const float2*>(p.s + gi));
             } else {
                 v.x = (gi >= 0 && gi < p.L) ? APX_LD_IN(p.s + gi) : 0.f;
                 v.y = (gi + 1 >= 0 && gi + 1 < p.L) ? APX_LD_IN(p.s + gi + 1) : 0.f;
             }
+        }
+        return v;
+    };
+    // 16-byte loads when every run of the warp starts on a 16-byte boundary of
+    // the signal and lies inside the window and the signal (warp-uniform):
+    // lanes 2c and 2c + 1 form a couple; of runs 2a and 2a + 1, the even lane
+    // loads run 2a for both, the odd lane run 2a + 1, and each passes the
+    // other its half by a shuffle.  Runs 8 bytes off a boundary take 8-byte
+    // loads, which cover them in as few instructions.
+    constexpr int kRuns = kVals / 2;
+    const int lane = t & 31, pw = t - lane;
+    const long long gw = start + 2ll * pw;
+    const bool vec = ((reinterpret_cast<uintptr_t>(p.s + gw) & 15u) == 0) && pw + 31 + (kRuns - 1) * nt < p.Wb / 2 &&
+                     gw >= 0 && gw + 2ll * (kRuns - 1) * nt + 63 < p.L;
+    if (vec) {
+        const bool even = (lane & 1) == 0;
+        const float* b = p.s + start + 2ll * t;  // this thread's pair of run 0
+#pragma unroll
+        for (int a = 0; a < kRuns / 2; ++a) {
+            const float4 w = APX_LD_IN(reinterpret_cast<const float4*>(even ? b + 4 * a * nt
+                                                                             : b + 2 * (2 * a + 1) * nt - 2));
+            const float2 mine = even ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
+            const float2 other = even ? make_float2(w.z, w.w) : make_float2(w.x, w.y);
+            float2 got;
+            got.x = __shfl_xor_sync(0xffffffffu, other.x, 1);
+            got.y = __shfl_xor_sync(0xffffffffu, other.y, 1);
+            const float2 v0 = even ? mine : got, v1 = even ? got : mine;
+            xv[4 * a] = v0.x;
+            xv[4 * a + 1] = v0.y;
+            xv[4 * a + 2] = v1.x;
+            xv[4 * a + 3] = v1.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kRuns; ++i) {
+            const float2 v = pair_at(i);
             xv[2 * i] = v.x;
             xv[2 * i + 1] = v.y;
         }
@@ -148,13 +183,10 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
         // Full precision: finish the FP32 real-FFT convolution.
         spectral_multiply(Zf, mf, static_cast<const float2*>(p.Hfull), p.tw32, p.ntab / p.Wb, true, p.status);
         fft_smem<float2, true>(Zf, mf, p.tw32, p.ntab, p.status);
-        for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
-            const long long o = g.start + j;
-            if (o < 0 || o >= p.out_len) continue;
-            if (!APX_IN_BOUNDS(j >= 0 && j < p.Wb, p.status)) continue;
-            p.r[o] = word<float>(Zf, j);
-            if (p.rq) p.rq[o] = 0;
-        }
+        store_kept(p, g, [&](int j, int& iv) {
+            iv = 0;
+            return APX_IN_BOUNDS(j >= 0 && j < p.Wb, p.status) ? word<float>(Zf, j) : 0.f;
+        });
         write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, Ms, sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
         return;
     }
@@ -253,13 +285,11 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
     __syncthreads();
     const float inv = (float)sh.bcast[2];
     auto Tat = [&](int idx) { return scaled(word<double>(Z, idx), c.sc); };
-    for (int j = g.lo + threadIdx.x; j < g.hi; j += blockDim.x) {
-        const long long o = g.start + j;
-        if (o < 0 || o >= p.out_len) continue;
-        long long rt = c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat) : unpack_asym(c, j, Ls, nr, Tat);
-        p.r[o] = __fmul_rn(__ll2float_rn(rt), inv);
-        if (p.rq) p.rq[o] = (int)rt;
-    }
+    store_kept<true>(p, g, [&](int j, int& iv) {
+        const long long rt = c.blk == APX_BLK_SYM ? unpack_sym(c, j, g.wstart, Tat) : unpack_asym(c, j, Ls, nr, Tat);
+        iv = (int)rt;
+        return __fmul_rn(__ll2float_rn(rt), inv);
+    });
     if (p.st && threadIdx.x == 0)
         write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, sig2k, Mk, c.S, c.K), ferr);
 }

@@ -76,6 +76,7 @@ struct Params {
     long long L;
     const float* k;       // kernel taps as given (the template for cross-correlation)
     int N, Nodd, Wb, W, head, fft, xcorr;
+    int pf;               // FFT core, single call with the spectrum launches: k_spec prefetches the signal into L2
     long long P, out_len;
     float* r;             // output, out_len
     int* rq;              // integer-domain output or null

@@ -13,6 +13,27 @@
 
 namespace apx {
 
+// The signal's bytes, a slice per CTA, into L2 while the kernel preparation
+// runs (the block kernel reads every sample, most of them twice): the first
+// warp issues bulk L2 prefetches of up to 64 KB between the slice's 16-byte
+// boundaries, inside the signal.  Nothing waits for them.
+__device__ __forceinline__ void prefetch_signal(const Params& p) {
+    if (threadIdx.x >= 32) return;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p.s), e = a + 4ull * (uintptr_t)p.L;
+    const uintptr_t lo = (a + 15u) & ~(uintptr_t)15u, hi = e & ~(uintptr_t)15u;
+    if (hi <= lo) return;
+    const uintptr_t per = (((hi - lo) + gridDim.x - 1) / gridDim.x + 15u) & ~(uintptr_t)15u;
+    const uintptr_t s0 = lo + per * blockIdx.x, s1 = s0 + per < hi ? s0 + per : hi;
+    constexpr uintptr_t kPiece = 64u * 1024u;
+    for (uintptr_t q = s0 + kPiece * threadIdx.x; q < s1; q += kPiece * 32u) {
+        const uint32_t n = (uint32_t)(s1 - q < kPiece ? s1 - q : kPiece);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(
+                         reinterpret_cast<const void*>(q))),
+                     "r"(n)
+                     : "memory");
+    }
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -29,6 +50,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec(const Params p0, const Ba
         p0.claim[threadIdx.x] = p0.claim_init;
         p0.ready[threadIdx.x] = 0u;
     }
+    if (!BATCH && p0.pf) prefetch_signal(p0);
     if (cta == spec_r1(p.Wb)) spec_stats(p, sh);
     else spec_subfft(p, cta, reinterpret_cast<float2*>(smem));
 }

@@ -60,7 +60,21 @@ constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;  // warp 0 TMA, warp 1 MMA, wa
 constexpr uint32_t kTcABytes = kTcM * 128;  // a K slice: one 128-byte row per operand row
 constexpr uint32_t kTcBBytes = kTcN * 128;
 constexpr uint32_t kTcTmemCols = kTcN;
-constexpr uint32_t kTcStageOut = kTcEpiWarps * 4096;  // output staging, 4 KB per epilogue warp
+// Output staging per epilogue warp: kTcStgBufs buffers of kTcStgChunks 4 KB
+// chunks (32 rows x 32 FP32 outputs); a buffer's chunks are written back by one
+// bulk tensor store, and a warp refills a buffer while its other buffers'
+// stores are still reading.
+#ifndef APX_TC_STG_BUFS
+#define APX_TC_STG_BUFS 1
+#endif
+#ifndef APX_TC_STG_CHUNKS
+#define APX_TC_STG_CHUNKS 2
+#endif
+constexpr int kTcStgBufs = APX_TC_STG_BUFS;
+constexpr int kTcStgChunks = APX_TC_STG_CHUNKS;
+static_assert(kTcStgChunks == 1 || kTcStgChunks == 2 || kTcStgChunks == 4, "chunks per store divide P / 32");
+constexpr uint32_t kTcStgWarp = (uint32_t)(kTcStgBufs * kTcStgChunks) * 4096u;
+constexpr uint32_t kTcStageOut = kTcEpiWarps * kTcStgWarp;
 constexpr int kTcABoxRows = 64;                     // resident A: TMA box rows
 constexpr uint32_t kTcABoxBytes = kTcABoxRows * 128;
 constexpr uint32_t kTcIdesc = umma_idesc_f16(kTcM, kTcN);  // FP16 operands, FP32 accumulators, M 128, N 256
@@ -100,8 +114,20 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t sr
         "r"(x), "r"(y), "r"(z), "r"(src)
         : "memory");
 }
-// The bulk stores of this thread have finished reading shared memory.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// The same through the 4-D map of whole rows: box (32 phases, 32 rows, chunks, 1).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int x, int y, int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n\t"
+        "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(z), "r"(w), "r"(src)
+        : "memory");
+}
+// The bulk stores of this thread, all but the N most recent, have finished
+// reading shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
 // ... and their writes are performed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -282,53 +308,73 @@ __global__ void __launch_bounds__(256) k_tc_kern(const float* __restrict__ kb, T
 // 32 accumulator rows in 32-column chunks (chunk ch is columns 32 ch .. 32 ch
 // + 31, kernel fl = ch / (P / 32)), the load of the next chunk in flight while
 // this one is processed; scale by the block's and kernel's (c_s c_k)^-1
-// (Eq. 16); stage the 32 x 32 chunk in the warp's 4 KB buffer in the 128-byte
-// swizzled layout (16-byte slot i of row r at r * 128 + ((i ^ (r & 7)) * 16):
-// conflict-free writes) and write it with one TMA store of the box (columns
-// c .. c + 31 of P, time rows row0 .. row0 + 31, kernel f) of the output map.
-// The map covers the out_len / P whole rows of each kernel, so TMA drops rows
-// past them; the one partial row at the end (out_len % P outputs) is written
-// by its lane with plain stores.
+// (Eq. 16); stage the 32 x 32 chunk in shared memory in the 128-byte swizzled
+// layout (16-byte slot i of row r at r * 128 + ((i ^ (r & 7)) * 16):
+// conflict-free writes).  g.stg_ch consecutive chunks of one kernel fill a
+// staging buffer, written by one TMA store of the box (g.stg_ch = 1: columns c
+// .. c + 31 of P, time rows row0 .. row0 + 31, kernel f, through the 3-D map;
+// otherwise the 4-D map's sub-rows of 32 phases, so that 2 or 4 chunks make
+// whole 256- or 512-byte rows).  The warp's kTcStgBufs buffers rotate (sg
+// counts the warp's stores).  The maps cover the out_len / P whole rows of each
+// kernel, so TMA drops rows past them; the one partial row at the end (out_len
+// % P outputs) is written by its lane with plain stores.
 __device__ __forceinline__ void epilogue_tile(const TcGeom& g, const CUtensorMap* tmY, int64_t blk, int grp,
                                               uint32_t acc0, uint32_t stg, int lane, int lq,
                                               const float* __restrict__ inv_tab, float* __restrict__ y,
-                                              int32_t* __restrict__ yq, unsigned* status) {
+                                              int32_t* __restrict__ yq, unsigned* status, int& sg) {
     const int64_t row0 = blk * kTcM + lq * 32;  // first time row of this warp's quarter
     const int64_t rows_full = g.out_len / g.P;  // rows the output map covers
     const int64_t tail_row = (g.out_len % g.P) ? rows_full : -1;
+    const bool stores = row0 < rows_full;       // the same for every tile after the first that has none
     const uint32_t acc = acc0 + ((uint32_t)(lq * 32) << 16);
     const int nf = g.F - grp * g.G < g.G ? g.F - grp * g.G : g.G;  // kernels of this group
     const float inv_l = lane < nf ? inv_tab[blk * (int64_t)(g.ngroups * g.G) + grp * g.G + lane] : 0.f;
     const int cpk = g.P / 32;  // chunks per kernel
+    const int chg = g.stg_ch;  // chunks per store (divides cpk)
     const int nchunks = nf * cpk;
     uint32_t rn[32];
-    if (!APX_IN_BOUNDS(nchunks * 32 <= kTcN, status)) return;
+    if (!APX_IN_BOUNDS(nchunks * 32 <= kTcN && chg <= kTcStgChunks && cpk % chg == 0, status)) return;
     tmem_ld32_nowait(acc, rn);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int fl = ch / cpk, c = (ch - fl * cpk) * 32;
         const int f = grp * g.G + fl;
+        const int sub = (ch - fl * cpk) % chg;  // position of the chunk in its store
         uint32_t r[32];
         tmem_wait_ld(rn);
 #pragma unroll
         for (int i = 0; i < 32; ++i) r[i] = rn[i];
         if (ch + 1 < nchunks) tmem_ld32_nowait(acc + (uint32_t)(32 * (ch + 1)), rn);
         const float inv = __shfl_sync(0xffffffffu, inv_l, fl);
-        // the previous chunk's store has read the staging buffer
-        if (lane == 0) bulk_wait_read();
-        __syncwarp();
+        const uint32_t buf = stg + (uint32_t)(sg % kTcStgBufs) * (uint32_t)(kTcStgChunks * 4096);
+        if (sub == 0) {
+            // this buffer's previous store has read it (with no store in this
+            // tile, wait for every store: the rotation no longer counts)
+            if (lane == 0) {
+                if (stores) bulk_wait_read<kTcStgBufs - 1>();
+                else bulk_wait_read<0>();
+            }
+            __syncwarp();
+        }
+        const uint32_t cb = buf + (uint32_t)sub * 4096u;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float v[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(__uint_as_float(r[4 * i + e]), inv);
             asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
-                             stg + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
+                             cb + (uint32_t)lane * 128u + (uint32_t)((i ^ (lane & 7)) * 16)),
                          "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
                          : "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
-        __syncwarp();
-        if (lane == 0 && row0 < rows_full) tma_store_3d(tmY, stg, c, (int)row0, f);
+        if (sub == chg - 1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
+            __syncwarp();
+            if (lane == 0 && stores) {
+                if (chg == 1) tma_store_3d(tmY, buf, c, (int)row0, f);
+                else tma_store_4d(tmY, buf, 0, (int)row0, c / 32 - (chg - 1), f);
+            }
+            ++sg;
+        }
         const int64_t t0 = (row0 + lane) * g.P + c;  // this lane's first output
         if (row0 + lane == tail_row) {
             float* yf = y + (int64_t)f * g.ldy;
@@ -359,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, issued_sh;
     const uint32_t base = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;
-    // [output staging, 4 KB per epilogue warp][A buffer 0][A buffer 1][B stages] (RESIDENT_A)
+    // [output staging, kTcStgWarp per epilogue warp][A buffer 0][A buffer 1][B stages] (RESIDENT_A)
     // [output staging][B stage, A stage] x stages (otherwise)
     const uint32_t abuf0 = base + kTcStageOut;
     const uint32_t ring = RESIDENT_A ? abuf0 + 2u * (uint32_t)g.abuf_bytes : abuf0;
@@ -482,7 +528,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {  // epilogue: warps 2-5, tensor-memory lane quarter warp % 4
         const int lq = warp & 3;
-        int local = 0;
+        int local = 0, sg = 0;
         for (int64_t u = blockIdx.x; u < nsets; u += gridDim.x, ++local) {
             const int a = local & 1;
             const bool ok = mbar_wait(smem_u32(&accf_bar[a]), (uint32_t)(local >> 1) & 1u, true);
@@ -494,8 +540,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             const int64_t blk = u / g.ngroups;
             const int grp = (int)(u % g.ngroups);
-            epilogue_tile(g, &tmY, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * 4096u,
-                          lane, lq, inv_tab, y, yq, status);
+            epilogue_tile(g, &tmY, blk, grp, tmem + (uint32_t)(a * kTcTmemCols), base + (uint32_t)(warp - 2) * kTcStgWarp,
+                          lane, lq, inv_tab, y, yq, status, sg);
             // every tcgen05.ld of this buffer has completed (wait::ld): hand it back
             tc_fence_before();
             __syncwarp();
@@ -556,20 +602,34 @@ bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The FP32 outputs as a 3-D map for the epilogue's stores: P phases (inner), the
-// out_len / P whole rows of a kernel (row pitch P floats), F kernels (pitch ldy
-// floats); box 32 x 32 x 1 (one 32-row, 128-byte-wide chunk), 128-byte swizzle.
-// With fewer than P outputs there is no whole row: the map gets one row and the
-// epilogue stores nothing through it.
+// The FP32 outputs as a map for the epilogue's stores, 128-byte swizzle.  One
+// chunk per store: 3-D, P phases (inner), the out_len / P whole rows of a
+// kernel (row pitch P floats), F kernels (pitch ldy floats); box 32 x 32 x 1.
+// Several: 4-D, 32 phases (inner), rows (pitch P floats), P / 32 sub-rows
+// (pitch 32 floats), F kernels; box 32 x 32 x stg_ch x 1, so that the staged
+// chunks of a store are [sub-row][row][32 phases] in shared memory and each
+// 128-byte line keeps the swizzle phase of its row.  With fewer than P outputs
+// there is no whole row: the map gets one row and the epilogue stores nothing
+// through it.
 bool encode_out(CUtensorMap* m, float* y, const TcGeom& g) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const int64_t rows = g.out_len / g.P;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)(rows > 0 ? rows : 1), (cuuint64_t)g.F};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4u, (cuuint64_t)g.ldy * 4u};
-    const cuuint32_t box[3] = {32, 32, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const cuuint64_t nrows = (cuuint64_t)(rows > 0 ? rows : 1);
+    if (g.stg_ch == 1) {
+        const cuuint64_t dims[3] = {(cuuint64_t)g.P, nrows, (cuuint64_t)g.F};
+        const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4u, (cuuint64_t)g.ldy * 4u};
+        const cuuint32_t box[3] = {32, 32, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const cuuint64_t dims[4] = {32, nrows, (cuuint64_t)(g.P / 32), (cuuint64_t)g.F};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.P * 4u, 128u, (cuuint64_t)g.ldy * 4u};
+    const cuuint32_t box[4] = {32, 32, (cuuint32_t)g.stg_ch, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -595,6 +655,7 @@ bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g) {
     g->nb = (g->out_len + g->T - 1) / g->T;
     g->seg_rows = ((int64_t)g->T + g->Kpad + g->P - 1) / g->P;
     g->ldy = g->out_len;
+    g->stg_ch = kTcStgChunks < g->P / 32 ? kTcStgChunks : g->P / 32;
     const int budget = kTcSmemCap - 1024;  // data bytes after the 1024-byte alignment slack
     if (g->P * esize == 128) {
         g->a_loads = (kTcM - 1 + g->ktiles + kTcABoxRows - 1) / kTcABoxRows;

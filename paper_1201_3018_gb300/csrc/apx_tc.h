@@ -49,6 +49,7 @@ struct TcGeom {
     int a_loads;      // P = 64: 128-row TMA boxes that make up a tile's whole A operand
     int abuf_bytes;   // P = 64: bytes of one A buffer (a_loads x 16 KB)
     int smem_bytes;   // dynamic shared memory of the GEMM kernel
+    int stg_ch;       // output chunks (32 rows x 32 phases) per bulk store of the epilogue
 };
 
 bool tc_geometry(int64_t L, int F, int N, int esize, TcGeom* g);
