@@ -189,6 +189,7 @@ struct KStats {
     float Mk;
     int bad;
     double sig2k;
+    float sig2k_f, thr_f;  // sig2k and the call's SNR threshold rounded to FP32 (the model's FP32 screen)
 };
 
 // ||k||_inf and, when a packing candidate needs it, the kernel's second moment
@@ -227,6 +228,8 @@ __device__ inline KStats kernel_stats(const Params& p, Shared& sh) {
         acc = block_reduce<long long, false>(acc, sh.redl);
         k.sig2k = fx_moment(acc, f, p.N, sh);
     }
+    k.sig2k_f = (float)k.sig2k;
+    k.thr_f = (float)p.thr;
     return k;
 }
 
@@ -277,25 +280,72 @@ __device__ __forceinline__ void write_stats(const Params& p, long long i, int mo
 }
 
 // Prologue result.
+// A block's maximum and second moment.  The moment stays the exact
+// fixed-point sum acc (scale 2^fsh) in every thread; pro_sig2 gives the FP64
+// value (as fx_moment rounds it) where a thread needs it, and s2s_f its FP32
+// approximation for the model's FP32 screen.
 struct Pro {
     int kind;     // 0 full / packed decided later, 2 zero, 3 non-finite
     float Ms;
-    double sig2;
+    long long acc;
+    int fsh;
+    float s2s_f;
 };
+
+// The FP32 approximation of sum q^2 * 2^(-2 sh) / n (sum >= 0): within 2^-22
+// relative where the result is a normal number.
+__device__ __forceinline__ float fx_moment_f32(long long sum, int sh, int n) {
+    const float hi = (float)(int)(sum >> 32), lo = (float)(unsigned)(sum & 0xffffffffll);
+    return __fdiv_rn(ldexpf(fmaf(hi, 4294967296.f, lo), -2 * sh), (float)n);
+}
+
+// The block's second moment in FP64, the same bits as fx_moment.
+__device__ __forceinline__ double pro_sig2(const Pro& r, int n) {
+    if (r.kind != 0) return 0.0;
+    const double v = ldexp(__ll2double_rn(r.acc), -2 * r.fsh);
+    return (n & (n - 1)) == 0 ? ldexp(v, -(31 - __clz(n))) : __ddiv_rn(v, (double)n);
+}
 
 __device__ __forceinline__ Pro block_prologue(const Params& p, const float* xs, const KStats& ks, Shared& sh) {
     Pro r;
     r.Ms = block_maxabs(xs, p.Wb, sh.redf, sh.redi);
-    r.sig2 = 0.0;
+    r.acc = 0;
+    r.fsh = 0;
+    r.s2s_f = 0.f;
     if (!(r.Ms <= 3.402823466e38f) || ks.bad) { r.kind = 3; return r; }  // NaN or inf
     if (r.Ms == 0.f || ks.Mk == 0.f) { r.kind = 2; return r; }
     const FxScale f = fx_scale(r.Ms);
     long long acc = 0;
     for (int t = threadIdx.x; t < p.Wb; t += blockDim.x) acc += fx_sq(f, xs[t]);
-    acc = block_reduce<long long, false>(acc, sh.redl);
-    r.sig2 = fx_moment(acc, f, p.Wb, sh);
+    r.acc = block_reduce<long long, false>(acc, sh.redl);
+    r.fsh = f.sh;
+    r.s2s_f = fx_moment_f32(r.acc, f.sh, p.Wb);
     r.kind = 0;
     return r;
+}
+
+// feasible_mask for a block of the direct cores: lane c of warp 0 decides
+// candidate c by the FP32 screen and evaluates the FP64 model only where the
+// screen leaves it open, so that the FP64 chain (a slow pipe on this part)
+// rarely runs; the decisions are snr_feasible's, bit for bit.
+__device__ inline unsigned feasible_mask_pro(const Params& p, const Pro& pr, const KStats& ks, unsigned* slot) {
+    if (threadIdx.x < 32) {
+        const int c = threadIdx.x;
+        bool ok = false;
+        if (c < p.ncand) {
+            if (!p.autosel) {
+                ok = true;
+            } else {
+                const int S = p.cand[c].S, K = p.cand[c].K;
+                const int sc = snr_screen(pr.s2s_f, pr.Ms, ks.sig2k_f, ks.Mk, S, K, ks.thr_f);
+                ok = sc > 0 || (sc == 0 && snr_feasible(pro_sig2(pr, p.Wb), pr.Ms, ks.sig2k, ks.Mk, S, K, p.thr));
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (c == 0) *slot = m;
+    }
+    __syncthreads();
+    return *slot;
 }
 
 __device__ __forceinline__ void handle_trivial(const Params& p, long long i, const BlockGeom& g, const Pro& pr) {

@@ -179,7 +179,9 @@ __device__ void full_block_f32(const Params& p, long long i, const BlockGeom& g,
             }
         }
     }
-    write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+    if (p.st && threadIdx.x == 0)
+        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pro_sig2(pr, p.Wb),
+                    __longlong_as_double(0x7ff0000000000000ll), 0.0);
 }
 
 // ---- the tensor-core candidate (APX_CORE_TC)
@@ -282,9 +284,13 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
                             sdesc_sw128(tb.bbase + (uint32_t)kt * 8192u + 32u * k), umma_idesc_f16(128, kTcbRow),
                             (kt | k) != 0);
         umma_commit(bar);
+        // the issuing thread alone waits (bounded: false after about two
+        // seconds); the others wait at the barrier instead of polling
+        sh.redi[0] = mbar_wait(bar, parity, true) ? 1 : 0;
     }
-    const bool ok = mbar_wait(bar, parity, true);  // bounded: false after about two seconds
+    __syncthreads();
     tc_fence_after();
+    const bool ok = sh.redi[0] != 0;
     // Accumulator row q (tensor-memory lane q) into the FP32 window's space, now
     // dead, at the columns tc_stage_col gives.
     float* stage = xs;
@@ -316,7 +322,8 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
         return __fmul_rn(v, inv);
     });
     if (p.st && t == 0)  // (the model's FP64 log10 only where a record is written)
-        write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K),
+        write_stats(p, i, APX_BLK_TC, &c, cs, pr.Ms, pro_sig2(pr, p.Wb),
+                    snr_model_db(pro_sig2(pr, p.Wb), pr.Ms, ks.sig2k, ks.Mk, c.S, c.K),
                     0.0);
 }
 
@@ -324,7 +331,7 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
 // an instantiation of its own, so that the other kernels are compiled as if
 // it did not exist.
 template <bool BATCH, bool LIT>
-__global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, const BatchTab bt) {
+__global__ void __launch_bounds__(kDirectThreads, 4) k_direct(const Params p0, const BatchTab bt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ unsigned s_feas;
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
 
     // Section IV.D: first candidate (in the Table 1 order) whose model SNR meets
     // the target; with a fixed quantiser the single candidate is taken.
-    const unsigned feas = feasible_mask(p, pr.sig2, pr.Ms, ks.sig2k, ks.Mk, &s_feas);
+    const unsigned feas = feasible_mask_pro(p, pr, ks, &s_feas);
     const int ci = feas ? __ffs(feas) - 1 : -1;
 
     if (ci < 0 && p.full64) {
@@ -380,7 +387,9 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
                 }
             }
         }
-        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pr.sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        if (p.st && threadIdx.x == 0)
+            write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pro_sig2(pr, p.Wb),
+                        __longlong_as_double(0x7ff0000000000000ll), 0.0);
         return;
     }
     if (ci < 0) {
@@ -465,7 +474,8 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const Params p0, cons
         return __fmul_rn(__ll2float_rn(rt), inv);
     });
     if (p.st && threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, pr.Ms, pr.sig2, snr_model_db(pr.sig2, pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
+        write_stats(p, i, c.blk, &c, cs, pr.Ms, pro_sig2(pr, p.Wb),
+                    snr_model_db(pro_sig2(pr, p.Wb), pr.Ms, ks.sig2k, ks.Mk, c.S, c.K), 0.0);
 }
 
 // The tensor-core candidate's kernel (APX_CORE_TC): each CTA takes kTcbBlocks
@@ -510,7 +520,7 @@ __global__ void __launch_bounds__(kDirectThreads, 4) k_direct_tc(const Params p0
         const Pro pr = block_prologue(p, xs, ks, sh);
         if (pr.kind != 0) {
             handle_trivial(p, i, g, pr);
-        } else if (!feasible_mask(p, pr.sig2, pr.Ms, ks.sig2k, ks.Mk, &s_feas)) {
+        } else if (!feasible_mask_pro(p, pr, ks, &s_feas)) {
             full_block_f32(p, i, g, pr, xs, smem);
         } else {
             tc_block_body(p, i, g, p.cand[0], ks, pr, ck, xs, tb, tmem, smem_u32(&s_bar), phase, sh);

@@ -137,7 +137,9 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
         Pro pr;
         pr.kind = (!finite || kbad) ? 3 : 2;
         pr.Ms = Ms;
-        pr.sig2 = 0.0;
+        pr.acc = 0;
+        pr.fsh = 0;
+        pr.s2s_f = 0.f;
         handle_trivial(p, i, g, pr);
         return;
     }

@@ -144,7 +144,7 @@ constexpr long long kTcbSumMax = 1LL << 24;
 __host__ __device__ constexpr int tcb_kshift(int Nodd) { return (Nodd - 1 + kTcbRow - 1) / kTcbRow * kTcbRow; }
 __host__ __device__ constexpr int tcb_kslices(int Nodd) { return tcb_kshift(Nodd) / kTcbRow + 1; }
 // blocks per CTA of the tensor-core kernel (its setup is shared by them)
-constexpr int kTcbBlocks = 8;
+constexpr int kTcbBlocks = 12;
 __host__ __device__ constexpr long long tcb_ctas(long long P) { return (P + kTcbBlocks - 1) / kTcbBlocks; }
 
 // Several requests in one launch: request r owns CTAs [cta_start[r], cta_start[r+1]).
@@ -224,6 +224,32 @@ __device__ inline bool snr_feasible(double s2s, float Ms, double s2k, float Mk, 
     double c = __dmul_rn(__dmul_rn(s2k, K2), Ms2);
     double den = __dadd_rn(__dmul_rn(12.0, __dadd_rn(a, c)), __dmul_rn(Ms2, Mk2));
     return num >= __dmul_rn(thr, den);
+}
+
+// The same comparison in FP32, as a screen: +1 feasible, -1 not, 0 undecided
+// (left to snr_feasible).  With every operand and intermediate in [1e-30,
+// 1e30] (normal, finite) each FP32 value is within 2^-20 relative of its FP64
+// counterpart (inputs rounded once, a few products of non-negative terms), so
+// a decision with a margin of 2^-14 between the two sides is the one the FP64
+// comparison takes.
+__device__ inline int snr_screen(float s2s, float Ms, float s2k, float Mk, int S, int K, float thr) {
+    const float S2 = (float)S * (float)S, K2 = (float)K * (float)K;
+    const float Ms2 = Ms * Ms, Mk2 = Mk * Mk;
+    const float ss = s2s * s2k, SK = S2 * K2, t144 = 144.f * ss;
+    const float num = t144 * SK;
+    const float sa = s2s * S2, a = sa * Mk2;
+    const float kc = s2k * K2, c = kc * Ms2;
+    const float mm = Ms2 * Mk2, den = 12.f * (a + c) + mm;
+    const float rhs = thr * den;
+    const float lo = fminf(fminf(fminf(fminf(s2s, s2k), fminf(Ms2, Mk2)), fminf(fminf(ss, SK), fminf(t144, num))),
+                           fminf(fminf(fminf(sa, a), fminf(kc, c)), fminf(fminf(mm, den), fminf(rhs, thr))));
+    const float hi = fmaxf(fmaxf(fmaxf(fmaxf(s2s, s2k), fmaxf(Ms2, Mk2)), fmaxf(fmaxf(ss, SK), fmaxf(t144, num))),
+                           fmaxf(fmaxf(fmaxf(sa, a), fmaxf(kc, c)), fmaxf(fmaxf(mm, den), fmaxf(rhs, thr))));
+    if (!(lo >= 1e-30f && hi <= 1e30f)) return 0;
+    const float marg = 1.f + 0x1p-14f;
+    if (num >= rhs * marg) return 1;
+    if (num * marg <= rhs) return -1;
+    return 0;
 }
 
 __device__ inline double snr_model_db(double s2s, float Ms, double s2k, float Mk, int S, int K) {
