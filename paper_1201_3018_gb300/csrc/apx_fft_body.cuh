@@ -98,14 +98,22 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
     const int bad = mb > 0x7f800000;
     const float m = bad ? 0.f : __int_as_float(mb);
     const bool finite = !bad && m <= 3.402823466e38f;
-    double sig2 = 0.0;
+    // the second moment as its exact fixed-point sum (pro_sig2 rounds it to
+    // FP64 where a thread needs it; s2s_f feeds the model's FP32 screen)
+    Pro pr;
+    pr.kind = 0;
+    pr.Ms = m;
+    pr.acc = 0;
+    pr.fsh = 0;
+    pr.s2s_f = 0.f;
     if (finite && m > 0.f) {
         const FxScale f = fx_scale(m);
         long long acc = 0;
 #pragma unroll
         for (int v = 0; v < kVals; ++v) acc += fx_sq(f, xv[v]);
-        acc = block_reduce<long long, false>(acc, sh.redl);
-        sig2 = fx_moment(acc, f, p.Wb, sh);
+        pr.acc = block_reduce<long long, false>(acc, sh.redl);
+        pr.fsh = f.sh;
+        pr.s2s_f = fx_moment_f32(pr.acc, f.sh, p.Wb);
     }
 
     // Full precision is every block's fallback: start its forward FFT (FP32)
@@ -134,12 +142,8 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
     const double sig2k = __ldcg(&p.ki->sig2k);
     const float Ms = bad ? __int_as_float(0x7fc00000) : m;
     if (!finite || kbad || m == 0.f || Mk == 0.f) {
-        Pro pr;
         pr.kind = (!finite || kbad) ? 3 : 2;
         pr.Ms = Ms;
-        pr.acc = 0;
-        pr.fsh = 0;
-        pr.s2s_f = 0.f;
         handle_trivial(p, i, g, pr);
         return;
     }
@@ -149,7 +153,13 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
     float cs = 0.f, ck = 0.f;
     double ferr = 0.0;
     bool have_window = false;
-    const unsigned feas = feasible_mask(p, sig2, m, sig2k, Mk, &s_feas);
+    KStats ks;
+    ks.Mk = Mk;
+    ks.bad = kbad;
+    ks.sig2k = sig2k;
+    ks.sig2k_f = threadIdx.x < 32 ? (float)sig2k : 0.f;  // FP64 conversions in the deciding warp only
+    ks.thr_f = threadIdx.x < 32 ? (float)p.thr : 0.f;
+    const unsigned feas = feasible_mask_pro(p, pr, ks, &s_feas);
     for (int c = 0; c < p.ncand; ++c) {
         if (!((feas >> c) & 1u)) continue;
         const Cand& cd = p.cand[c];
@@ -189,7 +199,9 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
             iv = 0;
             return APX_IN_BOUNDS(j >= 0 && j < p.Wb, p.status) ? word<float>(Zf, j) : 0.f;
         });
-        write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, Ms, sig2, __longlong_as_double(0x7ff0000000000000ll), 0.0);
+        if (p.st && threadIdx.x == 0)
+            write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, Ms, pro_sig2(pr, p.Wb),
+                        __longlong_as_double(0x7ff0000000000000ll), 0.0);
         return;
     }
 
@@ -293,7 +305,8 @@ __device__ __forceinline__ void fft_block_body(const Params& p, long long i, int
         return __fmul_rn(__ll2float_rn(rt), inv);
     });
     if (p.st && threadIdx.x == 0)
-        write_stats(p, i, c.blk, &c, cs, Ms, sig2, snr_model_db(sig2, m, sig2k, Mk, c.S, c.K), ferr);
+        write_stats(p, i, c.blk, &c, cs, Ms, pro_sig2(pr, p.Wb), snr_model_db(pro_sig2(pr, p.Wb), m, sig2k, Mk, c.S, c.K),
+                    ferr);
 }
 
 }  // namespace apx
