@@ -184,22 +184,21 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Block-wide reduction; `red` is shared scratch of >= 32 elements of T.
+// Every warp reduces the per-warp partials itself (the same values in the
+// same shuffle order, so every thread gets the same bits), which takes two
+// barriers: the partials written, then read by everyone before any thread
+// writes `red` again.  Other users of the scratch end with a barrier after
+// their last read, so none is needed before the partials are written.
 template <typename T, bool IS_MAX>
 __device__ T block_reduce(T v, T* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = IS_MAX ? warp_max(v) : warp_sum(v);
-    __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    if (wid == 0) {
-        T t = lane < nw ? red[lane] : (IS_MAX ? red[0] : T(0));
-        t = IS_MAX ? warp_max(t) : warp_sum(t);
-        if (lane == 0) red[0] = t;
-    }
+    T t = lane < nw ? red[lane] : (IS_MAX ? red[0] : T(0));
+    t = IS_MAX ? warp_max(t) : warp_sum(t);
     __syncthreads();
-    T out = red[0];
-    __syncthreads();
-    return out;
+    return t;
 }
 
 // ||x||_inf over n samples in shared memory; returns NaN if any sample is NaN
