@@ -327,6 +327,23 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
                     0.0);
 }
 
+// One tap chunk [n0, n1) of the packed FP64 convolution over outputs [olo,
+// ohi), R per thread, continuing the partial sums in tb.
+template <int R, bool LIT>
+__device__ __forceinline__ void packed_conv_pass(const double* sb, int nsb, const double* kb, double* tb, int n0,
+                                                 int n1, int olo, int ohi) {
+    for (int ch = threadIdx.x; olo + ch * R < ohi; ch += blockDim.x) {
+        const int j0 = olo + ch * R;
+        double acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = (n0 > 0 && j0 + r < ohi) ? tb[j0 + r] : 0.0;
+        conv_f64<R, LIT>(sb, nsb, kb, n0, n1, j0, acc);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (j0 + r < ohi) tb[j0 + r] = acc[r];
+    }
+}
+
 // LIT: the paper-literal symmetric form (APX_LITERAL, single calls only) in
 // an instantiation of its own, so that the other kernels are compiled as if
 // it did not exist.
@@ -447,17 +464,11 @@ __global__ void __launch_bounds__(kDirectThreads, 4) k_direct(const Params p0, c
         for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x)  // Eq. (5) / k~
             kb[n - n0] = LIT ? kbar_literal(p, c, ck, n) : (double)kbar_int(p, c, ck, n);
         __syncthreads();
-        for (int ch = threadIdx.x; olo + ch * kRd < ohi; ch += blockDim.x) {
-            const int j0 = olo + ch * kRd;
-            double acc[kRd];
-#pragma unroll
-            for (int r = 0; r < kRd; ++r) acc[r] = (n0 > 0 && j0 + r < ohi) ? tb[j0 + r] : 0.0;
-            if (LIT) conv_f64<kRd, true>(sb, nsb, kb, n0, n1, j0, acc);
-            else conv_f64<kRd, false>(sb, nsb, kb, n0, n1, j0, acc);
-#pragma unroll
-            for (int r = 0; r < kRd; ++r)
-                if (j0 + r < ohi) tb[j0 + r] = acc[r];
-        }
+        // two outputs per thread when four would leave most threads idle (a
+        // W_block of 1024 has about 580 packed outputs): the FP64 pipe then sees
+        // twice the warps; each output's sum runs in the same order either way
+        if (ohi - olo < 4 * (int)blockDim.x) packed_conv_pass<2, LIT>(sb, nsb, kb, tb, n0, n1, olo, ohi);
+        else packed_conv_pass<kRd, LIT>(sb, nsb, kb, tb, n0, n1, olo, ohi);
     }
     __syncthreads();
 
