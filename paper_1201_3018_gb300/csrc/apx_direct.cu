@@ -327,6 +327,37 @@ __device__ void tc_block_body(const Params& p, long long i, const BlockGeom& g, 
                     0.0);
 }
 
+// The FP64 full-precision form over the block's kept outputs, R per thread,
+// rounded once to FP32 (16-byte stores for runs of 4 kept whole and aligned).
+template <int R>
+__device__ __forceinline__ void full64_pass(const Params& p, const BlockGeom& g, const double* sd, const double* kd,
+                                            int nkp) {
+    const int nout = g.hi - g.lo;
+    for (int ch = threadIdx.x; ch * R < nout; ch += blockDim.x) {
+        const int j0 = g.lo + ch * R;
+        double acc[R];
+        conv_f64_full<R>(sd, kd, nkp, j0, acc);
+        float accf[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) accf[r] = __double2float_rn(acc[r]);
+        if constexpr (R % 4 == 0) {
+            if (run_vec<R>(p, g, j0)) {
+                store_run<R>(p, g.start + j0, accf, p.rq != nullptr);
+                continue;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = j0 + r;
+            const long long o = g.start + j;
+            if (j < g.hi && o >= 0 && o < p.out_len) {
+                p.r[o] = accf[r];
+                if (p.rq) p.rq[o] = 0;
+            }
+        }
+    }
+}
+
 // One tap chunk [n0, n1) of the packed FP64 convolution over outputs [olo,
 // ohi), R per thread, continuing the partial sums in tb.
 template <int R, bool LIT>
@@ -382,28 +413,10 @@ __global__ void __launch_bounds__(kDirectThreads, 4) k_direct(const Params p0, c
         for (int t = threadIdx.x; t < dl.nS - dl.padS; t += blockDim.x) sd[t] = t < p.Wb ? (double)xs[t] : 0.0;
         for (int n = threadIdx.x; n < nkp; n += blockDim.x) kd[n] = (double)ktap(p, n);
         __syncthreads();
-        const int nout = g.hi - g.lo;
-        for (int ch = threadIdx.x; ch * kRd < nout; ch += blockDim.x) {
-            const int j0 = g.lo + ch * kRd;
-            double acc[kRd];
-            conv_f64_full<kRd>(sd, kd, nkp, j0, acc);
-            float accf[kRd];
-#pragma unroll
-            for (int r = 0; r < kRd; ++r) accf[r] = __double2float_rn(acc[r]);
-            if (run_vec<kRd>(p, g, j0)) {
-                store_run<kRd>(p, g.start + j0, accf, p.rq != nullptr);
-            } else {
-#pragma unroll
-                for (int r = 0; r < kRd; ++r) {
-                    const int j = j0 + r;
-                    const long long o = g.start + j;
-                    if (j < g.hi && o >= 0 && o < p.out_len) {
-                        p.r[o] = accf[r];
-                        if (p.rq) p.rq[o] = 0;
-                    }
-                }
-            }
-        }
+        // two outputs per thread when four would leave most threads idle, as the
+        // packed form does (the same sums either way)
+        if (g.hi - g.lo < 4 * (int)blockDim.x) full64_pass<2>(p, g, sd, kd, nkp);
+        else full64_pass<kRd>(p, g, sd, kd, nkp);
         if (p.st && threadIdx.x == 0)
             write_stats(p, i, APX_BLK_FULL, nullptr, 0.f, pr.Ms, pro_sig2(pr, p.Wb),
                         __longlong_as_double(0x7ff0000000000000ll), 0.0);
