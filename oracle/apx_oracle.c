@@ -610,7 +610,7 @@ static int prep_mode(mode_t_* md, int blk, int32_t S, int32_t K, const float* kr
     } else if (blk == OR_BLK_SYM) {
         md->nk = (Nodd + 1) / 2;
         md->kpk = malloc(sizeof(double) * (size_t)md->nk);
-        or_pack_sym_kernel(kq, Nodd, md->b, md->kpk);                 /* Eq. (5), c2 */
+        or_pack_sym_kernel(kq, Nodd, md->b, md->kpk);                 /* Eq. (5), the pair swapped */
         int64_t l1 = 0;
         for (int32_t n = 0; n < md->nk; ++n) {
             int64_t ko = (2 * n + 1 < Nodd) ? kq[2 * n + 1] : 0;

@@ -9,11 +9,11 @@
  * the CUDA library: its own header, its own constants, its own arithmetic.
  *
  * Every function cites the passage of the paper it follows.  Where the paper
- * is silent, ambiguous or garbled the reading taken is stated beside the code
- * (readings c1..c11: block geometry, the kernel-pair order of symmetric
- * packing, power-of-two epsilon, the u_sys term, exactness bounds, the
- * asymmetric layout, FFT exactness, rounding, cross-correlation, the
- * per-block selector, SNR measurement).
+ * is silent, ambiguous or garbled the reading taken is stated beside the code:
+ * the block geometry, the kernel-pair order of symmetric packing, a
+ * power-of-two epsilon, the u_sys term, the exactness bounds, the asymmetric
+ * layout, FFT exactness, rounding, cross-correlation, the per-block selector
+ * and SNR measurement.
  */
 #ifndef APX_ORACLE_H
 #define APX_ORACLE_H
