@@ -8,7 +8,8 @@
 // The FP32 spectrum H[k] = FFT_n(taps)[k] / (4m), k in [0, m], n = W_block = 2m:
 //   spec_subfft(r)   Y_r = FFT_{n/R1}(h[r], h[r+R1], ...) into Ysub, r < R1
 //                    (decimation in time; the transform takes the radix of a
-//                    kSpecThreads-thread CTA whatever the caller's size)
+//                    kSpecRadixNt-thread CTA whatever the caller's size: radix
+//                    8 at 512 points, three passes)
 //   spec_combine(k)  H[k] = sum_{r < R1} W_n^(r k) Y_r[k mod n/R1] (the last
 //                    decimation stage, one frequency)
 //   spec_stats()     ||k||_inf, the second moment and the exact ||kbar||_1 of
@@ -21,15 +22,18 @@
 namespace apx {
 
 constexpr long long kPrepSpinCycles = 2000000000LL;  // about one second at the maximum SM clock
+// the thread count the sub-transforms' radix is chosen for (their CTAs have
+// more threads; the surplus waits at the passes' barriers)
+constexpr int kSpecRadixNt = 64;
 
 // Y_r into Ysub[r * ns ..], Z: shared scratch of padded_len(ns) entries.
 __device__ inline void spec_subfft(const Params& p, int r, float2* Z) {
     const int n = p.Wb, R1 = spec_r1(n), ns = n / R1;
     for (int j = threadIdx.x; j < ns; j += blockDim.x) Z[pad16(j)] = make_float2(ktap(p, r + j * R1), 0.f);
     __syncthreads();
-    fft_smem_nt<float2, false>(Z, ns, kSpecThreads, p.tw32, p.ntab, p.status);
+    fft_smem_nt<float2, false>(Z, ns, kSpecRadixNt, p.tw32, p.ntab, p.status);
     for (int k = threadIdx.x; k < ns; k += blockDim.x)
-        p.Ysub[r * ns + k] = Z[pad16(fft_perm_nt<float2>(k, ns, kSpecThreads))];
+        p.Ysub[r * ns + k] = Z[pad16(fft_perm_nt<float2>(k, ns, kSpecRadixNt))];
     __syncthreads();  // Z is free again
 }
 
